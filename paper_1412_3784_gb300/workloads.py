@@ -1,0 +1,232 @@
+"""Seeded synthetic inputs for the cell-list force evaluation.
+
+This module only *constructs inputs*: flows (A, L0, M, T), strain times and
+particle positions.  It holds none of the method's arithmetic (no lattice
+evolution kernel, no wrapping, no cell assignment, no forces); both the CUDA
+path and the CPU oracle read what it produces, and neither is imported here.
+
+Inputs follow the paper's problem statement: a lattice L = [v1 v2 v3] whose
+columns are the lattice vectors (Sec. 2), a linear flow u(x) = A x with
+L_t = exp(tA) L0 (Sec. 2.1, Eq. for dL/dt), and the Kraynik-Reinelt
+condition exp(A t*) L0 = L0 M with M in SL(3,Z) (Sec. 2.2, Eq. kr).
+
+Construction of the KR flows.  For a symmetric M in SL(3,Z) with distinct
+positive eigenvalues lambda_k and orthonormal eigenvectors V, the flow
+A = V diag(ln lambda_k) V^T / T with a cubic L0 = s I satisfies the KR
+condition exactly: exp(T A) L0 = s V diag(lambda) V^T = L0 M.  Particles are
+placed affinely with the flow: q(t) = F(tau) L0 s_fcc + delta, where
+F(tau) = V diag(lambda^(tau/T)) V^T is the deformation this construction
+prescribes, s_fcc are ideal face-centred-cubic fractional sites and delta is a
+fixed i.i.d. Gaussian displacement per particle.  The density is preserved
+because det F = 1.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+# The two remapping matrices of the planar and general 3D flows.
+M_PLANAR = np.array([[2, 1, 0], [1, 1, 0], [0, 0, 1]], dtype=np.int64)
+M_GENERAL = np.array([[3, 2, 1], [2, 2, 1], [1, 1, 1]], dtype=np.int64)
+M_IDENTITY = np.eye(3, dtype=np.int64)
+
+RHO_DEFAULT = 0.8442
+DISPLACEMENT_STD = 0.05
+WCA_RC = 2.0 ** (1.0 / 6.0)
+LJ_RC = 2.5
+
+POT_LJ = 0
+POT_WCA = 1
+
+
+@dataclasses.dataclass
+class Workload:
+    """One force-evaluation input: flow, time, positions and potential."""
+
+    name: str
+    A: np.ndarray          # (3,3) float64 flow matrix
+    L0: np.ndarray         # (3,3) float64, columns are lattice vectors
+    M: np.ndarray          # (3,3) int64 remapping matrix, det 1
+    T: float               # period of the KR remap
+    t: float               # evaluation time
+    q: np.ndarray          # (N,3) float64 Cartesian positions, any image
+    kind: int = POT_LJ     # POT_LJ or POT_WCA
+    rc: float = LJ_RC
+    eps: float = 1.0
+    sigma: float = 1.0
+    shift: int = 1         # energy shifted to zero at rc
+
+    @property
+    def n(self) -> int:
+        return int(self.q.shape[0])
+
+
+def fcc_fractional(k: int) -> np.ndarray:
+    """Ideal FCC sites of k^3 conventional cells in the unit cube, shape (4k^3, 3)."""
+    basis = np.array([[0.0, 0.0, 0.0], [0.5, 0.5, 0.0], [0.5, 0.0, 0.5], [0.0, 0.5, 0.5]])
+    g = np.arange(k, dtype=np.float64)
+    cz, cy, cx = np.meshgrid(g, g, g, indexing="ij")
+    corners = np.stack([cx.ravel(), cy.ravel(), cz.ravel()], axis=1)
+    sites = (corners[:, None, :] + basis[None, :, :]).reshape(-1, 3)
+    return sites / float(k)
+
+
+def kr_flow(M: np.ndarray, T: float = 1.0):
+    """Flow construction for a symmetric M: returns (A, V, lam).
+
+    A = V diag(ln lam) V^T / T.  V has orthonormal columns sorted by eigenvalue.
+    """
+    Mf = np.asarray(M, dtype=np.float64)
+    if not np.allclose(Mf, Mf.T):
+        raise ValueError("kr_flow builds flows for symmetric M only")
+    lam, V = np.linalg.eigh(Mf)
+    if np.any(lam <= 0):
+        raise ValueError("M must be positive definite")
+    A = (V * (np.log(lam) / T)) @ V.T
+    A = 0.5 * (A + A.T)
+    return A, V, lam
+
+
+def _deformation(V, lam, tau, T):
+    return (V * (lam ** (tau / T))) @ V.T
+
+
+def perturbed_fcc(k: int, rho: float, rng: np.random.Generator, *, vacancies: int = 0,
+                  std: float = DISPLACEMENT_STD):
+    """Fractional FCC sites (with optional random vacancies), box side and displacements."""
+    s = fcc_fractional(k)
+    if vacancies:
+        keep = np.sort(rng.permutation(s.shape[0])[: s.shape[0] - vacancies])
+        s = s[keep]
+    n = s.shape[0]
+    side = (n / rho) ** (1.0 / 3.0)
+    delta = rng.normal(0.0, std, size=(n, 3))
+    return s, side, delta
+
+
+def _finish(name, A, L0, M, T, t, s, delta, F, rng, kind, rc, shuffle=True):
+    q = (F @ (L0 @ s.T)).T + delta
+    if shuffle:
+        q = q[rng.permutation(q.shape[0])]
+    return Workload(name=name, A=A, L0=L0, M=M, T=T, t=t, q=np.ascontiguousarray(q),
+                    kind=kind, rc=rc)
+
+
+def config_equilibrium_wca(k: int = 10, seed: int = 0) -> Workload:
+    """Plain WCA system at rest: N = 4k^3, cubic box at density 0.8442, A = 0, t = 0."""
+    rng = np.random.default_rng(seed)
+    s, side, delta = perturbed_fcc(k, RHO_DEFAULT, rng)
+    L0 = side * np.eye(3)
+    return _finish(f"wca_eq_N{s.shape[0]}", np.zeros((3, 3)), L0, M_IDENTITY.copy(), 1.0, 0.0,
+                   s, delta, np.eye(3), rng, POT_WCA, WCA_RC)
+
+
+def config_flow(M: np.ndarray, k: int, t: float, seed: int, *, T: float = 1.0,
+                rho: float = RHO_DEFAULT, kind: int = POT_LJ, rc: float | None = None,
+                rate: float = 1.0, vacancies: int = 0, name: str | None = None) -> Workload:
+    """Perturbed FCC under the KR flow of a symmetric M, evaluated at time t.
+
+    rate scales the strain rate: A = rate * V diag(ln lam) V^T / T, period T / rate.
+    Positions are affine in the flow (see module docstring); the same seed gives
+    the same sites and displacements at every t.
+    """
+    rng = np.random.default_rng(seed)
+    s, side, delta = perturbed_fcc(k, rho, rng, vacancies=vacancies)
+    period = T / rate
+    A, V, lam = kr_flow(M, period)
+    tau = t - period * math.floor(t / period)
+    F = _deformation(V, lam, tau, period)
+    L0 = side * np.eye(3)
+    if rc is None:
+        rc = WCA_RC if kind == POT_WCA else LJ_RC
+    nm = name or f"kr_N{s.shape[0]}_t{t:.6g}"
+    return _finish(nm, A, L0, np.asarray(M, dtype=np.int64).copy(), period, t, s, delta, F,
+                   rng, kind, rc)
+
+
+def config_planar(i: int = 0, nstrain: int = 64, k: int = 20, seed: int = 1) -> Workload:
+    """Planar elongational flow, N = 4k^3 (32000 at k = 20), LJ rc = 2.5, t = i / nstrain."""
+    return config_flow(M_PLANAR, k, i / nstrain, seed, name=f"planar_N{4 * k ** 3}_i{i}")
+
+
+def config_general(i: int = 0, nstrain: int = 128, k: int = 40, seed: int = 2,
+                   t: float | None = None) -> Workload:
+    """General 3D flow, N = 4k^3 (256000 at k = 40), LJ rc = 2.5, t = i / nstrain."""
+    tt = i / nstrain if t is None else t
+    return config_flow(M_GENERAL, k, tt, seed, name=f"general_N{4 * k ** 3}_t{tt:.6g}")
+
+
+NEAR_REMAP_T = 1.0 - 2.0 ** -20
+
+
+def batched_systems(nsys: int = 256, seed: int = 3, nmin: int = 1000, nmax: int = 20000):
+    """Independent replicas of uneven N and different flows.
+
+    N ~ U[nmin, nmax]; FCC with kc = ceil((N/4)^(1/3)) cells and 4 kc^3 - N random
+    vacancies; density ~ U(0.8, 0.9); flow planar or general (coin flip) at a
+    strain rate ~ U(0.5, 2) and phase t ~ U[0, period); WCA or LJ rc = 2.5.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for s_idx in range(nsys):
+        n = int(rng.integers(nmin, nmax + 1))
+        kc = int(math.ceil((n / 4.0) ** (1.0 / 3.0) - 1e-12))
+        vac = 4 * kc ** 3 - n
+        rho = float(rng.uniform(0.8, 0.9))
+        M = M_PLANAR if rng.random() < 0.5 else M_GENERAL
+        rate = float(rng.uniform(0.5, 2.0))
+        period = 1.0 / rate
+        t = float(rng.uniform(0.0, period))
+        kind = POT_WCA if rng.random() < 0.5 else POT_LJ
+        sub_seed = int(rng.integers(0, 2 ** 31 - 1))
+        out.append(config_flow(M, kc, t, sub_seed, rho=rho, kind=kind, rate=rate,
+                               vacancies=vac, name=f"batch{s_idx}_N{n}"))
+    return out
+
+
+def uniform_random(n: int, L: np.ndarray, seed: int, rc: float = LJ_RC,
+                   kind: int = POT_LJ) -> Workload:
+    """Uniform random points in a static box L (A = 0), for statistical checks."""
+    rng = np.random.default_rng(seed)
+    s = rng.random((n, 3))
+    q = (np.asarray(L, dtype=np.float64) @ s.T).T
+    return Workload(name=f"uniform_N{n}", A=np.zeros((3, 3)), L0=np.asarray(L, dtype=np.float64),
+                    M=M_IDENTITY.copy(), T=1.0, t=0.0, q=np.ascontiguousarray(q), kind=kind, rc=rc)
+
+
+def random_sl3z(rng: np.random.Generator, steps: int = 6) -> np.ndarray:
+    """A random unimodular integer matrix built from elementary row operations."""
+    M = np.eye(3, dtype=np.int64)
+    for _ in range(steps):
+        a, b = rng.choice(3, size=2, replace=False)
+        c = int(rng.choice([-1, 1]))
+        E = np.eye(3, dtype=np.int64)
+        E[a, b] = c
+        M = M @ E
+    return M
+
+
+def small_random_box(rng: np.random.Generator, n: int, rc: float, hmin: float = 1.0,
+                     hmax: float = 3.5):
+    """A random skewed triclinic box whose heights lie in [hmin*rc, hmax*rc], plus points.
+
+    Used for brute-force pair-set checks on tiny inputs, including boxes with
+    one or two cells per direction.
+    """
+    for _ in range(1000):
+        L = rng.normal(size=(3, 3))
+        if np.linalg.det(L) < 0:
+            L[:, 0] = -L[:, 0]
+        Linv = np.linalg.inv(L)
+        h = 1.0 / np.linalg.norm(Linv, axis=1)
+        target = rng.uniform(hmin, hmax, size=3) * rc
+        L = L @ np.diag(target / h)
+        Linv = np.linalg.inv(L)
+        h = 1.0 / np.linalg.norm(Linv, axis=1)
+        if np.all(h >= hmin * rc * 1.0001):
+            s = rng.random((n, 3))
+            q = (L @ s.T).T + rng.normal(0, 0.5, size=(n, 3))
+            return L, np.ascontiguousarray(q)
+    raise RuntimeError("could not build a random box")

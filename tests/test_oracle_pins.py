@@ -1,0 +1,342 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a closed
+form, an invariant, a textbook/library routine, brute force on tiny inputs, or
+a value the paper prints (tests/golden/paper_constants.json).
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import oracle
+from paper_1412_3784_gb300 import workloads as W
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")))
+
+
+# --------------------------------------------------------------------------
+# Lattice evolution (Sec. 2.1, 2.2)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("M", [W.M_PLANAR, W.M_GENERAL])
+def test_kr_identity(M):
+    """exp(A T) L0 = L0 M (Eq. kr) for the symmetric-eigen flows."""
+    A, _, _ = W.kr_flow(M)
+    L0 = 33.59 * np.eye(3)
+    assert oracle.kr_residual(A, L0, M, 1.0) < 1e-14
+    lat = oracle.lattice(A, L0, 1.0, 1.0 - 1e-15)
+    assert np.abs(lat["L"] - L0 @ M).max() / 33.59 < 1e-13
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_expm_against_scipy(seed):
+    """Both expm paths (Jacobi for symmetric A, Pade otherwise) against scipy's expm."""
+    rng = np.random.default_rng(seed)
+    B = rng.normal(size=(3, 3))
+    # non-normal matrices amplify rounding in any expm: 1e-12 relative there
+    for A, tol in ((B + B.T, 1e-13), (B, 1e-12)):
+        for tau in (0.0, 0.3, 1.7):
+            E = oracle.expm(A, tau)
+            ref = scipy.linalg.expm(tau * A)
+            assert np.abs(E - ref).max() <= tol * max(1.0, np.abs(ref).max())
+
+
+def test_det_preserved_incompressible():
+    """tr A = 0 gives det L(t) = det L0 (volume preserved by the flow)."""
+    A, _, _ = W.kr_flow(W.M_GENERAL)
+    L0 = 10.0 * np.eye(3)
+    for t in np.linspace(0, 3, 13):
+        lat = oracle.lattice(A, L0, 1.0, t)
+        assert abs(lat["V"] - 1000.0) < 1e-10
+
+
+def test_remap_period():
+    """L(t) repeats with period T: the remap by M^-1 at each period (reading c1)."""
+    A, _, _ = W.kr_flow(W.M_PLANAR)
+    L0 = 20.0 * np.eye(3)
+    a = oracle.lattice(A, L0, 1.0, 0.3)["L"]
+    b = oracle.lattice(A, L0, 1.0, 5.3)["L"]
+    assert np.abs(a - b).max() < 1e-12
+
+
+def test_lees_edwards_closed_form_and_angle():
+    """Shear: L_t = [[a, a eps t, 0],[0,a,0],[0,0,a]] and the 26.57 deg angle at half spacing."""
+    a, eps = 7.0, 0.5
+    A = np.array([[0, eps, 0], [0, 0, 0], [0, 0, 0]], dtype=float)
+    L0 = a * np.eye(3)
+    t = 1.0 / (2.0 * eps)   # sheared half a lattice spacing
+    lat = oracle.lattice(A, L0, 0.0, t)
+    ref = np.array([[a, a * eps * t, 0], [0, a, 0], [0, 0, a]])
+    assert np.abs(lat["L"] - ref).max() < 1e-13
+    v1, v2 = lat["L"][:, 0], lat["L"][:, 1]
+    ang = math.degrees(math.acos(v1 @ v2 / np.linalg.norm(v1) / np.linalg.norm(v2)))
+    g = GOLDEN["lees_edwards_max_angle_deg"]
+    assert round(90.0 - ang, g["digits"]) == g["value"]
+    # KR condition of the shear remap matrix of Sec. 2.2 at t* = 1/eps
+    Msh = np.array([[1, 1, 0], [0, 1, 0], [0, 0, 1]], dtype=np.int64)
+    assert oracle.kr_residual(A, L0, Msh, 1.0 / eps) < 1e-14
+
+
+# --------------------------------------------------------------------------
+# Box geometry (Sec. 4.1 heights, Sec. 4.2 QR)
+# --------------------------------------------------------------------------
+
+def test_heights_closed_forms():
+    h = oracle.heights(np.diag([3.0, 4.0, 5.0]))
+    assert np.allclose(h, [3, 4, 5], rtol=0, atol=1e-14)
+    a, g = 2.0, 0.75
+    h = oracle.heights(np.array([[a, a * g, 0], [0, a, 0], [0, 0, a]]))
+    assert np.allclose(h, [a / math.sqrt(1 + g * g), a, a], rtol=1e-15)
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        L = rng.normal(size=(3, 3))
+        # height = 1 / |row of L^-1| (distance between lattice planes)
+        ref = 1.0 / np.linalg.norm(np.linalg.inv(L), axis=1)
+        assert np.allclose(oracle.heights(L), ref, rtol=1e-12)
+
+
+def test_qr():
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        L = rng.normal(size=(3, 3))
+        Q, R = oracle.qr(L)
+        assert np.allclose(Q @ R, L, atol=1e-13)
+        assert np.allclose(Q.T @ Q, np.eye(3), atol=1e-13)
+        assert np.all(np.diag(R) > 0) and R[1, 0] == R[2, 0] == R[2, 1] == 0
+        q2, r2 = np.linalg.qr(L)
+        sgn = np.sign(np.diag(r2))
+        assert np.allclose(R, sgn[:, None] * r2, atol=1e-12)
+        assert abs(np.prod(np.diag(R)) - abs(np.linalg.det(L))) < 1e-12 * abs(np.linalg.det(L)) + 1e-14
+
+
+def test_wrap_lattice_translation():
+    """s in [0,1) and q' - q is a lattice vector."""
+    rng = np.random.default_rng(2)
+    L = rng.normal(size=(3, 3)) * 5
+    Linv = np.linalg.inv(L)
+    q = rng.normal(size=(1000, 3)) * 30
+    s, qp = oracle.wrap(L, Linv, q)
+    assert np.all(s >= 0) and np.all(s < 1)
+    n = np.linalg.solve(L, (qp - q).T).T
+    assert np.abs(n - np.round(n)).max() < 1e-9
+    # boundary: a point exactly on a lattice plane wraps to s = 0
+    s0, _ = oracle.wrap(np.eye(3), np.eye(3), np.array([[1.0, -0.0, 2.0], [-1e-18, 0.5, 0.5]]))
+    assert np.all(s0[0] == 0) and s0[1, 0] == 0.0
+
+
+# --------------------------------------------------------------------------
+# Pair sets: brute force, both cell lists, and an independent enumeration
+# --------------------------------------------------------------------------
+
+def _numpy_pairs(L, qp, rc, nmax=3):
+    """Independent enumeration: every pair, every image in [-nmax, nmax]^3, vectorised."""
+    n = qp.shape[0]
+    imgs = np.array(list(itertools.product(range(-nmax, nmax + 1), repeat=3)), dtype=np.int64)
+    out = []
+    for i in range(n):
+        d = (qp[None, :, :] - qp[i][None, None, :]) + (imgs @ L.T)[:, None, :]
+        r2 = np.einsum("kja,kja->kj", d, d)
+        k, j = np.nonzero(r2 < rc * rc)
+        for kk, jj in zip(k, j):
+            nn = imgs[kk]
+            if jj < i or (jj == i and tuple(nn) <= (0, 0, 0)):
+                continue
+            out.append((i, jj, *nn))
+    return np.array(out, dtype=np.int64).reshape(-1, 5)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_pair_sets_tiny_boxes(seed):
+    """Brute force == DS == DO on small skewed boxes with 1-3 cells per direction."""
+    rng = np.random.default_rng(100 + seed)
+    rc = 1.3
+    L, q = W.small_random_box(rng, 40, rc, 1.0, 3.2)
+    lat_L = L
+    Linv = np.linalg.inv(L)
+    s, qp = oracle.wrap(lat_L, Linv, q)
+    rb = oracle.brute(lat_L, s, qp, rc)
+    kb = oracle.canonical_pair_keys(rb.pairs)
+    ref = oracle.canonical_pair_keys(_numpy_pairs(lat_L, qp, rc))
+    assert np.array_equal(kb, ref)
+    for kfac in (1, 2):
+        rd = oracle.cells_ds(lat_L, s, qp, rc, kfac)
+        ro = oracle.cells_do(lat_L, s, qp, rc, kfac)
+        assert np.array_equal(oracle.canonical_pair_keys(rd.pairs), kb)
+        assert np.array_equal(oracle.canonical_pair_keys(ro.pairs), kb)
+        assert abs(rd.U - rb.U) <= 1e-10 * max(1, abs(rb.U))
+        assert np.abs(ro.F - rb.F).max() <= 1e-9 * max(1, np.abs(rb.F).max())
+
+
+def test_pair_sets_config0_and_strained():
+    for w in (W.config_equilibrium_wca(), W.config_planar(40, k=6),
+              W.config_general(t=W.NEAR_REMAP_T, k=6)):
+        rb = oracle.evaluate(w, "brute", want_pairs=True)
+        kb = oracle.canonical_pair_keys(rb.pairs)
+        for m in ("ds", "do"):
+            r = oracle.evaluate(w, m, want_pairs=True)
+            assert np.array_equal(oracle.canonical_pair_keys(r.pairs), kb), (w.name, m)
+
+
+# --------------------------------------------------------------------------
+# Forces, energy, virial
+# --------------------------------------------------------------------------
+
+def test_two_particle_closed_form():
+    L = 20.0 * np.eye(3)
+    r = 1.3
+    q = np.array([[1.0, 1.0, 1.0], [1.0 + r, 1.0, 1.0]])
+    s, qp = oracle.wrap(L, np.linalg.inv(L), q)
+    for rc, shift in ((2.5, 1), (2.5, 0), (2 ** (1 / 6), 1)):
+        res = oracle.brute(L, s, qp, rc, 1.0, 1.0, shift)
+        if r >= rc:
+            assert res.npairs == 0
+            continue
+        u = 4 * (r ** -12 - r ** -6) - (4 * (rc ** -12 - rc ** -6) if shift else 0.0)
+        du = -48 * r ** -13 + 24 * r ** -7   # du/dr
+        assert abs(res.U - u) < 1e-13
+        assert abs(res.F[1, 0] - (-du)) < 1e-12 and abs(res.F[0, 0] - du) < 1e-12
+        assert abs(res.W[0, 0] - (-du * r)) < 1e-12
+    # sigma and eps scaling
+    res = oracle.brute(L, s, qp, 2.5 * 1.1, 2.0, 1.1, 0)
+    x = 1.1 / r
+    assert abs(res.U - 8 * (x ** 12 - x ** 6)) < 1e-12
+
+
+def test_perfect_fcc_zero_force():
+    """Inversion symmetry: an unperturbed FCC crystal at rest has zero force on every site."""
+    k = 6
+    s = W.fcc_fractional(k)
+    side = (4 * k ** 3 / W.RHO_DEFAULT) ** (1 / 3)
+    L = side * np.eye(3)
+    q = s @ L.T
+    ss, qp = oracle.wrap(L, np.linalg.inv(L), q)
+    for m in ("ds", "do"):
+        fn = oracle.cells_ds if m == "ds" else oracle.cells_do
+        res = fn(L, ss, qp, 2.5, want_pairs=False)
+        assert np.abs(res.F).max() < 1e-10
+        # FCC shells at a sqrt(m/2), a = 1.6796: m = 1..4 lie inside 2.5 with
+        # 12 + 6 + 24 + 12 = 54 neighbours, m = 5 (2.656) lies outside
+        assert res.npairs == len(s) * 54 // 2
+
+
+def test_newton_third_law_and_virial_symmetry():
+    w = W.config_planar(17, k=6)
+    r = oracle.evaluate(w, "do")
+    assert np.abs(r.F.sum(0)).max() < 1e-9 * np.abs(r.F).max()
+    assert np.abs(r.W - r.W.T).max() < 1e-12 * np.abs(r.W).max()
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_invariance_under_basis_change(seed):
+    """The lattice generated by L M' equals that of L (Sec. 2.2): forces, energy,
+    virial and the pair count are unchanged by a change of basis M' in SL(3,Z)."""
+    rng = np.random.default_rng(seed)
+    w = W.config_planar(11, k=5)
+    r0 = oracle.evaluate(w, "brute")
+    L = r0.lattice["L"]
+    Mp = W.random_sl3z(rng, steps=3)
+    L2 = L @ Mp.astype(float)
+    s2, qp2 = oracle.wrap(L2, np.linalg.inv(L2), w.q)
+    r2 = oracle.brute(L2, s2, qp2, w.rc, want_pairs=False)
+    assert r2.npairs == r0.npairs
+    assert abs(r2.U - r0.U) <= 1e-10 * abs(r0.U)
+    assert np.abs(r2.W - r0.W).max() <= 1e-10 * np.abs(r0.W).max()
+    assert np.abs(r2.F - r0.F).max() <= 1e-9 * np.abs(r0.F).max()
+
+
+def test_nve_energy_conservation():
+    """Velocity Verlet at A = 0 with oracle forces conserves energy (WCA, N = 256)."""
+    k = 4
+    rng = np.random.default_rng(7)
+    s = W.fcc_fractional(k)
+    side = (len(s) / 0.8442) ** (1 / 3)
+    L = side * np.eye(3)
+    Linv = np.linalg.inv(L)
+    q = s @ L.T + rng.normal(0, 0.02, size=s.shape)
+    v = rng.normal(0, 1.0, size=s.shape)
+    v -= v.mean(0)
+    rc = 2 ** (1 / 6)
+    dt = 0.002
+
+    def force(q):
+        ss, qp = oracle.wrap(L, Linv, q)
+        r = oracle.cells_ds(L, ss, qp, rc, want_pairs=False)
+        return r.F, r.U
+
+    F, U = force(q)
+    E0 = U + 0.5 * (v * v).sum()
+    for _ in range(1000):
+        v += 0.5 * dt * F
+        q += dt * v
+        F, U = force(q)
+        v += 0.5 * dt * F
+    E1 = U + 0.5 * (v * v).sum()
+    assert abs(E1 - E0) / abs(E0) < 1e-4
+
+
+# --------------------------------------------------------------------------
+# Cell counts and neighbourhoods (Sec. 4.1, 4.2, 5.1, 5.2)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("M", [W.M_PLANAR, W.M_GENERAL])
+def test_cell_counts_and_face_widths_over_a_period(M):
+    A, _, _ = W.kr_flow(M)
+    L0 = 67.18 * np.eye(3)
+    rc = 2.5
+    for t in np.concatenate([np.linspace(0, 1, 65)[:-1], [W.NEAR_REMAP_T]]):
+        lat = oracle.lattice(A, L0, 1.0, t)
+        c = oracle.ds_counts(lat["L"], rc)
+        assert np.array_equal(c, np.floor(lat["h"] / rc).astype(np.int64))
+        assert np.all(lat["h"] / c >= rc)
+        l = oracle.do_counts(lat["R"], rc)
+        assert np.array_equal(l, np.floor(np.diag(lat["R"]) / rc).astype(np.int64))
+        assert np.all(np.diag(lat["R"]) / l >= rc)
+        assert abs(np.prod(np.diag(lat["R"])) - lat["V"]) < 1e-9 * lat["V"]
+
+
+@pytest.mark.parametrize("l2,l3", [(2, 2), (3, 5), (7, 4), (10, 10), (31, 6)])
+def test_do_fixed_rule_average(l2, l3):
+    """The four cases (27/30/34/36) average to 27 + 14/l3 + 6/l2 - 4/(l2 l3) (Sec. 5.2)."""
+    l = np.array([5, l2, l3])
+    counts = [oracle.do_fixed_count(l, iy, iz) for iz in range(l3) for iy in range(l2)]
+    assert set(counts) <= set(GOLDEN["do_case_cell_counts"]["value"])
+    avg = sum(counts) / len(counts)
+    assert abs(avg - (27 + 14 / l3 + 6 / l2 - 4 / (l2 * l3))) < 1e-12
+
+
+def test_do_tight_rule_within_fixed_rule():
+    """The computed dynamic offset neighbourhood never exceeds the paper's case sizes,
+    and is exactly 27 cells in an undeformed box."""
+    A, _, _ = W.kr_flow(W.M_GENERAL)
+    L0 = 40.0 * np.eye(3)
+    for t in (0.0, 0.2, 0.5, 0.77, W.NEAR_REMAP_T):
+        lat = oracle.lattice(A, L0, 1.0, t)
+        l, rows = oracle.do_stencil(lat["R"], 2.5)
+        per = {}
+        for iy, iz, jyu, jzu, lo, hi in rows:
+            per[(iy, iz)] = per.get((iy, iz), 0) + (hi - lo + 1)
+        for (iy, iz), cnt in per.items():
+            assert cnt <= oracle.do_fixed_count(l, iy, iz)
+        if t == 0.0:
+            assert set(per.values()) == {27}
+
+
+def test_search_efficiency_equilibrium():
+    """Uniform random points with sides divisible by d_cut: interacting / candidate
+    pairs -> (4 pi / 3) / 27 = 0.1551 (Sec. 5)."""
+    rc = 1.0
+    side = 8 * rc * (1 + 1e-9)
+    w = W.uniform_random(6000, side * np.eye(3), seed=5, rc=rc)
+    r = oracle.evaluate(w, "ds")
+    eta = 2 * r.npairs / r.ncand
+    g = GOLDEN["equilibrium_search_efficiency"]
+    assert round((4 * math.pi / 3) / 27, g["digits"]) == g["value"]
+    sigma = math.sqrt(g["value"] * (1 - g["value"]) / r.ncand) * 3 + 2e-3
+    assert abs(eta - g["value"]) < sigma
+    ro = oracle.evaluate(w, "do")
+    assert ro.ncand == r.ncand and ro.npairs == r.npairs
