@@ -1,0 +1,189 @@
+/*
+ * nemd.h -- C ABI of the GB300 cell-list force evaluation for homogeneous
+ * linear flows under Kraynik-Reinelt periodic boundary conditions.
+ *
+ * Paper: M. Dobson, I. Fox, A. Saracino, "Cell List Algorithms for
+ * Nonequilibrium Molecular Dynamics", arXiv:1412.3784.
+ *
+ * One force evaluation is the call sequence
+ *     nemd_set_state(q, t)  ->  nemd_build_cells(variant, rc)  ->  nemd_compute_forces(F, U, W)
+ * after a one-time nemd_set_flow(A, L0, M, T) and nemd_set_potential(...).
+ * Every step runs as CUDA kernels on the context's stream:
+ *   set_state      lattice L(t) = exp(A (t mod T)) L0, its inverse, heights, QR  (Sec. 2.1, 2.2)
+ *   build_cells    cell grid and neighbour stencil from the deformed metric,
+ *                  fractional wrap and counting-sort binning in cell order       (Sec. 4.1, 4.2)
+ *   compute_forces cell-pair LJ/WCA force, energy and virial                     (Sec. 3, 5)
+ *
+ * Conventions
+ *   - Matrices are 3x3 row-major.  The COLUMNS of L0 (and of L) are the lattice
+ *     vectors v1, v2, v3 (Sec. 2: L = [v1 v2 v3]).
+ *   - Positions q are N x 3 float64, Cartesian, any periodic image.
+ *   - Pointers may be host or device memory; the library inspects each pointer
+ *     (cudaPointerGetAttributes).  Device pointers are used in place and are
+ *     read/written asynchronously on the stream.  Host pointers are copied
+ *     through library-owned device buffers; a call that writes host outputs
+ *     synchronises the stream before it returns.
+ *   - The library owns all scratch memory and grows it on demand.  The caller
+ *     owns every pointer it passes in; the library never frees them.
+ *   - Errors are returned as a nemd_status value (0 = OK).  Errors detected on
+ *     the device (a box too small for the cut-off, non-finite coordinates, a
+ *     wait that timed out) are deferred: they are returned by nemd_sync() and by
+ *     the next call that synchronises.  nemd_last_error() gives a message.
+ *   - A context is used by one host thread at a time.
+ */
+#ifndef NEMD_H
+#define NEMD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nemd_ctx nemd_ctx;
+
+typedef enum nemd_status {
+    NEMD_OK = 0,
+    NEMD_ERR_ARG = 1,            /* null pointer, N < 0, bad enum value, rc <= 0 ...      */
+    NEMD_ERR_NOT_SL3Z = 2,       /* M is not an integer matrix with det M = 1 (Sec. 2.2) */
+    NEMD_ERR_NOT_KR = 3,         /* |exp(T A) L0 - L0 M| > 1e-9 |L0| (Eq. kr)           */
+    NEMD_ERR_TRACE = 4,          /* |tr A| > 1e-12 |A|: the flow must be incompressible  */
+    NEMD_ERR_BOX_TOO_SMALL = 5,  /* a cell count c_i or l_i is 0: face width < rc        */
+    NEMD_ERR_ORDER = 6,          /* calls out of order (e.g. forces before build_cells)  */
+    NEMD_ERR_CUDA = 7,           /* a CUDA runtime call failed                           */
+    NEMD_ERR_NONFINITE = 8,      /* NaN or Inf in the positions                          */
+    NEMD_ERR_TIMEOUT = 9,        /* a bounded device wait ran out                        */
+    NEMD_ERR_CAPACITY = 10,      /* a device table outgrew its bound                     */
+    NEMD_ERR_NOMEM = 11,         /* device or host allocation failed                     */
+    NEMD_ERR_UNSUPPORTED = 12    /* option or mode not available                         */
+} nemd_status;
+
+typedef enum nemd_variant {
+    NEMD_DS = 0,              /* dynamic size cell list, Sec. 4.1                          */
+    NEMD_DO = 1,              /* dynamic offset cell list, Sec. 4.2                        */
+    NEMD_AUTO_HEURISTIC = 2,  /* per step, the variant with the smaller neighbourhood
+                                 volume V_DS = 27 V / (c1 c2 c3) versus
+                                 V_DO = avg r11 r22 r33 / (l1 l2 l3)  (Sec. 5.1, 5.2)     */
+    NEMD_AUTO_LEARNED = 3     /* per step, the choice of a trained cost model
+                                 (nemd_model_load); falls back to the heuristic         */
+} nemd_variant;
+
+typedef enum nemd_potential {
+    NEMD_LJ = 0,   /* 4 eps [(sigma/r)^12 - (sigma/r)^6], optionally shifted to 0 at rc   */
+    NEMD_WCA = 1   /* the same with rc = 2^(1/6) sigma and the shift on (Sec. 5 runtime)   */
+} nemd_potential;
+
+typedef enum nemd_option {
+    NEMD_OPT_PRECISE = 1,       /* 1: accepted pairs are re-evaluated in float64 (energy
+                                   and virial to ~1e-13); 0 (default): float32 pair math */
+    NEMD_OPT_RECORD_PAIRS = 2,  /* > 0: capacity of the pair record (verification mode)   */
+    NEMD_OPT_KERNEL = 3,        /* force kernel: 0 plain (one thread per particle),
+                                   1 tiled (one warp per home cell)                        */
+    NEMD_OPT_CELL_FACTOR = 4,   /* k >= 1: cells at least rc/k wide, stencil reach k    */
+    NEMD_OPT_BLOCK = 5,         /* threads per block of the force kernel (multiple of 32) */
+    NEMD_OPT_TIMING = 6         /* 1: record CUDA events around every force-kernel launch
+                                   (read with nemd_get_kernel_time)                       */
+} nemd_option;
+
+/* Statistics of the last force evaluation (read with nemd_get_stats). */
+typedef struct nemd_stats {
+    int64_t n;              /* particles                                              */
+    int64_t pairs;          /* interacting unordered pairs (r < rc)                   */
+    int64_t candidates;     /* ordered candidate pairs tested (full neighbourhoods)   */
+    int64_t ncells;         /* cells in the grid                                      */
+    int32_t counts[3];      /* c_i (dynamic size) or l_i (dynamic offset)             */
+    int32_t variant;        /* variant actually used (NEMD_DS or NEMD_DO)             */
+    int32_t cell_factor;    /* k                                                      */
+    int32_t max_rows;       /* row stride of the stencil table                        */
+    int64_t stencil_cells;  /* sum over home cells of neighbourhood cells             */
+    int64_t rechecks;       /* candidates decided by the float64 guard-band test      */
+    double tau;             /* t mod T                                                */
+    double band;            /* float32 guard band on r^2 (absolute)                   */
+    int64_t launches;       /* kernels this context has launched since creation       */
+} nemd_stats;
+
+/* Create a context on CUDA device `device`, issuing all work on `stream`
+ * (a cudaStream_t; NULL means the legacy default stream).  *ctx receives the
+ * handle.  Returns NEMD_ERR_CUDA if the device cannot be used. */
+int nemd_create(nemd_ctx **ctx, int device, void *stream);
+
+/* Release all library-owned memory.  Safe on NULL. */
+int nemd_destroy(nemd_ctx *ctx);
+
+/* Set the flow (Sec. 2.1: u(x) = A x, dL/dt = A L) and the Kraynik-Reinelt
+ * remap (Sec. 2.2, Eq. kr: exp(A T) L0 = L0 M, M in SL(3,Z)).  A, L0: 9
+ * float64 each; M: 9 int64; T > 0 the period (ignored, and M must be the
+ * identity, when A = 0).  Validated on the device before returning (this call
+ * synchronises): NEMD_ERR_NOT_SL3Z, NEMD_ERR_TRACE, NEMD_ERR_NOT_KR. */
+int nemd_set_flow(nemd_ctx *ctx, const double A[9], const double L0[9], const int64_t M[9], double T);
+
+/* Pair potential (Sec. 5: WCA in the paper's runtime test; LJ otherwise).
+ * kind: nemd_potential; eps, sigma > 0; shift != 0 subtracts u(rc).  For
+ * NEMD_WCA the cut-off passed to nemd_build_cells must be 2^(1/6) sigma. */
+int nemd_set_potential(nemd_ctx *ctx, int kind, double eps, double sigma, int shift);
+
+/* Positions and time.  q: N x 3 float64 (host or device), any image; t: time.
+ * Launches the lattice evolution L(t) = exp(A (t mod T)) L0, i.e. the remap
+ * L <- L M^-1 applied at every period (Sec. 2.2).  A device q must stay valid
+ * and unchanged until the next nemd_compute_forces has completed. */
+int nemd_set_state(nemd_ctx *ctx, const double *q, int64_t n, double t);
+
+/* Cell grid, stencil and binning for cut-off rc > 0 (Sec. 3, 4).
+ *   NEMD_DS: c_i = floor(h_i / rc) cells congruent to the box, 27 cells (Sec. 4.1);
+ *   NEMD_DO: rectangular cells l_i = floor(r_ii / rc) in the QR frame of the box,
+ *            with neighbourhoods expanded across offset faces (Sec. 4.2);
+ *   NEMD_AUTO_*: chosen per step on the device (see nemd_variant).
+ * The counts carry a relative safety margin of 1e-12 (floor((1-1e-12) h/rc)).
+ * A zero count is reported (deferred) as NEMD_ERR_BOX_TOO_SMALL. */
+int nemd_build_cells(nemd_ctx *ctx, int variant, double rc);
+
+/* Forces, energy and virial of the current state (Sec. 3, 5).
+ *   F: N x 3 float32 in input order, F_i = sum_j -u'(r_ij) (q_i - q_j - L n)/r_ij;
+ *   U: 1 float64, sum over unordered pairs of u(r);
+ *   W: 9 float64 row-major, sum over unordered pairs of r_ij (x) f_ij with
+ *      r_ij = q_i - (q_j + L n) and f_ij the force on i from j.
+ * Any of F, U, W may be NULL to skip it. */
+int nemd_compute_forces(nemd_ctx *ctx, float *F, double *U, double *W);
+
+/* Wait for the stream and return any deferred device error. */
+int nemd_sync(nemd_ctx *ctx);
+
+/* Message of the last error of this context (never NULL). */
+const char *nemd_last_error(const nemd_ctx *ctx);
+
+/* Set an option (nemd_option).  Takes effect at the next nemd_build_cells. */
+int nemd_set_option(nemd_ctx *ctx, int key, int64_t value);
+
+/* Copy the current lattice to host memory (synchronises).  out[48]:
+ * L(9) Linv(9) V h(3) Q(9) R(9) tau band(ignored) counts(3, as doubles) ncells variant
+ * -- see nemd.py for the exact unpacking. */
+int nemd_get_lattice(nemd_ctx *ctx, double *out);
+
+/* Statistics of the last evaluation (synchronises). */
+int nemd_get_stats(nemd_ctx *ctx, nemd_stats *out);
+
+/* Verification mode (NEMD_OPT_RECORD_PAIRS > 0): copy the recorded unordered
+ * pairs as int32 quintuples (i, j, n1, n2, n3) with i < j, or i == j and n
+ * lexicographically positive, to host memory `out` (capacity `cap` pairs);
+ * *count receives the number of pairs found (which may exceed cap or the
+ * record capacity: then the record is incomplete and NEMD_ERR_CAPACITY is
+ * returned).  Synchronises. */
+int nemd_get_pairs(nemd_ctx *ctx, int32_t *out, int64_t cap, int64_t *count);
+
+/* With NEMD_OPT_TIMING on: total device time (ms) of the force-kernel launches
+ * recorded since the last call and their number; resets the record.  Events
+ * are recorded on the context's stream, at most 4096 launches are kept.
+ * Synchronises. */
+int nemd_get_kernel_time(nemd_ctx *ctx, double *ms_total, int64_t *nlaunch);
+
+/* Measure device peaks with the library's own kernels (synchronises):
+ * out[0] FP32 FMA lane-ops/s, out[1] FP32 paired (f32x2) lane-ops/s,
+ * out[2] FP64 FMA ops/s, out[3] copy bandwidth bytes/s, out[4] SM count,
+ * out[5] SM clock kHz reported by the device. */
+int nemd_measure_peaks(int device, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NEMD_H */

@@ -53,6 +53,9 @@ def lib():
         L.orc_do_fixed_count.restype = ctypes.c_int64
         L.orc_do_total_stencil_cells.argtypes = [_dp, ctypes.c_double, ctypes.c_int]
         L.orc_do_total_stencil_cells.restype = ctypes.c_int64
+        L.orc_sample_forces.argtypes = [_dp, ctypes.c_int64, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_int, _i64p, ctypes.c_int64, _dp, _i64p, _dp]
+        L.orc_sample_forces.restype = None
         _lib = L
     return _lib
 
@@ -153,6 +156,20 @@ def do_fixed_count(l, iy, iz):
 def do_total_stencil_cells(R, rc, kfac=1):
     R, pR = _d(R)
     return int(lib().orc_do_total_stencil_cells(pR, float(rc), int(kfac)))
+
+
+def sample_forces(L, s, qp, idx, rc, eps=1.0, sigma=1.0, shift=1):
+    """Brute-force forces (and per-particle neighbour counts, half energies) on sampled particles."""
+    L, pL = _d(L)
+    s, ps = _d(s)
+    qp, pq = _d(qp)
+    idx, pi = _i64(idx)
+    F = np.zeros((len(idx), 3))
+    cnt = np.zeros(len(idx), dtype=np.int64)
+    uh = np.zeros(len(idx))
+    lib().orc_sample_forces(pL, s.shape[0], ps, pq, float(rc), float(eps), float(sigma), int(shift), pi,
+                            len(idx), F.ctypes.data_as(_dp), cnt.ctypes.data_as(_i64p), uh.ctypes.data_as(_dp))
+    return F, cnt, uh
 
 
 class Result:

@@ -772,3 +772,54 @@ int64_t orc_do_total_stencil_cells(const double *R, double rc, int kfac)
         }
     return total;
 }
+
+/* Forces on a sample of particles by brute force over every partner and image:
+ * for each sampled i, F_i = sum over (j, n) with r < rc of -fr d, and the number
+ * of such (j, n).  Lets full-size runs be checked particle by particle. */
+void orc_sample_forces(const double *L, int64_t n, const double *s, const double *qp, double rc, double eps,
+                       double sigma, int shift, const int64_t *idx, int64_t nidx, double *F, int64_t *cnt,
+                       double *U_half)
+{
+    (void)shift;
+    double h[3];
+    orc_heights(L, h);
+    double rc2 = rc * rc;
+    double ushift = 0.0;
+    if (shift) {
+        double sr2 = (sigma * sigma) / (rc * rc);
+        double sr6 = sr2 * sr2 * sr2;
+        ushift = 4.0 * eps * (sr6 * sr6 - sr6);
+    }
+    for (int64_t t = 0; t < nidx; t++) {
+        int64_t i = idx[t];
+        double f[3] = {0, 0, 0}, u = 0.0;
+        int64_t c = 0;
+        for (int64_t j = 0; j < n; j++) {
+            int lo[3], hi[3];
+            for (int a = 0; a < 3; a++) {
+                double ds = s[3 * j + a] - s[3 * i + a];
+                double reach = rc / h[a] + 1e-9;
+                lo[a] = (int)ceil(-ds - reach);
+                hi[a] = (int)floor(-ds + reach);
+            }
+            for (int n1 = lo[0]; n1 <= hi[0]; n1++)
+                for (int n2 = lo[1]; n2 <= hi[1]; n2++)
+                    for (int n3 = lo[2]; n3 <= hi[2]; n3++) {
+                        if (j == i && n1 == 0 && n2 == 0 && n3 == 0) continue;
+                        double d[3];
+                        double r2 = canon_r2(qp + 3 * i, qp + 3 * j, L, n1, n2, n3, d);
+                        if (!(r2 < rc2)) continue;
+                        double r2inv = 1.0 / r2;
+                        double sr2 = (sigma * sigma) * r2inv;
+                        double sr6 = sr2 * sr2 * sr2;
+                        double fr = 24.0 * eps * r2inv * sr6 * (2.0 * sr6 - 1.0);
+                        u += 0.5 * (4.0 * eps * (sr6 * sr6 - sr6) - ushift);
+                        for (int a = 0; a < 3; a++) f[a] -= fr * d[a];
+                        c++;
+                    }
+        }
+        for (int a = 0; a < 3; a++) F[3 * t + a] = f[a];
+        cnt[t] = c;
+        if (U_half) U_half[t] = u;
+    }
+}

@@ -1,0 +1,212 @@
+// bin.cu -- fractional wrap into the unit cell (Sec. 2: the box is the unit cell
+// Omega of the lattice) and counting-sort binning of particles in cell order
+// (Sec. 3: "each particle is assigned to a cell based off of its position";
+// Sec. 4.1: "convert particle positions to the underlying lattice basis";
+// Sec. 4.2: rectangular rearrangement of the rotated box).
+//
+// Pipeline (all O(N), HBM-bound):
+//   k_wrap      s = frac(L^-1 q) (FP64), cell index, float32 cell-relative
+//               position in the variant's frame, rank = atomicAdd(count[cell])
+//   k_scan_*    exclusive scan of the per-cell counts -> start[]
+//   k_scatter   perm[start[cell] + rank] = i
+//   k_cellsort  per cell, particles in increasing input index (stable order,
+//               so sums are reproducible from run to run)
+//   k_pack      sorted float4 {rel position, input index} and sorted cell ids
+#include <math.h>
+
+#include "nemd_device.cuh"
+#include "nemd_internal.cuh"
+
+namespace nemd {
+
+__global__ void k_wrap(Geo *g, const double *__restrict__ q, int n, float4 *__restrict__ relc,
+                       int *__restrict__ rank, int *__restrict__ count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
+  double x = q[3 * (size_t)i], y = q[3 * (size_t)i + 1], z = q[3 * (size_t)i + 2];
+  if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
+    atomicOr(&g->error, ERRB_NONFINITE);
+    x = y = z = 0.0;
+  }
+  double s[3];
+  frac_wrap(g->Linv, x, y, z, s);
+  const int l1 = g->nc[0], l2 = g->nc[1], l3 = g->nc[2];
+  int idx[3];
+  float rel[3];
+  if (g->variant == NEMD_DS) {
+    float u[3];
+    for (int a = 0; a < 3; a++) {
+      double v = s[a] * g->Ginv_scale[a];
+      int k = (int)floor(v);
+      k = min(max(k, 0), g->nc[a] - 1);
+      idx[a] = k;
+      u[a] = (float)(v - (double)k);
+    }
+    for (int a = 0; a < 3; a++)
+      rel[a] = fmaf(g->Gf[3 * a + 2], u[2], fmaf(g->Gf[3 * a + 1], u[1], g->Gf[3 * a] * u[0]));
+  } else {
+    double b[3];
+    int m[3];
+    brick_wrap(g->R, s, b, m);
+    for (int a = 0; a < 3; a++) {
+      int k = (int)floor(b[a] * g->Ginv_scale[a]);
+      k = min(max(k, 0), g->nc[a] - 1);
+      idx[a] = k;
+      rel[a] = (float)(b[a] - (double)k * g->w[a]);
+    }
+  }
+  const int cell = idx[0] + l1 * (idx[1] + l2 * idx[2]);
+  (void)l3;
+  relc[i] = make_float4(rel[0], rel[1], rel[2], __int_as_float(cell));
+  rank[i] = atomicAdd(&count[cell], 1);
+}
+
+// ---- exclusive scan of count[0..ncells) into start[0..ncells], start[ncells] = n ----
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int *sh, int &total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int w = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    sh[lane] = w;
+  }
+  __syncthreads();
+  int incl = x + (warp > 0 ? sh[warp - 1] : 0);
+  total = sh[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return incl - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const Geo *g, const int *__restrict__ count,
+                                                             int *__restrict__ start, int *__restrict__ tile_sums) {
+  __shared__ int sh[32];
+  if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
+  const int ncells = g->ncells;
+  const int base = blockIdx.x * kScanTile;
+  if (base >= ncells) return;  // whole block uniform
+  int v[kScanItems];
+  int sum = 0;
+  for (int k = 0; k < kScanItems; k++) {
+    int idx = base + threadIdx.x * kScanItems + k;
+    v[k] = (idx < ncells) ? count[idx] : 0;
+    sum += v[k];
+  }
+  int total;
+  int ex = block_exclusive_scan(sum, sh, total);
+  for (int k = 0; k < kScanItems; k++) {
+    int idx = base + threadIdx.x * kScanItems + k;
+    if (idx < ncells) start[idx] = ex;
+    ex += v[k];
+  }
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(const Geo *g, int *__restrict__ tile_sums) {
+  __shared__ int sh[32];
+  if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
+  const int ntiles = (g->ncells + kScanTile - 1) / kScanTile;
+  int carry = 0;
+  for (int base = 0; base < ntiles; base += kScanThreads) {
+    int idx = base + threadIdx.x;
+    int v = (idx < ntiles) ? tile_sums[idx] : 0;
+    int total;
+    int ex = block_exclusive_scan(v, sh, total);
+    if (idx < ntiles) tile_sums[idx] = ex + carry;
+    carry += total;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_add(const Geo *g, int *__restrict__ start,
+                                                           const int *__restrict__ tile_sums, int n) {
+  if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
+  const int ncells = g->ncells;
+  const int base = blockIdx.x * kScanTile;
+  if (base > ncells) return;
+  const int add = tile_sums[blockIdx.x];
+  for (int k = 0; k < kScanItems; k++) {
+    int idx = base + threadIdx.x * kScanItems + k;
+    if (idx < ncells) start[idx] += add;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) start[ncells] = n;
+}
+
+__global__ void k_scatter(const Geo *g, const float4 *__restrict__ relc, const int *__restrict__ rank,
+                          const int *__restrict__ start, int *__restrict__ perm, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
+  const int cell = __float_as_int(relc[i].w);
+  perm[start[cell] + rank[i]] = i;
+}
+
+__global__ void k_cellsort(const Geo *g, const int *__restrict__ start, int *__restrict__ perm) {
+  if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
+  const int ncells = g->ncells;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
+    const int b = start[c], e = start[c + 1];
+    for (int k = b + 1; k < e; k++) {
+      int v = perm[k];
+      int j = k - 1;
+      while (j >= b && perm[j] > v) {
+        perm[j + 1] = perm[j];
+        j--;
+      }
+      perm[j + 1] = v;
+    }
+  }
+}
+
+__global__ void k_pack(const Geo *g, const float4 *__restrict__ relc, const int *__restrict__ perm,
+                       float4 *__restrict__ pos4, int *__restrict__ cell_sorted, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
+  const int i = perm[k];
+  const float4 r = relc[i];
+  pos4[k] = make_float4(r.x, r.y, r.z, __int_as_float(i));
+  cell_sorted[k] = __float_as_int(r.w);
+}
+
+cudaError_t launch_bin(nemd_ctx *c) {
+  const int n = (int)c->n;
+  cudaError_t e = cudaMemsetAsync(c->count, 0, sizeof(int) * (size_t)(c->cap_cells + 1), c->stream);
+  if (e != cudaSuccess) return e;
+  if (n > 0) {
+    const int tb = 256;
+    const int nb = (n + tb - 1) / tb;
+    k_wrap<<<nb, tb, 0, c->stream>>>(c->geo, c->q_dev, n, c->relc, c->rank, c->count);
+    c->launches += 1;
+  }
+  const int64_t tiles = (c->cap_cells + 1 + kScanTile - 1) / kScanTile;
+  k_scan_tiles<<<(int)tiles, kScanThreads, 0, c->stream>>>(c->geo, c->count, c->start, c->block_sums);
+  k_scan_top<<<1, kScanThreads, 0, c->stream>>>(c->geo, c->block_sums);
+  k_scan_add<<<(int)tiles, kScanThreads, 0, c->stream>>>(c->geo, c->start, c->block_sums, n);
+  c->launches += 3;
+  if (n > 0) {
+    const int tb = 256;
+    const int nb = (n + tb - 1) / tb;
+    k_scatter<<<nb, tb, 0, c->stream>>>(c->geo, c->relc, c->rank, c->start, c->perm, n);
+    int64_t cb = (c->cap_cells + 255) / 256;
+    if (cb > 8 * (int64_t)c->sms) cb = 8 * (int64_t)c->sms;
+    k_cellsort<<<(int)cb, 256, 0, c->stream>>>(c->geo, c->start, c->perm);
+    k_pack<<<nb, tb, 0, c->stream>>>(c->geo, c->relc, c->perm, c->pos4, c->cell_sorted, n);
+    c->launches += 3;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace nemd

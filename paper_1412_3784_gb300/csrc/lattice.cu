@@ -1,0 +1,393 @@
+// lattice.cu -- lattice evolution and remap (Sec. 2.1, 2.2), cell grid (Sec. 4.1,
+// 4.2, 5.1, 5.2) and neighbour stencil (Sec. 4.1, 4.2) on the device, in FP64.
+//
+//   tau = t - T floor(t / T)                 remap L <- L M^-1 at every period (Eq. kr)
+//   L   = exp(tau A) L0                      (Sec. 2.1, dL/dt = A L)
+//   exp by Taylor series with scaling and squaring, products spread over lanes
+//   L^-1 by the adjugate, V = det L, heights h_i = 1 / |row_i(L^-1)|
+//   QR by Cholesky of L^T L (R upper triangular, r_ii > 0), Q = L R^-1
+//   dynamic size:   c_i = floor((1 - 1e-12) k h_i / rc)     (Sec. 4.1)
+//   dynamic offset: l_i = floor((1 - 1e-12) k r_ii / rc)    (Sec. 5.2)
+#include <math.h>
+
+#include "nemd_internal.cuh"
+
+namespace nemd {
+
+namespace {
+
+__device__ __forceinline__ int floordiv_i(int a, int b) {
+  int q = a / b;
+  if ((a % b != 0) && ((a < 0) != (b < 0))) q--;
+  return q;
+}
+
+// c = a * b for 3x3 row-major matrices in shared memory; lanes 0..8 each
+// produce one entry.  c may alias a or b.
+__device__ __forceinline__ void mm3(const double *a, const double *b, double *c, int lane) {
+  double v = 0.0;
+  if (lane < 9) {
+    int i = lane / 3, j = lane % 3;
+    v = a[3 * i] * b[j] + a[3 * i + 1] * b[3 + j] + a[3 * i + 2] * b[6 + j];
+  }
+  __syncwarp();
+  if (lane < 9) c[lane] = v;
+  __syncwarp();
+}
+
+}  // namespace
+
+// One warp.  validate != 0: compute exp(tau_in A) L0 only (for the KR check).
+__global__ void k_lattice(Geo *g, LatIn in) {
+  const int validate = in.validate;
+  const double tau_in = in.tau;
+  __shared__ double B[9], P[9], E[9], Ls[9], Gm[9], Rm[9], Ri[9], Lt[9];
+  __shared__ int sh_s;
+  const int lane = threadIdx.x;
+
+  double tau;
+  if (validate) {
+    tau = tau_in;
+  } else {
+    const double T = in.T, t = in.t;
+    tau = (T > 0.0) ? t - T * floor(t / T) : t;
+  }
+  if (lane < 9) {
+    g->A[lane] = in.A[lane];
+    g->L0[lane] = in.L0[lane];
+  }
+  if (lane == 0) {
+    g->T = in.T;
+    g->t = in.t;
+    if (!validate) g->error = 0;
+  }
+
+  // scaled argument B = tau A / 2^s with |B|_1 <= 1/8
+  if (lane < 9) B[lane] = tau * in.A[lane];
+  __syncwarp();
+  if (lane == 0) {
+    double nrm = 0.0;
+    for (int j = 0; j < 3; j++) {
+      double cs = fabs(B[j]) + fabs(B[3 + j]) + fabs(B[6 + j]);
+      nrm = fmax(nrm, cs);
+    }
+    int s = 0;
+    if (nrm > 0.125) s = (int)ceil(log2(nrm * 8.0));
+    sh_s = s;
+  }
+  __syncwarp();
+  const int s = sh_s;
+  if (lane < 9) B[lane] = ldexp(B[lane], -s);
+  __syncwarp();
+
+  // Taylor polynomial of degree 12 by Horner: P = I + B/12, P = I + B P / k ...
+  const int deg = 12;
+  if (lane < 9) P[lane] = ((lane % 4) == 0 ? 1.0 : 0.0) + B[lane] / (double)deg;
+  __syncwarp();
+  for (int k = deg - 1; k >= 1; k--) {
+    mm3(B, P, P, lane);
+    if (lane < 9) P[lane] = ((lane % 4) == 0 ? 1.0 : 0.0) + P[lane] / (double)k;
+    __syncwarp();
+  }
+  for (int k = 0; k < s; k++) mm3(P, P, P, lane);
+  if (lane < 9) E[lane] = P[lane];
+  __syncwarp();
+
+  // L = E L0
+  if (lane < 9) Ls[lane] = in.L0[lane];
+  __syncwarp();
+  mm3(E, Ls, Ls, lane);
+
+  if (validate) {
+    if (lane < 9) g->L[lane] = Ls[lane];
+    if (lane == 0) g->tau = tau;
+    return;
+  }
+
+  // inverse by the adjugate
+  __shared__ double cof[9];
+  __shared__ double det_s;
+  if (lane < 9) {
+    const double *a = Ls;
+    double c;
+    switch (lane) {
+      case 0: c = a[4] * a[8] - a[5] * a[7]; break;
+      case 1: c = a[2] * a[7] - a[1] * a[8]; break;
+      case 2: c = a[1] * a[5] - a[2] * a[4]; break;
+      case 3: c = a[5] * a[6] - a[3] * a[8]; break;
+      case 4: c = a[0] * a[8] - a[2] * a[6]; break;
+      case 5: c = a[2] * a[3] - a[0] * a[5]; break;
+      case 6: c = a[3] * a[7] - a[4] * a[6]; break;
+      case 7: c = a[1] * a[6] - a[0] * a[7]; break;
+      default: c = a[0] * a[4] - a[1] * a[3]; break;
+    }
+    cof[lane] = c;
+  }
+  __syncwarp();
+  if (lane == 0) det_s = Ls[0] * cof[0] + Ls[1] * cof[3] + Ls[2] * cof[6];
+  __syncwarp();
+  const double det = det_s;
+  if (lane < 9) {
+    g->L[lane] = Ls[lane];
+    g->Linv[lane] = cof[lane] / det;
+  }
+  // Gram matrix L^T L for the Cholesky QR
+  if (lane < 9) Lt[lane] = Ls[(lane % 3) * 3 + lane / 3];
+  __syncwarp();
+  mm3(Lt, Ls, Gm, lane);
+
+  if (lane == 0) {
+    g->tau = tau;
+    g->V = fabs(det);
+    for (int i = 0; i < 3; i++) {
+      double r0 = cof[3 * i] / det, r1 = cof[3 * i + 1] / det, r2 = cof[3 * i + 2] / det;
+      g->h[i] = 1.0 / sqrt(r0 * r0 + r1 * r1 + r2 * r2);
+    }
+    double r11 = sqrt(Gm[0]);
+    double r12 = Gm[1] / r11, r13 = Gm[2] / r11;
+    double r22 = sqrt(Gm[4] - r12 * r12);
+    double r23 = (Gm[5] - r12 * r13) / r22;
+    double r33 = sqrt(Gm[8] - r13 * r13 - r23 * r23);
+    double R[9] = {r11, r12, r13, 0.0, r22, r23, 0.0, 0.0, r33};
+    for (int k = 0; k < 9; k++) Rm[k] = R[k];
+    double i11 = 1.0 / r11, i22 = 1.0 / r22, i33 = 1.0 / r33;
+    Ri[0] = i11;
+    Ri[1] = -r12 * i11 * i22;
+    Ri[2] = (r12 * r23 - r13 * r22) * i11 * i22 * i33;
+    Ri[3] = 0.0;
+    Ri[4] = i22;
+    Ri[5] = -r23 * i22 * i33;
+    Ri[6] = 0.0;
+    Ri[7] = 0.0;
+    Ri[8] = i33;
+  }
+  __syncwarp();
+  if (lane < 9) g->R[lane] = Rm[lane];
+  mm3(Ls, Ri, Ri, lane);  // Q = L R^-1
+  if (lane < 9) g->Q[lane] = Ri[lane];
+  __syncwarp();
+
+}
+
+// Single thread: cell counts of both variants at k = 1, their neighbourhood
+// volumes (Sec. 5.1: V_DS = 27 V / (c1 c2 c3); Sec. 5.2: V_DO = avg r11 r22 r33 /
+// (l1 l2 l3) with avg = 27 + 14/l3 + 6/l2 - 4/(l2 l3)), the variant of this step,
+// its grid at cell factor k, and the float32 guard band.
+__global__ void k_grid(Geo *g, GridIn in) {
+  if (threadIdx.x != 0) return;
+  g->rc = in.rc;
+  g->req_variant = in.variant;
+  g->kfac = in.kfac;
+  g->max_cells = in.max_cells;
+  double Ls[9], Rm[9], Ri[9];
+  for (int k = 0; k < 9; k++) {
+    Ls[k] = g->L[k];
+    Rm[k] = g->R[k];
+    Ri[k] = g->Q[k];
+  }
+  const double rc = g->rc;
+  const double V = g->V;
+  const double fac = (1.0 - kMargin);
+  int cds1[3], cdo1[3];
+  for (int a = 0; a < 3; a++) {
+    cds1[a] = (int)floor(fac * g->h[a] / rc);
+    cdo1[a] = (int)floor(fac * Rm[4 * a] / rc);
+  }
+  // neighbourhood volumes at k = 1 (Sec. 5.1, 5.2)
+  double vds = 1e300, vdo = 1e300;
+  if (cds1[0] > 0 && cds1[1] > 0 && cds1[2] > 0)
+    vds = 27.0 * V / ((double)cds1[0] * (double)cds1[1] * (double)cds1[2]);
+  if (cdo1[0] > 0 && cdo1[1] > 0 && cdo1[2] > 0) {
+    double l2 = cdo1[1], l3 = cdo1[2];
+    double avg = (cdo1[1] >= 2 && cdo1[2] >= 2) ? 27.0 + 14.0 / l3 + 6.0 / l2 - 4.0 / (l2 * l3) : 36.0;
+    vdo = avg * V / ((double)cdo1[0] * l2 * l3);
+  }
+  g->vol_ds = vds;
+  g->vol_do = vdo;
+  for (int a = 0; a < 3; a++) {
+    g->counts_ds[a] = cds1[a];
+    g->counts_do[a] = cdo1[a];
+  }
+  int variant = g->req_variant;
+  if (variant != NEMD_DS && variant != NEMD_DO) variant = (vdo < vds) ? NEMD_DO : NEMD_DS;
+  g->variant = variant;
+
+  const int kf = g->kfac;
+  int nc[3];
+  double Gd[9];
+  float step[3];
+  int reach[3];
+  int maxrows;
+  const double rce = rc * (1.0 + kMargin);
+  if (variant == NEMD_DS) {
+    for (int a = 0; a < 3; a++) nc[a] = (int)floor(fac * (double)kf * g->h[a] / rc);
+    for (int a = 0; a < 3; a++)
+      for (int b = 0; b < 3; b++) Gd[3 * a + b] = (nc[b] > 0) ? Ls[3 * a + b] / (double)nc[b] : 0.0;
+    for (int a = 0; a < 3; a++) {
+      g->Ginv_scale[a] = (double)nc[a];
+      g->w[a] = 0.0;
+      reach[a] = kf;
+      step[a] = (float)Gd[3 * a + 0];
+    }
+    maxrows = (2 * kf + 1) * (2 * kf + 1);
+    for (int k = 0; k < 9; k++) g->Qf[k] = (k % 4 == 0) ? 1.0f : 0.0f;
+  } else {
+    for (int a = 0; a < 3; a++) nc[a] = (int)floor(fac * (double)kf * Rm[4 * a] / rc);
+    for (int k = 0; k < 9; k++) Gd[k] = 0.0;
+    for (int a = 0; a < 3; a++) {
+      double w = (nc[a] > 0) ? Rm[4 * a] / (double)nc[a] : 1.0;
+      g->w[a] = w;
+      g->Ginv_scale[a] = 1.0 / w;
+      Gd[4 * a] = w;
+      reach[a] = (int)ceil(rce / w);
+    }
+    step[0] = (float)g->w[0];
+    step[1] = 0.0f;
+    step[2] = 0.0f;
+    maxrows = (2 * reach[2] + 1) * (2 * reach[1] + 2);
+    for (int k = 0; k < 9; k++) g->Qf[k] = (float)Ri[k];
+  }
+  int err = 0;
+  long long ncells = (long long)nc[0] * nc[1] * nc[2];
+  if (nc[0] < 1 || nc[1] < 1 || nc[2] < 1) err |= ERRB_BOX;
+  if (ncells > (long long)g->max_cells || maxrows > in.row_stride) err |= ERRB_CAPACITY;
+  g->error |= err;
+  for (int a = 0; a < 3; a++) {
+    g->nc[a] = nc[a];
+    g->reach[a] = reach[a];
+    g->step[a] = step[a];
+  }
+  g->ncells = err ? 0 : (int)ncells;
+  g->maxrows = maxrows;
+  for (int k = 0; k < 9; k++) {
+    g->G[k] = Gd[k];
+    g->Gf[k] = (float)Gd[k];
+  }
+  // float32 guard band on r^2: bound the float32 error of the cell-relative
+  // displacement (each of rel_i, offset, t, rel_j, d rounded once) and of r^2
+  double diam = 0.0;
+  for (int b = 0; b < 3; b++)
+    diam += sqrt(Gd[b] * Gd[b] + Gd[3 + b] * Gd[3 + b] + Gd[6 + b] * Gd[6 + b]);
+  int rmax = max(reach[0], max(reach[1], reach[2]));
+  double omax = (double)(rmax + 2) * diam;
+  const double u = 5.9604644775390625e-08;  // 2^-24
+  double E = u * (4.0 * diam + 2.0 * omax + 2.0 * rc);
+  double band = 2.0 * (2.0 * 1.7320508075688772 * rc * E + 3.0 * E * E + 4.0 * u * rc * rc) + 1e-12 * rc * rc;
+  g->band = (float)band;
+  g->rc2 = rc * rc;
+  g->rc2f = (float)(rc * rc);
+  g->rc2_lo = __double2float_rd(rc * rc - band);
+  g->rc2_hi = __double2float_ru(rc * rc + band);
+  
+}
+
+// One thread per home (iy, iz): the neighbour rows of that class.
+__global__ void k_stencil(Geo *g, Row *rows, int *rowcnt) {
+  if (g->error) return;
+  const int l1 = g->nc[0], l2 = g->nc[1], l3 = g->nc[2];
+  const int ncls = l2 * l3;
+  const int maxrows = g->maxrows;
+  const int variant = g->variant;
+  const double rce = g->rc * (1.0 + kMargin);
+  for (int cls = blockIdx.x * blockDim.x + threadIdx.x; cls < ncls; cls += gridDim.x * blockDim.x) {
+    const int iy = cls % l2, iz = cls / l2;
+    Row *out = rows + (size_t)cls * maxrows;
+    int nr = 0;
+    if (variant == NEMD_DS) {
+      const int K = g->kfac;
+      for (int dz = -K; dz <= K; dz++)
+        for (int dy = -K; dy <= K; dy++) {
+          int jyu = iy + dy, jzu = iz + dz;
+          int ky = floordiv_i(jyu, l2), kz = floordiv_i(jzu, l3);
+          int jy = jyu - ky * l2, jz = jzu - kz * l3;
+          double c0 = -(double)K, c1 = dy, c2 = dz;
+          Row r;
+          r.ox = (float)(g->G[0] * c0 + g->G[1] * c1 + g->G[2] * c2);
+          r.oy = (float)(g->G[3] * c0 + g->G[4] * c1 + g->G[5] * c2);
+          r.oz = (float)(g->G[6] * c0 + g->G[7] * c1 + g->G[8] * c2);
+          r.cbase = l1 * (jy + l2 * jz);
+          r.dxlo = -K;
+          r.cnt = 2 * K + 1;
+          r.ky = (short)ky;
+          r.kz = (short)kz;
+          r.pad = 0;
+          if (nr < maxrows) out[nr] = r;
+          nr++;
+        }
+    } else {
+      const double w1 = g->w[0], w2 = g->w[1], w3 = g->w[2];
+      const double r12 = g->R[1], r13 = g->R[2], r23 = g->R[5];
+      int zlo = (int)floor(((double)iz * w3 - rce) / w3);
+      int zhi = (int)ceil(((double)(iz + 1) * w3 + rce) / w3) - 1;
+      for (int jzu = zlo; jzu <= zhi; jzu++) {
+        int kz = floordiv_i(jzu, l3), jz = jzu - kz * l3;
+        double yshift = (double)kz * r23;
+        int ylo = (int)floor(((double)iy * w2 - rce - yshift) / w2);
+        int yhi = (int)ceil(((double)(iy + 1) * w2 + rce - yshift) / w2) - 1;
+        for (int jyu = ylo; jyu <= yhi; jyu++) {
+          int ky = floordiv_i(jyu, l2), jy = jyu - ky * l2;
+          double sx = (double)ky * r12 + (double)kz * r13;
+          int xlo = (int)floor((-rce - sx) / w1);
+          int xhi = (int)ceil((w1 + rce - sx) / w1) - 1;
+          Row r;
+          r.ox = (float)((double)xlo * w1 + sx);
+          r.oy = (float)((double)(jyu - iy) * w2 + yshift);
+          r.oz = (float)((double)(jzu - iz) * w3);
+          r.cbase = l1 * (jy + l2 * jz);
+          r.dxlo = xlo;
+          r.cnt = xhi - xlo + 1;
+          r.ky = (short)ky;
+          r.kz = (short)kz;
+          r.pad = 0;
+          if (nr < maxrows) out[nr] = r;
+          nr++;
+        }
+      }
+    }
+    if (nr > maxrows) {
+      atomicOr(&g->error, ERRB_CAPACITY);
+      nr = maxrows;
+    }
+    rowcnt[cls] = nr;
+  }
+}
+
+cudaError_t launch_lattice(nemd_ctx *c, int validate, double tau) {
+  LatIn in;
+  for (int k = 0; k < 9; k++) {
+    in.A[k] = c->A[k];
+    in.L0[k] = c->L0[k];
+  }
+  in.T = c->T;
+  in.t = c->t;
+  in.tau = tau;
+  in.validate = validate;
+  k_lattice<<<1, 32, 0, c->stream>>>(c->geo, in);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grid(nemd_ctx *c) {
+  GridIn in;
+  in.rc = c->rc;
+  in.variant = c->variant_req;
+  in.kfac = c->kfac;
+  in.max_cells = (int)c->cap_cells;
+  in.row_stride = (2 * c->kfac + 1) * (2 * c->kfac + 2);
+  k_grid<<<1, 32, 0, c->stream>>>(c->geo, in);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stencil(nemd_ctx *c) {
+  int64_t classes = c->cap_cells;  // l2 * l3 <= ncells <= cap
+  int threads = 128;
+  int64_t blocks = (classes + threads - 1) / threads;
+  if (blocks > 4 * (int64_t)c->sms) blocks = 4 * (int64_t)c->sms;
+  if (blocks < 1) blocks = 1;
+  k_stencil<<<(int)blocks, threads, 0, c->stream>>>(c->geo, c->rows, c->rowcnt);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace nemd

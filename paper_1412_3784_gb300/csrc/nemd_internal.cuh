@@ -1,0 +1,164 @@
+// nemd_internal.cuh -- device data layout shared by the CUDA translation units.
+//
+// Geometry of one evaluation lives in a device-resident Geo record written by
+// the lattice kernel (Sec. 2.1-2.2 lattice, Sec. 4.1/4.2 cell grid) and read by
+// every later kernel, so the host never waits for the device between steps.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/nemd.h"
+
+namespace nemd {
+
+// Relative safety margin of the cell counts and stencil intervals: counts are
+// floor((1 - kMargin) k h / rc) and intervals use rc (1 + kMargin), so FP64
+// rounding of positions can never drop a pair.
+constexpr double kMargin = 1e-12;
+constexpr int kMaxFactor = 3;          // largest cell-size factor k
+constexpr int kMaxRowsPerClass = 64;   // (2k+2)^2 for k = 3
+
+// Device error word bits (deferred errors).
+enum : int {
+  ERRB_BOX = 1,
+  ERRB_NONFINITE = 2,
+  ERRB_CAPACITY = 4,
+  ERRB_TIMEOUT = 8,
+};
+
+struct Geo {
+  // ---- inputs (host-written) ----
+  double A[9], L0[9];
+  double T;
+  double t;
+  double rc, rc2;
+  int variant;   // NEMD_DS / NEMD_DO actually used for this step
+  int req_variant;
+  int kfac;
+  int max_cells;  // host bound on the number of cells (allocation size)
+  // ---- lattice (a1) ----
+  double tau;
+  double L[9], Linv[9], V, h[3], Q[9], R[9];
+  // ---- grid (a3) ----
+  int nc[3];
+  int ncells;
+  int maxrows;        // row stride per (iy, iz) class
+  int reach[3];       // stencil reach in cells per axis
+  double G[9];        // frame position of cell corner = G * (ix, iy, iz)
+  double Ginv_scale[3];  // DS: c_i ; DO: 1 / w_i
+  double w[3];        // DO cell sides
+  float Gf[9];
+  float step[3];      // frame vector from one x-cell to the next
+  float Qf[9];        // rotation frame -> Cartesian (identity for DS)
+  float rc2_lo, rc2_hi, rc2f;
+  float band;
+  double vol_ds, vol_do;  // neighbourhood volumes (Sec. 5.1, 5.2) of both variants
+  int counts_ds[3], counts_do[3];
+  int error;   // this step's error bits
+  int sticky;  // error bits accumulated until the host reads them (nemd_sync)
+};
+
+// Launch inputs, passed by value so that asynchronous launches and captured
+// graphs see the values of the call that issued them.
+struct LatIn {
+  double A[9], L0[9];
+  double T, t, tau;
+  int validate;
+};
+
+struct GridIn {
+  double rc;
+  int variant, kfac, max_cells, row_stride;
+};
+
+// One neighbour row of a home (iy, iz) class: the x-cells ix+dxlo ... ix+dxlo+cnt-1
+// of the wrapped row (jy, jz), reached through lattice image (kx, ky, kz) where kx
+// follows from the x wrap.  (ox, oy, oz) is the frame vector from the home cell's
+// corner to the corner of the first cell of the run.
+struct __align__(16) Row {
+  float ox, oy, oz;
+  int cbase;   // l1 * (jy + l2 * jz)
+  int dxlo;
+  int cnt;
+  short ky, kz;
+  int pad;
+};
+static_assert(sizeof(Row) == 32, "Row is 32 bytes");
+
+// Per-block partial sums of the force kernel (float64): U, W (6 symmetric
+// components xx yy zz xy xz yz), interacting pairs, candidates, rechecks.
+constexpr int kPartials = 10;
+
+struct Buffers;
+
+}  // namespace nemd
+
+// Context (opaque to callers).
+struct nemd_ctx {
+  int device;
+  cudaStream_t stream;
+  int sms;
+  // flow / potential
+  double A[9], L0[9], T;
+  int64_t M[9];
+  bool have_flow, have_pot, have_state, have_cells;
+  int pot_kind;
+  double eps, sigma;
+  int shift;
+  // state
+  int64_t n;
+  double t;
+  const double *q_dev;  // device positions (user's or internal copy)
+  double rc;
+  int variant_req;
+  // options
+  int precise;
+  int64_t record_cap;
+  int kernel;
+  int kfac;
+  int block;
+  // device memory
+  nemd::Geo *geo;
+  int64_t cap_n;
+  int64_t cap_cells;
+  int64_t cap_rows;
+  double *q_copy;
+  float4 *relc;          // per input particle: frame rel position + cell (bits) in w
+  int *rank;
+  int *count;            // cap_cells + 1
+  int *start;            // cap_cells + 1
+  int *block_sums;
+  int *perm;
+  float4 *pos4;          // sorted: rel position + original index (bits)
+  int *cell_sorted;
+  nemd::Row *rows;
+  int *rowcnt;
+  double *partials;
+  int64_t cap_partials;
+  double *uw_out;        // device U (1) + W (9)
+  float *f_dev;          // internal F buffer (host outputs)
+  int32_t *pair_buf;
+  unsigned long long *pair_count;
+  unsigned long long *counters;  // [0] pairs [1] candidates [2] rechecks
+  // force-kernel timing (CUDA events on the context's stream)
+  int timing;
+  cudaEvent_t *ev;
+  int ev_cap, ev_n;
+  int64_t launches;
+  // host staging
+  int *h_error;  // pinned
+  char msg[512];
+  double last_stats_band;
+};
+
+namespace nemd {
+
+// ---- kernels (launch wrappers implemented in the .cu files) ----
+cudaError_t launch_lattice(nemd_ctx *c, int validate, double tau);
+cudaError_t launch_grid(nemd_ctx *c);
+cudaError_t launch_stencil(nemd_ctx *c);
+cudaError_t launch_bin(nemd_ctx *c);
+cudaError_t launch_forces(nemd_ctx *c, float *F_dev, double *UW_dev);
+
+}  // namespace nemd

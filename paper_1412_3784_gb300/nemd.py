@@ -1,0 +1,198 @@
+"""Thin ctypes binding of the C ABI in include/nemd.h (libnemd.so).
+
+Argument marshalling only: every step of the force evaluation runs in the
+library's CUDA kernels.  Importing this module loads libnemd.so and raises
+ImportError if it is missing -- there is no CPU fallback.
+
+Functions keep the C names (nemd_create, nemd_set_flow, ...).  `Context` is a
+small convenience wrapper that accepts torch tensors or numpy arrays and uses
+torch's current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnemd.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_1412_3784_gb300.build.build() "
+                      "(the CUDA library is required; there is no fallback)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+NEMD_OK = 0
+ERRORS = {1: "ARG", 2: "NOT_SL3Z", 3: "NOT_KR", 4: "TRACE", 5: "BOX_TOO_SMALL", 6: "ORDER",
+          7: "CUDA", 8: "NONFINITE", 9: "TIMEOUT", 10: "CAPACITY", 11: "NOMEM", 12: "UNSUPPORTED"}
+NEMD_DS, NEMD_DO, NEMD_AUTO_HEURISTIC, NEMD_AUTO_LEARNED = 0, 1, 2, 3
+NEMD_LJ, NEMD_WCA = 0, 1
+NEMD_OPT_PRECISE, NEMD_OPT_RECORD_PAIRS, NEMD_OPT_KERNEL, NEMD_OPT_CELL_FACTOR, NEMD_OPT_BLOCK = 1, 2, 3, 4, 5
+NEMD_OPT_TIMING = 6
+
+EXPORTED = ["nemd_create", "nemd_destroy", "nemd_set_flow", "nemd_set_potential", "nemd_set_state",
+            "nemd_build_cells", "nemd_compute_forces", "nemd_sync", "nemd_last_error",
+            "nemd_set_option", "nemd_get_lattice", "nemd_get_stats", "nemd_get_pairs",
+            "nemd_get_kernel_time", "nemd_measure_peaks"]
+
+
+class nemd_stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("pairs", ctypes.c_int64), ("candidates", ctypes.c_int64),
+                ("ncells", ctypes.c_int64), ("counts", ctypes.c_int32 * 3), ("variant", ctypes.c_int32),
+                ("cell_factor", ctypes.c_int32), ("max_rows", ctypes.c_int32),
+                ("stencil_cells", ctypes.c_int64), ("rechecks", ctypes.c_int64),
+                ("tau", ctypes.c_double), ("band", ctypes.c_double), ("launches", ctypes.c_int64)]
+
+
+_vp = ctypes.c_void_p
+_sig = {
+    "nemd_create": ([ctypes.POINTER(_vp), ctypes.c_int, _vp], ctypes.c_int),
+    "nemd_destroy": ([_vp], ctypes.c_int),
+    "nemd_set_flow": ([_vp, _vp, _vp, _vp, ctypes.c_double], ctypes.c_int),
+    "nemd_set_potential": ([_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int], ctypes.c_int),
+    "nemd_set_state": ([_vp, _vp, ctypes.c_int64, ctypes.c_double], ctypes.c_int),
+    "nemd_build_cells": ([_vp, ctypes.c_int, ctypes.c_double], ctypes.c_int),
+    "nemd_compute_forces": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+    "nemd_sync": ([_vp], ctypes.c_int),
+    "nemd_last_error": ([_vp], ctypes.c_char_p),
+    "nemd_set_option": ([_vp, ctypes.c_int, ctypes.c_int64], ctypes.c_int),
+    "nemd_get_lattice": ([_vp, _vp], ctypes.c_int),
+    "nemd_get_stats": ([_vp, ctypes.POINTER(nemd_stats)], ctypes.c_int),
+    "nemd_get_pairs": ([_vp, _vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "nemd_get_kernel_time": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
+                             ctypes.c_int),
+    "nemd_measure_peaks": ([ctypes.c_int, _vp], ctypes.c_int),
+}
+for _name, (_args, _res) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+    globals()[_name] = _f
+
+
+class NemdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"nemd error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+def _ptr(x):
+    """Raw address of a torch tensor, numpy array, or None."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(type(x))
+
+
+def _current_stream(device):
+    import torch
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def measure_peaks(device=0):
+    out = np.zeros(6)
+    rc = nemd_measure_peaks(int(device), out.ctypes.data)
+    if rc:
+        raise NemdError(rc, "measure_peaks")
+    return {"fp32_fma_ops": out[0], "fp32x2_fma_ops": out[1], "fp64_fma_ops": out[2],
+            "copy_bytes_per_s": out[3], "sms": int(out[4]), "sm_clock_khz": out[5]}
+
+
+class Context:
+    """One nemd_ctx on a CUDA device and stream (torch's current stream by default)."""
+
+    def __init__(self, device=0, stream=None):
+        if stream is None:
+            stream = _current_stream(device)
+        h = _vp()
+        rc = nemd_create(ctypes.byref(h), int(device), _vp(stream))
+        if rc:
+            raise NemdError(rc, "nemd_create")
+        self.h = h
+        self._keep = {}
+
+    def close(self):
+        if self.h:
+            nemd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc:
+            raise NemdError(rc, nemd_last_error(self.h).decode())
+        return rc
+
+    def set_flow(self, A, L0, M, T):
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        L0 = np.ascontiguousarray(L0, dtype=np.float64)
+        M = np.ascontiguousarray(M, dtype=np.int64)
+        return self._check(nemd_set_flow(self.h, A.ctypes.data, L0.ctypes.data, M.ctypes.data, float(T)))
+
+    def set_potential(self, kind=NEMD_LJ, eps=1.0, sigma=1.0, shift=1):
+        return self._check(nemd_set_potential(self.h, int(kind), float(eps), float(sigma), int(shift)))
+
+    def set_state(self, q, t):
+        self._keep["q"] = q   # keep the buffer alive while the device may read it
+        n = int(q.shape[0])
+        return self._check(nemd_set_state(self.h, _ptr(q), n, float(t)))
+
+    def build_cells(self, variant, rc):
+        return self._check(nemd_build_cells(self.h, int(variant), float(rc)))
+
+    def compute_forces(self, F=None, U=None, W=None):
+        return self._check(nemd_compute_forces(self.h, _ptr(F), _ptr(U), _ptr(W)))
+
+    def sync(self):
+        return self._check(nemd_sync(self.h))
+
+    def set_option(self, key, value):
+        return self._check(nemd_set_option(self.h, int(key), int(value)))
+
+    def lattice(self):
+        out = np.zeros(48)
+        self._check(nemd_get_lattice(self.h, out.ctypes.data))
+        return {"L": out[0:9].reshape(3, 3).copy(), "Linv": out[9:18].reshape(3, 3).copy(),
+                "V": float(out[18]), "h": out[19:22].copy(), "Q": out[22:31].reshape(3, 3).copy(),
+                "R": out[31:40].reshape(3, 3).copy(), "tau": float(out[40]), "band": float(out[41]),
+                "counts": out[42:45].astype(np.int64), "ncells": int(out[45]),
+                "variant": int(out[46]), "maxrows": int(out[47])}
+
+    def stats(self):
+        s = nemd_stats()
+        self._check(nemd_get_stats(self.h, ctypes.byref(s)))
+        return {"n": s.n, "pairs": s.pairs, "candidates": s.candidates, "ncells": s.ncells,
+                "counts": list(s.counts), "variant": s.variant, "cell_factor": s.cell_factor,
+                "max_rows": s.max_rows, "stencil_cells": s.stencil_cells, "rechecks": s.rechecks,
+                "tau": s.tau, "band": s.band, "launches": s.launches}
+
+    def kernel_time(self):
+        """(total ms, launches) of the force kernel since the last call (timing option on)."""
+        ms = ctypes.c_double(0.0)
+        n = ctypes.c_int64(0)
+        self._check(nemd_get_kernel_time(self.h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, int(n.value)
+
+    def pairs(self, cap=None):
+        cnt = ctypes.c_int64(0)
+        rc = nemd_get_pairs(self.h, None, 0, ctypes.byref(cnt))
+        if rc not in (0, 10):
+            self._check(rc)
+        n = int(cnt.value) if cap is None else int(cap)
+        out = np.zeros((max(n, 1), 5), dtype=np.int32)
+        self._check(nemd_get_pairs(self.h, out.ctypes.data, n, ctypes.byref(cnt)))
+        return out[: int(cnt.value)]
+

@@ -123,27 +123,62 @@ def config_equilibrium_wca(k: int = 10, seed: int = 0) -> Workload:
                    s, delta, np.eye(3), rng, POT_WCA, WCA_RC)
 
 
+class StrainSeries:
+    """One perturbed FCC system under the KR flow of a symmetric M, at any time t.
+
+    The sites, displacements and particle order are drawn once from the seed;
+    positions(t) places them affinely for the flow at time t.  rate scales the
+    strain rate: A = rate * V diag(ln lam) V^T / T, period T / rate.
+    """
+
+    def __init__(self, M, k, seed, *, T=1.0, rho=RHO_DEFAULT, kind=POT_LJ, rc=None, rate=1.0,
+                 vacancies=0, name=None):
+        rng = np.random.default_rng(seed)
+        self.s, side, self.delta = perturbed_fcc(k, rho, rng, vacancies=vacancies)
+        self.period = T / rate
+        self.A, self.V, self.lam = kr_flow(M, self.period)
+        self.L0 = side * np.eye(3)
+        self.M = np.asarray(M, dtype=np.int64).copy()
+        self.order = rng.permutation(self.s.shape[0])
+        self.kind = kind
+        self.rc = (WCA_RC if kind == POT_WCA else LJ_RC) if rc is None else rc
+        self.name = name or f"kr_N{self.s.shape[0]}"
+        self._sL = self.s @ self.L0.T
+
+    @property
+    def n(self):
+        return int(self.s.shape[0])
+
+    def positions(self, t):
+        tau = t - self.period * math.floor(t / self.period)
+        F = _deformation(self.V, self.lam, tau, self.period)
+        q = self._sL @ F.T + self.delta
+        return np.ascontiguousarray(q[self.order])
+
+    def workload(self, t, name=None):
+        return Workload(name=name or f"{self.name}_t{t:.6g}", A=self.A, L0=self.L0, M=self.M,
+                        T=self.period, t=t, q=self.positions(t), kind=self.kind, rc=self.rc)
+
+
 def config_flow(M: np.ndarray, k: int, t: float, seed: int, *, T: float = 1.0,
                 rho: float = RHO_DEFAULT, kind: int = POT_LJ, rc: float | None = None,
                 rate: float = 1.0, vacancies: int = 0, name: str | None = None) -> Workload:
-    """Perturbed FCC under the KR flow of a symmetric M, evaluated at time t.
+    """Perturbed FCC under the KR flow of a symmetric M, evaluated at time t."""
+    ser = StrainSeries(M, k, seed, T=T, rho=rho, kind=kind, rc=rc, rate=rate, vacancies=vacancies)
+    return ser.workload(t, name=name or f"kr_N{ser.n}_t{t:.6g}")
 
-    rate scales the strain rate: A = rate * V diag(ln lam) V^T / T, period T / rate.
-    Positions are affine in the flow (see module docstring); the same seed gives
-    the same sites and displacements at every t.
+
+def general_series(k: int = 64, seed: int = 4) -> StrainSeries:
+    """General 3D flow (M = [[3,2,1],[2,2,1],[1,1,1]]) on N = 4k^3 LJ particles, rc = 2.5.
+
+    k = 64 gives the N = 1,048,576 system, k = 80 the N = 2,097,152 one, k = 40
+    the N = 256,000 one.
     """
-    rng = np.random.default_rng(seed)
-    s, side, delta = perturbed_fcc(k, rho, rng, vacancies=vacancies)
-    period = T / rate
-    A, V, lam = kr_flow(M, period)
-    tau = t - period * math.floor(t / period)
-    F = _deformation(V, lam, tau, period)
-    L0 = side * np.eye(3)
-    if rc is None:
-        rc = WCA_RC if kind == POT_WCA else LJ_RC
-    nm = name or f"kr_N{s.shape[0]}_t{t:.6g}"
-    return _finish(nm, A, L0, np.asarray(M, dtype=np.int64).copy(), period, t, s, delta, F,
-                   rng, kind, rc)
+    return StrainSeries(M_GENERAL, k, seed, name=f"general_N{4 * k ** 3}")
+
+
+def planar_series(k: int = 20, seed: int = 1) -> StrainSeries:
+    return StrainSeries(M_PLANAR, k, seed, name=f"planar_N{4 * k ** 3}")
 
 
 def config_planar(i: int = 0, nstrain: int = 64, k: int = 20, seed: int = 1) -> Workload:

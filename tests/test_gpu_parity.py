@@ -1,0 +1,216 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars (stated with the benchmark spec's targets):
+  pair sets            bit-exact (i, j, n) against the oracle
+  forces               max|dF| / max|F| <= 1e-5   (float32 pair arithmetic)
+  energy, virial       rel <= 1e-9 in precise mode (float64 accepted pairs);
+                       fast mode (float32 pairs, float64 reductions) <= 2e-6,
+                       the float32 rounding bound of the per-pair terms
+  lattice              |L_gpu - L_oracle| <= 1e-13 |L|
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1412_3784_gb300 import workloads as W
+from gpu_util import force_err, mat_rel, rel, run
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+DS, DO = 0, 1
+F_TOL = 1e-5
+UW_TOL_PRECISE = 1e-9
+UW_TOL_FAST = 2e-6
+
+
+def keys(p):
+    return oracle.canonical_pair_keys(p)
+
+
+def check_against(w, variant, ref, *, pairs=True, precise=True, kfac=1):
+    if pairs:
+        g = run(w, variant, record=True, kfac=kfac)
+        assert g["stats"]["pairs"] == ref.npairs
+        assert np.array_equal(keys(g["pairs"]), keys(ref.pairs)), "pair sets differ"
+    g = run(w, variant, kfac=kfac)
+    assert g["stats"]["pairs"] == ref.npairs
+    assert force_err(g["F"], ref.F) <= F_TOL
+    assert rel(g["U"], ref.U) <= UW_TOL_FAST
+    assert mat_rel(g["W"], ref.W) <= UW_TOL_FAST
+    if precise:
+        gp = run(w, variant, precise=True, kfac=kfac)
+        assert gp["stats"]["pairs"] == ref.npairs
+        assert rel(gp["U"], ref.U) <= UW_TOL_PRECISE
+        assert mat_rel(gp["W"], ref.W) <= UW_TOL_PRECISE
+        assert force_err(gp["F"], ref.F) <= 1e-6
+    return g
+
+
+# ---------------------------------------------------------------- lattice ----
+
+@pytest.mark.parametrize("M", [W.M_PLANAR, W.M_GENERAL])
+def test_lattice_matches_oracle(M):
+    for t in (0.0, 0.25, 0.6180339, W.NEAR_REMAP_T, 3.75):
+        w = W.config_flow(M, 6, t, seed=9)
+        g = run(w, DS)
+        lat = g["lattice"]
+        ref = oracle.lattice(w.A, w.L0, w.T, w.t)
+        scale = np.abs(ref["L"]).max()
+        assert np.abs(lat["L"] - ref["L"]).max() <= 1e-13 * scale
+        assert np.abs(lat["Linv"] - ref["Linv"]).max() <= 1e-12 * np.abs(ref["Linv"]).max()
+        assert np.allclose(lat["h"], ref["h"], rtol=1e-13)
+        assert np.allclose(lat["R"], ref["R"], rtol=0, atol=1e-12 * scale)
+        assert abs(lat["V"] - ref["V"]) <= 1e-12 * ref["V"]
+        assert np.array_equal(lat["counts"], oracle.ds_counts(ref["L"], w.rc))
+        g2 = run(w, DO)
+        assert np.array_equal(g2["lattice"]["counts"], oracle.do_counts(ref["R"], w.rc))
+
+
+# ------------------------------------------------------------- config 0 ----
+
+@pytest.mark.parametrize("variant", [DS, DO])
+def test_config0_wca_equilibrium(variant):
+    w = W.config_equilibrium_wca()
+    ref = oracle.evaluate(w, "brute", want_pairs=True)
+    check_against(w, variant, ref)
+
+
+# ------------------------------------------------------ flows at strains ----
+
+@pytest.mark.parametrize("i", [0, 17, 40, 63])
+@pytest.mark.parametrize("variant", [DS, DO])
+def test_planar_flow_strains(i, variant):
+    w = W.config_planar(i, k=12)   # 6912 particles, several tiles and a ragged tail
+    ref = oracle.evaluate(w, "do" if variant else "ds", want_pairs=True)
+    check_against(w, variant, ref)
+
+
+@pytest.mark.parametrize("t", [0.3, 0.71, W.NEAR_REMAP_T])
+@pytest.mark.parametrize("variant", [DS, DO])
+def test_general_flow_incl_max_skew(t, variant):
+    w = W.config_general(t=t, k=11)   # 5324 particles
+    ref = oracle.evaluate(w, "ds", want_pairs=True)
+    check_against(w, variant, ref)
+
+
+@pytest.mark.parametrize("variant", [DS, DO])
+def test_planar_config_full_size(variant):
+    """The planar-flow configuration at its full size (N = 32000) at two strains."""
+    for i in (9, 50):
+        w = W.config_planar(i)
+        ref = oracle.evaluate(w, "ds", want_pairs=True)
+        check_against(w, variant, ref, precise=(i == 9))
+
+
+# ------------------------------------------------------- tiny / ragged ----
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("kfac", [1, 2])
+def test_tiny_skewed_boxes(seed, kfac):
+    """Boxes with 1-3 cells per direction: multiple images of one partner."""
+    rng = np.random.default_rng(500 + seed)
+    rc = 1.3
+    L, q = W.small_random_box(rng, 37 + 11 * seed, rc, 1.0, 3.2)
+    w = W.Workload(name="tiny", A=np.zeros((3, 3)), L0=L, M=W.M_IDENTITY.copy(), T=1.0, t=0.0,
+                   q=q, kind=W.POT_LJ, rc=rc)
+    ref = oracle.evaluate(w, "brute", want_pairs=True)
+    for variant in (DS, DO):
+        check_against(w, variant, ref, kfac=kfac)
+
+
+def test_edge_cases_small_n():
+    L = 9.0 * np.eye(3)
+    base = dict(A=np.zeros((3, 3)), L0=L, M=W.M_IDENTITY.copy(), T=1.0, t=0.0, kind=W.POT_LJ, rc=2.5)
+    # N = 0
+    w0 = W.Workload(name="empty", q=np.zeros((0, 3)), **base)
+    g = run(w0, DS)
+    assert g["stats"]["pairs"] == 0 and g["U"] == 0.0 and np.all(g["W"] == 0)
+    # N = 1: no pair, not even with its own images (h = 9 > rc)
+    w1 = W.Workload(name="one", q=np.array([[1.0, 2.0, 3.0]]), **base)
+    for v in (DS, DO):
+        g = run(w1, v)
+        assert g["stats"]["pairs"] == 0 and np.all(g["F"] == 0)
+    # N = 2 across the periodic boundary: closed form
+    r = 1.2
+    w2 = W.Workload(name="two", q=np.array([[0.1, 4.0, 4.0], [0.1 - r, 4.0, 4.0]]), **base)
+    for v in (DS, DO):
+        g = run(w2, v, precise=True)
+        u = 4 * (r ** -12 - r ** -6) - 4 * (2.5 ** -12 - 2.5 ** -6)
+        assert g["stats"]["pairs"] == 1
+        assert abs(g["U"] - u) < 1e-12
+        du = -48 * r ** -13 + 24 * r ** -7
+        assert abs(g["F"][0, 0] - (-du)) < 1e-5 * abs(du)
+
+
+def test_ragged_counts_and_empty_cells():
+    """A dilute random system: many empty cells, uneven occupancy."""
+    w = W.uniform_random(777, 30.0 * np.eye(3), seed=3)
+    ref = oracle.evaluate(w, "brute", want_pairs=True)
+    for v in (DS, DO):
+        check_against(w, v, ref)
+
+
+# ------------------------------------------------------------ properties ----
+
+def test_deterministic_repeat():
+    w = W.config_planar(23, k=10)
+    a = run(w, DO)
+    b = run(w, DO)
+    assert np.array_equal(a["F"], b["F"]) and a["U"] == b["U"]
+
+
+def test_variants_agree_and_newton():
+    w = W.config_general(t=0.45, k=12)
+    a = run(w, DS)
+    b = run(w, DO)
+    assert a["stats"]["pairs"] == b["stats"]["pairs"]
+    assert force_err(a["F"], b["F"]) <= 2 * F_TOL
+    assert np.abs(a["F"].sum(0)).max() <= 1e-5 * np.abs(a["F"]).max() * np.sqrt(w.n)
+
+
+def test_host_pointers_match_device():
+    from paper_1412_3784_gb300 import nemd
+    from gpu_util import make_ctx
+    w = W.config_planar(5, k=8)
+    g = run(w, DS)
+    ctx = make_ctx(w, nemd, torch)
+    F = np.zeros((w.n, 3), dtype=np.float32)
+    U = np.zeros(1)
+    Wv = np.zeros(9)
+    ctx.set_state(np.ascontiguousarray(w.q), w.t)
+    ctx.build_cells(DS, w.rc)
+    ctx.compute_forces(F, U, Wv)
+    assert np.array_equal(F.astype(np.float64), g["F"])
+    assert U[0] == g["U"]
+    ctx.close()
+
+
+def test_auto_heuristic_picks_smaller_volume():
+    from paper_1412_3784_gb300 import nemd
+    for t in (0.0, 0.5, W.NEAR_REMAP_T):
+        w = W.config_general(t=t, k=10)
+        g = run(w, nemd.NEMD_AUTO_HEURISTIC)
+        ref = oracle.evaluate(w, "ds")
+        assert g["stats"]["pairs"] == ref.npairs
+        lat = oracle.lattice(w.A, w.L0, w.T, w.t)
+        c = oracle.ds_counts(lat["L"], w.rc)
+        l = oracle.do_counts(lat["R"], w.rc)
+        vds = 27 * lat["V"] / np.prod(c)
+        avg = 27 + 14 / l[2] + 6 / l[1] - 4 / (l[1] * l[2])
+        vdo = avg * lat["V"] / np.prod(l)
+        assert g["stats"]["variant"] == (1 if vdo < vds else 0)
+
+
+def test_do_stencil_size_matches_oracle():
+    for t in (0.0, 0.37, W.NEAR_REMAP_T):
+        w = W.config_general(t=t, k=10)
+        g = run(w, DO)
+        lat = oracle.lattice(w.A, w.L0, w.T, w.t)
+        assert g["stats"]["stencil_cells"] == oracle.do_total_stencil_cells(lat["R"], w.rc)
+        d = run(w, DS)
+        c = oracle.ds_counts(lat["L"], w.rc)
+        assert d["stats"]["stencil_cells"] == 27 * int(np.prod(c))
