@@ -5,13 +5,14 @@
 // Sec. 4.2: rectangular rearrangement of the rotated box).
 //
 // Pipeline (all O(N), HBM-bound):
-//   k_wrap      s = frac(L^-1 q) (FP64), cell index, float32 cell-relative
-//               position in the variant's frame, rank = atomicAdd(count[cell])
+//   k_wrap      s = frac(L^-1 q) (FP64), cell index, position relative to the
+//               cell centre in the variant's frame as a float32 multiple of the
+//               step's quantum plus a float32 residual, rank = atomicAdd(count[cell])
 //   k_scan_*    exclusive scan of the per-cell counts -> start[]
 //   k_scatter   perm[start[cell] + rank] = i
 //   k_cellsort  per cell, particles in increasing input index (stable order,
 //               so sums are reproducible from run to run)
-//   k_pack      sorted float4 {rel position, input index} and sorted cell ids
+//   k_pack      sorted float4 {rel position, input index}, residuals, cell ids
 #include <math.h>
 
 #include "nemd_device.cuh"
@@ -20,7 +21,7 @@
 namespace nemd {
 
 __global__ void k_wrap(Geo *g, const double *__restrict__ q, int n, float4 *__restrict__ relc,
-                       int *__restrict__ rank, int *__restrict__ count) {
+                       float4 *__restrict__ relr, int *__restrict__ rank, int *__restrict__ count) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
@@ -32,19 +33,21 @@ __global__ void k_wrap(Geo *g, const double *__restrict__ q, int n, float4 *__re
   double s[3];
   frac_wrap(g->Linv, x, y, z, s);
   const int l1 = g->nc[0], l2 = g->nc[1], l3 = g->nc[2];
+  // position relative to the centre of its cell, in the variant's frame:
+  // dynamic size: Cartesian, G (u - 1/2) with u = c s - idx the cell-fractional part;
+  // dynamic offset: the rotated frame, b - (idx + 1/2) w for the brick point b
   int idx[3];
-  float rel[3];
+  double rel[3];
   if (g->variant == NEMD_DS) {
-    float u[3];
+    double u[3];
     for (int a = 0; a < 3; a++) {
       double v = s[a] * g->Ginv_scale[a];
       int k = (int)floor(v);
       k = min(max(k, 0), g->nc[a] - 1);
       idx[a] = k;
-      u[a] = (float)(v - (double)k);
+      u[a] = (v - (double)k) - 0.5;
     }
-    for (int a = 0; a < 3; a++)
-      rel[a] = fmaf(g->Gf[3 * a + 2], u[2], fmaf(g->Gf[3 * a + 1], u[1], g->Gf[3 * a] * u[0]));
+    for (int a = 0; a < 3; a++) rel[a] = g->G[3 * a] * u[0] + g->G[3 * a + 1] * u[1] + g->G[3 * a + 2] * u[2];
   } else {
     double b[3];
     int m[3];
@@ -53,12 +56,21 @@ __global__ void k_wrap(Geo *g, const double *__restrict__ q, int n, float4 *__re
       int k = (int)floor(b[a] * g->Ginv_scale[a]);
       k = min(max(k, 0), g->nc[a] - 1);
       idx[a] = k;
-      rel[a] = (float)(b[a] - (double)k * g->w[a]);
+      rel[a] = b[a] - ((double)k + 0.5) * g->w[a];
     }
+  }
+  // split into an exact multiple of the quantum and a float32 residual
+  const double qu = g->quantum, qinv = 1.0 / qu;
+  float rq[3], rr[3];
+  for (int a = 0; a < 3; a++) {
+    double h = rint(rel[a] * qinv) * qu;
+    rq[a] = (float)h;
+    rr[a] = (float)(rel[a] - h);
   }
   const int cell = idx[0] + l1 * (idx[1] + l2 * idx[2]);
   (void)l3;
-  relc[i] = make_float4(rel[0], rel[1], rel[2], __int_as_float(cell));
+  relc[i] = make_float4(rq[0], rq[1], rq[2], __int_as_float(cell));
+  relr[i] = make_float4(rr[0], rr[1], rr[2], 0.0f);
   rank[i] = atomicAdd(&count[cell], 1);
 }
 
@@ -170,14 +182,16 @@ __global__ void k_cellsort(const Geo *g, const int *__restrict__ start, int *__r
   }
 }
 
-__global__ void k_pack(const Geo *g, const float4 *__restrict__ relc, const int *__restrict__ perm,
-                       float4 *__restrict__ pos4, int *__restrict__ cell_sorted, int n) {
+__global__ void k_pack(const Geo *g, const float4 *__restrict__ relc, const float4 *__restrict__ relr,
+                       const int *__restrict__ perm, float4 *__restrict__ pos4, float4 *__restrict__ posr,
+                       int *__restrict__ cell_sorted, int n) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
   const int i = perm[k];
   const float4 r = relc[i];
   pos4[k] = make_float4(r.x, r.y, r.z, __int_as_float(i));
+  posr[k] = relr[i];
   cell_sorted[k] = __float_as_int(r.w);
 }
 
@@ -188,7 +202,7 @@ cudaError_t launch_bin(nemd_ctx *c) {
   if (n > 0) {
     const int tb = 256;
     const int nb = (n + tb - 1) / tb;
-    k_wrap<<<nb, tb, 0, c->stream>>>(c->geo, c->q_dev, n, c->relc, c->rank, c->count);
+    k_wrap<<<nb, tb, 0, c->stream>>>(c->geo, c->q_dev, n, c->relc, c->relr, c->rank, c->count);
     c->launches += 1;
   }
   const int64_t tiles = (c->cap_cells + 1 + kScanTile - 1) / kScanTile;
@@ -203,7 +217,7 @@ cudaError_t launch_bin(nemd_ctx *c) {
     int64_t cb = (c->cap_cells + 255) / 256;
     if (cb > 8 * (int64_t)c->sms) cb = 8 * (int64_t)c->sms;
     k_cellsort<<<(int)cb, 256, 0, c->stream>>>(c->geo, c->start, c->perm);
-    k_pack<<<nb, tb, 0, c->stream>>>(c->geo, c->relc, c->perm, c->pos4, c->cell_sorted, n);
+    k_pack<<<nb, tb, 0, c->stream>>>(c->geo, c->relc, c->relr, c->perm, c->pos4, c->posr, c->cell_sorted, n);
     c->launches += 3;
   }
   return cudaGetLastError();

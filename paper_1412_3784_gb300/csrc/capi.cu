@@ -65,13 +65,15 @@ double det3(const double *a) {
 int rows_stride_bound(int kfac) { return (2 * kfac + 1) * (2 * kfac + 2); }
 
 int ensure_particles(nemd_ctx *c, int64_t n) {
-  if (n <= c->cap_n) return NEMD_OK;
+  if (n <= c->cap_n && c->partials) return NEMD_OK;
   int64_t cap = n + n / 8 + 1024;
   int r;
   if ((r = grow(c, &c->relc, cap, "relc"))) return r;
   if ((r = grow(c, &c->rank, cap, "rank"))) return r;
   if ((r = grow(c, &c->perm, cap, "perm"))) return r;
   if ((r = grow(c, &c->pos4, cap, "pos4"))) return r;
+  if ((r = grow(c, &c->relr, cap, "relr"))) return r;
+  if ((r = grow(c, &c->posr, cap, "posr"))) return r;
   if ((r = grow(c, &c->cell_sorted, cap, "cell_sorted"))) return r;
   int64_t nblocks = (cap + 31) / 32 + 1;  // enough for any block size >= 32
   if ((r = grow(c, &c->partials, nblocks * nemd::kPartials, "partials"))) return r;
@@ -180,7 +182,7 @@ int nemd_destroy(nemd_ctx *c) {
   if (!c) return NEMD_OK;
   cudaSetDevice(c->device);
   if (c->stream || true) cudaStreamSynchronize(c->stream);
-  void *ptrs[] = {c->geo,  c->q_copy, c->relc,     c->rank,     c->count,    c->start,
+  void *ptrs[] = {c->geo,  c->q_copy, c->relc,     c->relr, c->posr, c->rank,     c->count,    c->start,
                   c->block_sums, c->perm, c->pos4, c->cell_sorted, c->rows, c->rowcnt,
                   c->partials, c->uw_out, c->f_dev, c->pair_buf, c->pair_count, c->counters};
   for (void *p : ptrs)

@@ -44,6 +44,7 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[kPartials], doubl
 
 template <int NT, bool RECORD, bool PRECISE>
 __global__ void __launch_bounds__(NT) k_force_plain(const Geo *__restrict__ g, const float4 *__restrict__ pos,
+                                                    const float4 *__restrict__ posr,
                                                     const int *__restrict__ cell_sorted,
                                                     const int *__restrict__ start, const Row *__restrict__ rows,
                                                     const int *__restrict__ rowcnt, const double *__restrict__ q,
@@ -67,12 +68,16 @@ __global__ void __launch_bounds__(NT) k_force_plain(const Geo *__restrict__ g, c
     const int nr = rowcnt[cls];
     const float lo = g->rc2_lo, hi = g->rc2_hi;
     const float sx = g->step[0], sy = g->step[1], sz = g->step[2];
+    const float srx = g->step_r[0], sry = g->step_r[1], srz = g->step_r[2];
     const bool is_do = (g->variant == NEMD_DO);
+    const float4 pir = posr[k];
     int mi[3] = {0, 0, 0};
-    if ((RECORD || PRECISE) && is_do) brick_image(g, q, oi, mi);
+    bool have_mi = false;
     for (int r = 0; r < nr; r++) {
       const Row R = rw[r];
+      // t = x_i - o exactly (multiples of the quantum); T = residual of x_i - o
       float tx = pi.x - R.ox, ty = pi.y - R.oy, tz = pi.z - R.oz;
+      float Tx = pir.x - R.rx, Ty = pir.y - R.ry, Tz = pir.z - R.rz;
       const int jxu = ix + R.dxlo;
       int kx = floordiv_dev(jxu, l1);
       int jx = jxu - kx * l1;
@@ -82,13 +87,17 @@ __global__ void __launch_bounds__(NT) k_force_plain(const Geo *__restrict__ g, c
         ncand += e - b;
         for (int j = b; j < e; j++) {
           const float4 pj = pos[j];
-          const float dx = pj.x - tx, dy = pj.y - ty, dz = pj.z - tz;
+          float dx = pj.x - tx, dy = pj.y - ty, dz = pj.z - tz;
           const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
           if (r2 < hi) {
             const int oj = __float_as_int(pj.w);
             if (j == k && kx == 0 && R.ky == 0 && R.kz == 0) continue;
             int n1 = kx, n2 = R.ky, n3 = R.kz;
             if ((RECORD || PRECISE || r2 >= lo) && is_do) {
+              if (!have_mi) {
+                brick_image(g, q, oi, mi);
+                have_mi = true;
+              }
               int mj[3];
               brick_image(g, q, oj, mj);
               n1 += mi[0] - mj[0];
@@ -123,7 +132,14 @@ __global__ void __launch_bounds__(NT) k_force_plain(const Geo *__restrict__ g, c
             if (!accept) continue;
             npair++;
             if (!PRECISE) {
-              const float inv = __frcp_rn(r2);
+              // add back the residuals: d = (x_j - t) + (r_j - T), accurate to a
+              // rounding of d itself
+              const float4 pjr = posr[j];
+              dx += pjr.x - Tx;
+              dy += pjr.y - Ty;
+              dz += pjr.z - Tz;
+              const float r2c = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+              const float inv = __frcp_rn(r2c);
               const float s2 = pp.sig2 * inv;
               const float s6 = s2 * s2 * s2;
               const float fr = pp.eps24 * inv * s6 * (2.0f * s6 - 1.0f);
@@ -140,6 +156,10 @@ __global__ void __launch_bounds__(NT) k_force_plain(const Geo *__restrict__ g, c
               wyz = fmaf(gy, dz, wyz);
             }
             if (RECORD) {
+              if (is_do && !have_mi) {
+                brick_image(g, q, oi, mi);
+                have_mi = true;
+              }
               bool canon = (oi < oj) || (oi == oj && (n1 != 0 ? n1 > 0 : (n2 != 0 ? n2 > 0 : n3 > 0)));
               if (canon) {
                 unsigned long long slot = atomicAdd(pair_count, 1ull);
@@ -158,6 +178,9 @@ __global__ void __launch_bounds__(NT) k_force_plain(const Geo *__restrict__ g, c
         tx -= sx;
         ty -= sy;
         tz -= sz;
+        Tx -= srx;
+        Ty -= sry;
+        Tz -= srz;
         if (++jx == l1) {
           jx = 0;
           kx++;
@@ -285,7 +308,7 @@ static void launch_plain(nemd_ctx *c, int nblocks, Pot pp, float *F) {
   const bool pre = c->precise != 0;
   const int n = (int)c->n;
 #define NEMD_ARGS                                                                                         \
-  c->geo, c->pos4, c->cell_sorted, c->start, c->rows, c->rowcnt, c->q_dev, n, pp, F, c->partials, \
+  c->geo, c->pos4, c->posr, c->cell_sorted, c->start, c->rows, c->rowcnt, c->q_dev, n, pp, F, c->partials, \
       c->pair_buf, c->pair_count, (long long)c->record_cap
   if (rec && pre)
     k_force_plain<NT, true, true><<<nblocks, NT, 0, c->stream>>>(NEMD_ARGS);

@@ -35,6 +35,17 @@ __device__ __forceinline__ void mm3(const double *a, const double *b, double *c,
   __syncwarp();
 }
 
+// Offset split into an exact multiple of the quantum q and a float32 residual.
+__device__ __forceinline__ void set_offset(Row &r, double ox, double oy, double oz, double q) {
+  double qx = rint(ox / q) * q, qy = rint(oy / q) * q, qz = rint(oz / q) * q;
+  r.ox = (float)qx;
+  r.oy = (float)qy;
+  r.oz = (float)qz;
+  r.rx = (float)(ox - qx);
+  r.ry = (float)(oy - qy);
+  r.rz = (float)(oz - qz);
+}
+
 }  // namespace
 
 // One warp.  validate != 0: compute exp(tau_in A) L0 only (for the KR check).
@@ -227,7 +238,6 @@ __global__ void k_grid(Geo *g, GridIn in) {
       g->Ginv_scale[a] = (double)nc[a];
       g->w[a] = 0.0;
       reach[a] = kf;
-      step[a] = (float)Gd[3 * a + 0];
     }
     maxrows = (2 * kf + 1) * (2 * kf + 1);
     for (int k = 0; k < 9; k++) g->Qf[k] = (k % 4 == 0) ? 1.0f : 0.0f;
@@ -241,9 +251,6 @@ __global__ void k_grid(Geo *g, GridIn in) {
       Gd[4 * a] = w;
       reach[a] = (int)ceil(rce / w);
     }
-    step[0] = (float)g->w[0];
-    step[1] = 0.0f;
-    step[2] = 0.0f;
     maxrows = (2 * reach[2] + 1) * (2 * reach[1] + 2);
     for (int k = 0; k < 9; k++) g->Qf[k] = (float)Ri[k];
   }
@@ -255,7 +262,6 @@ __global__ void k_grid(Geo *g, GridIn in) {
   for (int a = 0; a < 3; a++) {
     g->nc[a] = nc[a];
     g->reach[a] = reach[a];
-    g->step[a] = step[a];
   }
   g->ncells = err ? 0 : (int)ncells;
   g->maxrows = maxrows;
@@ -263,22 +269,38 @@ __global__ void k_grid(Geo *g, GridIn in) {
     g->G[k] = Gd[k];
     g->Gf[k] = (float)Gd[k];
   }
-  // float32 guard band on r^2: bound the float32 error of the cell-relative
-  // displacement (each of rel_i, offset, t, rel_j, d rounded once) and of r^2
-  double diam = 0.0;
-  for (int b = 0; b < 3; b++)
-    diam += sqrt(Gd[b] * Gd[b] + Gd[3 + b] * Gd[3 + b] + Gd[6 + b] * Gd[6 + b]);
-  int rmax = max(reach[0], max(reach[1], reach[2]));
-  double omax = (double)(rmax + 2) * diam;
+  // Quantum: float32 positions and offsets are stored as exact multiples of a
+  // power of two q, chosen so that every intermediate (|rel| + |offset| bounded
+  // by M) has at most 24 significant bits.  Then t = x_i - o and d = x_j - t are
+  // exact in float32; only the residuals (each < q/2, carried separately) are
+  // missing from the distance test, and they are added back for accepted pairs.
+  double gmax = 0.0;
+  for (int a = 0; a < 3; a++) gmax = fmax(gmax, fabs(Gd[3 * a]) + fabs(Gd[3 * a + 1]) + fabs(Gd[3 * a + 2]));
+  const int rmax = max(reach[0], max(reach[1], reach[2]));
+  const double M = (double)(rmax + 3) * gmax + 2.0 * rc;
+  int e2;
+  frexp(M, &e2);             // M < 2^e2
+  const double q = ldexp(1.0, e2 - 23);
+  g->quantum = q;
+  // frame vector between consecutive x-cells: G e_x (dynamic size), (w1, 0, 0) (dynamic offset)
+  for (int a = 0; a < 3; a++) {
+    double sv = Gd[3 * a];
+    double sq = rint(sv / q) * q;
+    step[a] = (float)sq;
+    g->step_r[a] = (float)(sv - sq);
+  }
+  // float32 guard band on r^2: the test misses the residuals of rel_i, rel_j and
+  // the accumulated offset residual, at most (2 rmax + 5) q / 2 per component,
+  // plus the float32 rounding of r^2 itself
   const double u = 5.9604644775390625e-08;  // 2^-24
-  double E = u * (4.0 * diam + 2.0 * omax + 2.0 * rc);
-  double band = 2.0 * (2.0 * 1.7320508075688772 * rc * E + 3.0 * E * E + 4.0 * u * rc * rc) + 1e-12 * rc * rc;
+  const double E = (double)(2 * rmax + 5) * 0.5 * q;
+  double band = 2.0 * (2.0 * 1.7320508075688772 * rc * E + 3.0 * E * E + 3.0 * u * rc * rc) + 1e-12 * rc * rc;
+  for (int a = 0; a < 3; a++) g->step[a] = step[a];
   g->band = (float)band;
   g->rc2 = rc * rc;
   g->rc2f = (float)(rc * rc);
   g->rc2_lo = __double2float_rd(rc * rc - band);
   g->rc2_hi = __double2float_ru(rc * rc + band);
-  
 }
 
 // One thread per home (iy, iz): the neighbour rows of that class.
@@ -289,6 +311,7 @@ __global__ void k_stencil(Geo *g, Row *rows, int *rowcnt) {
   const int maxrows = g->maxrows;
   const int variant = g->variant;
   const double rce = g->rc * (1.0 + kMargin);
+  const double q = g->quantum;
   for (int cls = blockIdx.x * blockDim.x + threadIdx.x; cls < ncls; cls += gridDim.x * blockDim.x) {
     const int iy = cls % l2, iz = cls / l2;
     Row *out = rows + (size_t)cls * maxrows;
@@ -302,15 +325,14 @@ __global__ void k_stencil(Geo *g, Row *rows, int *rowcnt) {
           int jy = jyu - ky * l2, jz = jzu - kz * l3;
           double c0 = -(double)K, c1 = dy, c2 = dz;
           Row r;
-          r.ox = (float)(g->G[0] * c0 + g->G[1] * c1 + g->G[2] * c2);
-          r.oy = (float)(g->G[3] * c0 + g->G[4] * c1 + g->G[5] * c2);
-          r.oz = (float)(g->G[6] * c0 + g->G[7] * c1 + g->G[8] * c2);
+          set_offset(r, g->G[0] * c0 + g->G[1] * c1 + g->G[2] * c2, g->G[3] * c0 + g->G[4] * c1 + g->G[5] * c2,
+                     g->G[6] * c0 + g->G[7] * c1 + g->G[8] * c2, q);
           r.cbase = l1 * (jy + l2 * jz);
           r.dxlo = -K;
           r.cnt = 2 * K + 1;
           r.ky = (short)ky;
           r.kz = (short)kz;
-          r.pad = 0;
+          r.pad0 = r.pad1 = 0;
           if (nr < maxrows) out[nr] = r;
           nr++;
         }
@@ -330,15 +352,13 @@ __global__ void k_stencil(Geo *g, Row *rows, int *rowcnt) {
           int xlo = (int)floor((-rce - sx) / w1);
           int xhi = (int)ceil((w1 + rce - sx) / w1) - 1;
           Row r;
-          r.ox = (float)((double)xlo * w1 + sx);
-          r.oy = (float)((double)(jyu - iy) * w2 + yshift);
-          r.oz = (float)((double)(jzu - iz) * w3);
+          set_offset(r, (double)xlo * w1 + sx, (double)(jyu - iy) * w2 + yshift, (double)(jzu - iz) * w3, q);
           r.cbase = l1 * (jy + l2 * jz);
           r.dxlo = xlo;
           r.cnt = xhi - xlo + 1;
           r.ky = (short)ky;
           r.kz = (short)kz;
-          r.pad = 0;
+          r.pad0 = r.pad1 = 0;
           if (nr < maxrows) out[nr] = r;
           nr++;
         }

@@ -49,10 +49,12 @@ struct Geo {
   double Ginv_scale[3];  // DS: c_i ; DO: 1 / w_i
   double w[3];        // DO cell sides
   float Gf[9];
-  float step[3];      // frame vector from one x-cell to the next
+  float step[3];      // frame vector from one x-cell to the next: quantised part
+  float step_r[3];    //   and its residual
   float Qf[9];        // rotation frame -> Cartesian (identity for DS)
   float rc2_lo, rc2_hi, rc2f;
   float band;
+  double quantum;     // float32 coordinates and offsets are multiples of this power of 2
   double vol_ds, vol_do;  // neighbourhood volumes (Sec. 5.1, 5.2) of both variants
   int counts_ds[3], counts_do[3];
   int error;   // this step's error bits
@@ -75,16 +77,18 @@ struct GridIn {
 // One neighbour row of a home (iy, iz) class: the x-cells ix+dxlo ... ix+dxlo+cnt-1
 // of the wrapped row (jy, jz), reached through lattice image (kx, ky, kz) where kx
 // follows from the x wrap.  (ox, oy, oz) is the frame vector from the home cell's
-// corner to the corner of the first cell of the run.
+// centre to the centre of the first cell of the run, split into a part that is an
+// exact multiple of Geo::quantum and a float32 residual (rx, ry, rz).
 struct __align__(16) Row {
   float ox, oy, oz;
   int cbase;   // l1 * (jy + l2 * jz)
+  float rx, ry, rz;
   int dxlo;
   int cnt;
   short ky, kz;
-  int pad;
+  int pad0, pad1;
 };
-static_assert(sizeof(Row) == 32, "Row is 32 bytes");
+static_assert(sizeof(Row) == 48, "Row is 48 bytes");
 
 // Per-block partial sums of the force kernel (float64): U, W (6 symmetric
 // components xx yy zz xy xz yz), interacting pairs, candidates, rechecks.
@@ -130,7 +134,9 @@ struct nemd_ctx {
   int *start;            // cap_cells + 1
   int *block_sums;
   int *perm;
-  float4 *pos4;          // sorted: rel position + original index (bits)
+  float4 *relr;          // per input particle: residual of the quantised rel position
+  float4 *pos4;          // sorted: quantised rel position + original index (bits)
+  float4 *posr;          // sorted: residual of the quantised rel position
   int *cell_sorted;
   nemd::Row *rows;
   int *rowcnt;
