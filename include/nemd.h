@@ -182,6 +182,47 @@ int nemd_get_kernel_time(nemd_ctx *ctx, double *ms_total, int64_t *nlaunch);
  * out[5] SM clock kHz reported by the device. */
 int nemd_measure_peaks(int device, double *out);
 
+/* ---- Force evaluation without any memory allocation --------------------
+ *
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot call cudaMalloc -- for example a simulation loop that must never
+ * allocate once it is running, or a plug-in that has no access to the CUDA
+ * allocator of the process hosting it.  It performs one whole force
+ * evaluation (the same kernels as nemd_set_state -> nemd_build_cells ->
+ * nemd_compute_forces, dynamic size / dynamic offset / heuristic variant,
+ * cell factor 1, float32 pair arithmetic) without allocating anything: no
+ * cudaMalloc, no cudaFree, no allocating library routine.
+ *
+ * Scratch: one file-scope device array of NEMD_NOALLOC_SCRATCH_BYTES bytes
+ * (about 10.4 MB), present on every GPU that loads the library until the
+ * process exits.  It holds at most NEMD_NOALLOC_MAX_N particles and
+ * NEMD_NOALLOC_MAX_CELLS cells; larger requests (N, or the cell bound
+ * |det L0| / rc^3 + 1) return NEMD_ERR_CAPACITY before anything is launched.
+ * Every call on a device shares that array and leaves its contents behind
+ * (each call clears what must start at zero), so calls whose work overlaps on
+ * the GPU -- on different streams, or from different threads -- race and give
+ * wrong results: serialise them.
+ *
+ * Set-up: the first call on each device looks up the device address of the
+ * array (cudaGetSymbolAddress, with that device current) and caches it; make
+ * that first call before any stream capture begins.
+ *
+ * Arguments (the current CUDA device is used): A, L0 -- 9 float64 each, host
+ * (the flow is not re-validated: pass one that nemd_set_flow accepts; T is the
+ * KR period, t the time); q -- N x 3 float64, DEVICE; variant -- NEMD_DS,
+ * NEMD_DO or NEMD_AUTO_HEURISTIC; rc, kind, eps, sigma, shift -- as in
+ * nemd_build_cells / nemd_set_potential; F -- N x 3 float32, DEVICE; UW --
+ * 10 float64, DEVICE, receives U then W (row-major); status -- optional int,
+ * DEVICE, receives the deferred device error bits (0 = OK, 1 = box too small,
+ * 2 = non-finite position, 4 = capacity); stream -- a cudaStream_t (NULL =
+ * legacy default stream).  All work is asynchronous on `stream`. */
+#define NEMD_NOALLOC_MAX_N 16384
+#define NEMD_NOALLOC_MAX_CELLS 16384
+#define NEMD_NOALLOC_SCRATCH_BYTES 10891776
+int nemd_forces_noalloc(const double A[9], const double L0[9], double T, double t, const double *q, int64_t n,
+                        int variant, double rc, int kind, double eps, double sigma, int shift, float *F, double *UW,
+                        int *status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

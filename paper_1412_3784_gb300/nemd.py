@@ -35,7 +35,9 @@ NEMD_OPT_TIMING = 6
 EXPORTED = ["nemd_create", "nemd_destroy", "nemd_set_flow", "nemd_set_potential", "nemd_set_state",
             "nemd_build_cells", "nemd_compute_forces", "nemd_sync", "nemd_last_error",
             "nemd_set_option", "nemd_get_lattice", "nemd_get_stats", "nemd_get_pairs",
-            "nemd_get_kernel_time", "nemd_measure_peaks"]
+            "nemd_get_kernel_time", "nemd_measure_peaks", "nemd_forces_noalloc"]
+NEMD_NOALLOC_MAX_N = 16384
+NEMD_NOALLOC_MAX_CELLS = 16384
 
 
 class nemd_stats(ctypes.Structure):
@@ -64,6 +66,9 @@ _sig = {
     "nemd_get_kernel_time": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
                              ctypes.c_int),
     "nemd_measure_peaks": ([ctypes.c_int, _vp], ctypes.c_int),
+    "nemd_forces_noalloc": ([_vp, _vp, ctypes.c_double, ctypes.c_double, _vp, ctypes.c_int64, ctypes.c_int,
+                             ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                             _vp, _vp, _vp, _vp], ctypes.c_int),
 }
 for _name, (_args, _res) in _sig.items():
     _f = getattr(_lib, _name)
