@@ -55,6 +55,9 @@ def parse():
     p.add_argument("--strains", type=int, default=0, help="strains per step (default: the workload's)")
     p.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle sample")
     p.add_argument("--e2e-strains", type=int, default=16)
+    p.add_argument("--kernel", type=int, default=1, help="force kernel of the tuned form (0 plain, 1 grouped)")
+    p.add_argument("--group", type=int, default=16, help="lanes per group of the grouped kernel")
+    p.add_argument("--kfac", type=int, default=1, help="cell-size factor of the tuned form")
     return p.parse_args()
 
 
@@ -234,8 +237,9 @@ def main():
             ctx.set_option(nemd.NEMD_OPT_KERNEL, 0)
             ctx.set_option(nemd.NEMD_OPT_CELL_FACTOR, 1)
             return nemd.NEMD_DS if kind == "plain_ds" else nemd.NEMD_DO
-        ctx.set_option(nemd.NEMD_OPT_KERNEL, 0)
-        ctx.set_option(nemd.NEMD_OPT_CELL_FACTOR, 1)
+        ctx.set_option(nemd.NEMD_OPT_KERNEL, args.kernel)
+        ctx.set_option(nemd.NEMD_OPT_GROUP, args.group)
+        ctx.set_option(nemd.NEMD_OPT_CELL_FACTOR, args.kfac)
         return nemd.NEMD_AUTO_HEURISTIC
 
     def one_step(variant):
@@ -248,7 +252,7 @@ def main():
     per = {}
     for kind in ("plain_ds", "plain_do", "tuned"):
         variant = configure(kind)
-        pairs, cands, variants = [], [], []
+        pairs, cands, variants, rech = [], [], [], []
         for i in range(S):
             ctx.set_state(q_all[i], ts[i])
             ctx.build_cells(variant, ser.rc)
@@ -258,7 +262,8 @@ def main():
             pairs.append(st["pairs"])
             cands.append(st["candidates"])
             variants.append(st["variant"])
-        per[kind] = {"pairs": pairs, "cands": cands, "variants": variants}
+            rech.append(st["rechecks"])
+        per[kind] = {"pairs": pairs, "cands": cands, "variants": variants, "rechecks": rech}
     pairs_per_step = sum(per["tuned"]["pairs"])
     assert pairs_per_step == sum(per["plain_ds"]["pairs"]) == sum(per["plain_do"]["pairs"])
     # algorithmic FP32 instructions of the tuned step, per the k = 1 stencil of the
@@ -325,7 +330,7 @@ def main():
     achieved = ops_per_launch / avg_launch_s
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
-                "kernel": "k_force_plain", "ops_per_launch": ops_per_launch,
+                "kernel": "k_force_chunk" if args.kernel == 1 else "k_force_plain", "ops_per_launch": ops_per_launch,
                 "avg_launch_ms": avg_launch_s * 1e3,
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x {peak_mhz:.0f} MHz (FP32 instruction lane-ops/s)"}
 
@@ -371,7 +376,9 @@ def main():
                                    f"perturbed FCC N={n}, rho=0.8442, LJ rc=2.5, {S} strains per step "
                                    f"(one period), one force evaluation per strain",
                        "n": n, "strains_per_step": S, "pairs_per_step": pairs_per_step,
-                       "tuned": "per-strain variant by neighbourhood volume, plain kernel, k=1",
+                       "tuned": f"per-strain variant by neighbourhood volume, kernel {args.kernel} "
+                                f"(group {args.group}), cell factor {args.kfac}",
+                       "coarse_band_candidates_per_step": int(sum(per["tuned"]["rechecks"])),
                        "l2": "inputs larger than L2: a distinct 24 MB position array per strain",
                        "parallelism": f"replicas x{world}"},
             "plain": {"dynamic_size_pairs_per_s": plain_ds, "dynamic_offset_pairs_per_s": plain_do,

@@ -78,11 +78,14 @@ typedef enum nemd_option {
                                    and virial to ~1e-13); 0 (default): float32 pair math */
     NEMD_OPT_RECORD_PAIRS = 2,  /* > 0: capacity of the pair record (verification mode)   */
     NEMD_OPT_KERNEL = 3,        /* force kernel: 0 plain (one thread per particle),
-                                   1 tiled (one warp per home cell)                        */
+                                   1 grouped (a group of lanes per chunk of a cell row,
+                                   queued force evaluation; needs N <= 2^21 and k <= 2,
+                                   otherwise the plain kernel runs)                        */
     NEMD_OPT_CELL_FACTOR = 4,   /* k >= 1: cells at least rc/k wide, stencil reach k    */
     NEMD_OPT_BLOCK = 5,         /* threads per block of the force kernel (multiple of 32) */
-    NEMD_OPT_TIMING = 6         /* 1: record CUDA events around every force-kernel launch
+    NEMD_OPT_TIMING = 6,        /* 1: record CUDA events around every force-kernel launch
                                    (read with nemd_get_kernel_time)                       */
+    NEMD_OPT_GROUP = 7          /* lanes per group of the grouped kernel: 4, 8, 16 or 32 */
 } nemd_option;
 
 /* Statistics of the last force evaluation (read with nemd_get_stats). */
@@ -194,7 +197,7 @@ int nemd_measure_peaks(int device, double *out);
  * cudaMalloc, no cudaFree, no allocating library routine.
  *
  * Scratch: one file-scope device array of NEMD_NOALLOC_SCRATCH_BYTES bytes
- * (about 10.4 MB), present on every GPU that loads the library until the
+ * (about 10.6 MB), present on every GPU that loads the library until the
  * process exits.  It holds at most NEMD_NOALLOC_MAX_N particles and
  * NEMD_NOALLOC_MAX_CELLS cells; larger requests (N, or the cell bound
  * |det L0| / rc^3 + 1) return NEMD_ERR_CAPACITY before anything is launched.
@@ -218,7 +221,7 @@ int nemd_measure_peaks(int device, double *out);
  * legacy default stream).  All work is asynchronous on `stream`. */
 #define NEMD_NOALLOC_MAX_N 16384
 #define NEMD_NOALLOC_MAX_CELLS 16384
-#define NEMD_NOALLOC_SCRATCH_BYTES 10891776
+#define NEMD_NOALLOC_SCRATCH_BYTES 11154176
 int nemd_forces_noalloc(const double A[9], const double L0[9], double T, double t, const double *q, int64_t n,
                         int variant, double rc, int kind, double eps, double sigma, int shift, float *F, double *UW,
                         int *status, void *stream);

@@ -75,7 +75,8 @@ int ensure_particles(nemd_ctx *c, int64_t n) {
   if ((r = grow(c, &c->relr, cap, "relr"))) return r;
   if ((r = grow(c, &c->posr, cap, "posr"))) return r;
   if ((r = grow(c, &c->cell_sorted, cap, "cell_sorted"))) return r;
-  int64_t nblocks = (cap + 31) / 32 + 1;  // enough for any block size >= 32
+  if ((r = grow(c, &c->chunks, cap, "chunks"))) return r;
+  int64_t nblocks = (cap + 31) / 32 + 2;  // any block size >= 32, plus the fix-up slot
   if ((r = grow(c, &c->partials, nblocks * nemd::kPartials, "partials"))) return r;
   c->cap_partials = nblocks;
   if (c->q_copy) {
@@ -157,6 +158,9 @@ int nemd_create(nemd_ctx **out, int device, void *stream) {
       cudaMalloc((void **)&c->uw_out, 10 * sizeof(double)) != cudaSuccess ||
       cudaMalloc((void **)&c->counters, 4 * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMalloc((void **)&c->pair_count, sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMalloc((void **)&c->nchunks, sizeof(int)) != cudaSuccess ||
+      cudaMalloc((void **)&c->nrecheck, sizeof(int)) != cudaSuccess ||
+      cudaMalloc((void **)&c->recheck, sizeof(int4) * nemd::kRecheckCap) != cudaSuccess ||
       cudaMallocHost((void **)&c->h_error, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     nemd_destroy(c);
@@ -173,6 +177,7 @@ int nemd_create(nemd_ctx **out, int device, void *stream) {
   c->kfac = 1;
   c->kernel = 0;
   c->block = 128;
+  c->group = 16;
   snprintf(c->msg, sizeof c->msg, "ok");
   *out = c;
   return NEMD_OK;
@@ -182,7 +187,7 @@ int nemd_destroy(nemd_ctx *c) {
   if (!c) return NEMD_OK;
   cudaSetDevice(c->device);
   if (c->stream || true) cudaStreamSynchronize(c->stream);
-  void *ptrs[] = {c->geo,  c->q_copy, c->relc,     c->relr, c->posr, c->rank,     c->count,    c->start,
+  void *ptrs[] = {c->geo,  c->q_copy, c->relc,     c->relr, c->posr, c->rank,     c->count,    c->start, c->chunks, c->nchunks, c->recheck, c->nrecheck,
                   c->block_sums, c->perm, c->pos4, c->cell_sorted, c->rows, c->rowcnt,
                   c->partials, c->uw_out, c->f_dev, c->pair_buf, c->pair_count, c->counters};
   for (void *p : ptrs)
@@ -397,6 +402,11 @@ int nemd_set_option(nemd_ctx *c, int key, int64_t value) {
     case NEMD_OPT_CELL_FACTOR:
       if (value < 1 || value > nemd::kMaxFactor) return set_err(c, NEMD_ERR_ARG, "cell factor %lld", (long long)value);
       c->kfac = (int)value;
+      return NEMD_OK;
+    case NEMD_OPT_GROUP:
+      if (value != 4 && value != 8 && value != 16 && value != 32)
+        return set_err(c, NEMD_ERR_ARG, "group size %lld (4, 8, 16 or 32)", (long long)value);
+      c->group = (int)value;
       return NEMD_OK;
     case NEMD_OPT_TIMING:
       CK(cudaSetDevice(c->device));

@@ -1,46 +1,23 @@
 // force.cu -- cell-pair force, energy and virial (Sec. 3: only the 27 cells of a
 // neighbourhood are searched; Sec. 5: every force evaluation is preceded by a
-// distance check) and the deterministic float64 reductions.
+// distance check), the plain force kernel, and the deterministic float64
+// reductions shared by every force kernel.
 //
 // Plain kernel: one thread per particle in cell order.  The thread walks the
 // rows of its home cell's stencil (Sec. 4.1: 27 cells; Sec. 4.2: 27-36 cells),
 // each row a run of consecutive x-cells, and tests every particle of every
-// cell with a float32 distance check in cell-relative coordinates.  Candidates
-// whose float32 r^2 lies within the guard band of rc^2 are decided by the
-// canonical float64 displacement, so the pair set is exactly the definition's.
-// Full neighbourhoods: each unordered pair is met from both sides, every
-// particle's force is accumulated by its own thread, and U, W are halved.
+// cell with a float32 distance check on quantised cell-centred coordinates
+// (exact in float32).  Candidates near the cut-off are re-tested with the
+// residuals added back, and the few still within rounding of rc are decided
+// by the canonical float64 displacement, so the pair set is exactly the
+// definition's.  Full neighbourhoods: each unordered pair is met from both
+// sides, every particle's force is accumulated by its own thread, and U, W are
+// halved.
 #include <math.h>
 
-#include "nemd_device.cuh"
-#include "nemd_internal.cuh"
+#include "force_common.cuh"
 
 namespace nemd {
-
-struct Pot {
-  float eps4, eps24, sig2, ushift;
-  double eps4d, eps24d, sig2d, ushiftd;
-};
-
-template <int NT>
-__device__ __forceinline__ void block_reduce_store(double (&v)[kPartials], double *out) {
-  __shared__ double sh[NT / 32][kPartials];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < kPartials; k++) {
-    double x = v[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if (lane == 0) sh[warp][k] = x;
-  }
-  __syncthreads();
-  if (threadIdx.x < kPartials) {
-    double x = 0.0;
-#pragma unroll
-    for (int w = 0; w < NT / 32; w++) x += sh[w][threadIdx.x];
-    out[(size_t)blockIdx.x * kPartials + threadIdx.x] = x;
-  }
-}
 
 template <int NT, bool RECORD, bool PRECISE>
 __global__ void __launch_bounds__(NT) k_force_plain(const Geo *__restrict__ g, const float4 *__restrict__ pos,
@@ -50,15 +27,18 @@ __global__ void __launch_bounds__(NT) k_force_plain(const Geo *__restrict__ g, c
                                                     const int *__restrict__ rowcnt, const double *__restrict__ q,
                                                     int n, Pot pp, float *__restrict__ F,
                                                     double *__restrict__ partials, int32_t *__restrict__ pair_buf,
-                                                    unsigned long long *__restrict__ pair_count, long long pair_cap) {
+                                                    unsigned long long *__restrict__ pair_count, long long pair_cap,
+                                                    int4 *__restrict__ rlist, int *__restrict__ rcount,
+                                                    int *__restrict__ err) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  float fx = 0.f, fy = 0.f, fz = 0.f, uu = 0.f;
-  float wxx = 0.f, wyy = 0.f, wzz = 0.f, wxy = 0.f, wxz = 0.f, wyz = 0.f;
-  double dfx = 0, dfy = 0, dfz = 0, du = 0, dwxx = 0, dwyy = 0, dwzz = 0, dwxy = 0, dwxz = 0, dwyz = 0;
-  int npair = 0, ncand = 0, nre = 0;
+  Acc acc;
+  acc.zero();
+  double du = 0, dfx = 0, dfy = 0, dfz = 0, dwxx = 0, dwyy = 0, dwzz = 0, dwxy = 0, dwxz = 0, dwyz = 0;
+  int ncand = 0, nre = 0;
   const bool ok = !(g->error & (ERRB_BOX | ERRB_CAPACITY));
   if (ok && k < n) {
     const float4 pi = pos[k];
+    const float4 pir = posr[k];
     const int oi = __float_as_int(pi.w);
     const int cell = cell_sorted[k];
     const int l1 = g->nc[0], l2 = g->nc[1];
@@ -66,121 +46,73 @@ __global__ void __launch_bounds__(NT) k_force_plain(const Geo *__restrict__ g, c
     const int cls = iy + l2 * iz;
     const Row *rw = rows + (size_t)cls * g->maxrows;
     const int nr = rowcnt[cls];
-    const float lo = g->rc2_lo, hi = g->rc2_hi;
+    const float lo = g->rc2_lo, hi = g->rc2_hi, lo2 = g->rc2_lo2, hi2 = g->rc2_hi2;
     const float sx = g->step[0], sy = g->step[1], sz = g->step[2];
     const float srx = g->step_r[0], sry = g->step_r[1], srz = g->step_r[2];
-    const bool is_do = (g->variant == NEMD_DO);
-    const float4 pir = posr[k];
-    int mi[3] = {0, 0, 0};
-    bool have_mi = false;
     for (int r = 0; r < nr; r++) {
       const Row R = rw[r];
-      // t = x_i - o exactly (multiples of the quantum); T = residual of x_i - o
-      float tx = pi.x - R.ox, ty = pi.y - R.oy, tz = pi.z - R.oz;
-      float Tx = pir.x - R.rx, Ty = pir.y - R.ry, Tz = pir.z - R.rz;
       const int jxu = ix + R.dxlo;
       int kx = floordiv_dev(jxu, l1);
       int jx = jxu - kx * l1;
       for (int m = 0; m < R.cnt; m++) {
+        const int nidx = R.dxlo + m + R.sxi;
+        // t = x_i - o exactly (quantised); T = residual of x_i - o
+        const float tx = sub_offset(pi.x, R.shx, nidx, sx), ty = sub_offset(pi.y, R.shy, nidx, sy),
+                    tz = sub_offset(pi.z, R.shz, nidx, sz);
+        const float Tx = sub_residual(pir.x, R.srx, nidx, srx), Ty = sub_residual(pir.y, R.sry, nidx, sry),
+                    Tz = sub_residual(pir.z, R.srz, nidx, srz);
         const int c = R.cbase + jx;
         const int b = start[c], e = start[c + 1];
         ncand += e - b;
         for (int j = b; j < e; j++) {
           const float4 pj = pos[j];
-          float dx = pj.x - tx, dy = pj.y - ty, dz = pj.z - tz;
+          const float dx = pj.x - tx, dy = pj.y - ty, dz = pj.z - tz;
           const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
           if (r2 < hi) {
-            const int oj = __float_as_int(pj.w);
             if (j == k && kx == 0 && R.ky == 0 && R.kz == 0) continue;
-            int n1 = kx, n2 = R.ky, n3 = R.kz;
-            if ((RECORD || PRECISE || r2 >= lo) && is_do) {
-              if (!have_mi) {
-                brick_image(g, q, oi, mi);
-                have_mi = true;
-              }
-              int mj[3];
-              brick_image(g, q, oj, mj);
-              n1 += mi[0] - mj[0];
-              n2 += mi[1] - mj[1];
-              n3 += mi[2] - mj[2];
-            }
-            double dd[3];
-            bool accept = true;
-            if (PRECISE || r2 >= lo) {
-              double cr2 = canon_r2(g, q, oi, oj, n1, n2, n3, dd);
-              if (r2 >= lo) {
-                nre++;
-                accept = cr2 < g->rc2;
-              }
-              if (PRECISE && accept) {
-                double inv = 1.0 / cr2;
-                double s2 = pp.sig2d * inv;
-                double s6 = s2 * s2 * s2;
-                double fr = pp.eps24d * inv * s6 * (2.0 * s6 - 1.0);
-                du += pp.eps4d * s6 * (s6 - 1.0) - pp.ushiftd;
-                dfx -= fr * dd[0];
-                dfy -= fr * dd[1];
-                dfz -= fr * dd[2];
-                dwxx += fr * dd[0] * dd[0];
-                dwyy += fr * dd[1] * dd[1];
-                dwzz += fr * dd[2] * dd[2];
-                dwxy += fr * dd[0] * dd[1];
-                dwxz += fr * dd[0] * dd[2];
-                dwyz += fr * dd[1] * dd[2];
+            const int oj = __float_as_int(pj.w);
+            // residuals added back: d to one rounding of d itself
+            const float4 pjr = posr[j];
+            const float cx = dx + (pjr.x - Tx), cy = dy + (pjr.y - Ty), cz = dz + (pjr.z - Tz);
+            bool accept = r2 < lo;
+            if (!accept) {
+              nre++;
+              const float r2c = fmaf(cz, cz, fmaf(cy, cy, cx * cx));
+              accept = r2c < lo2;
+              if (!accept && r2c < hi2) {
+                if (RECORD || PRECISE)
+                  accept = guard_band_accept(g, q, oi, oj, kx, R.ky, R.kz);
+                else
+                  defer_recheck(rlist, rcount, err, k, j, kx, R.ky, R.kz);  // decided by the fix-up pass
               }
             }
             if (!accept) continue;
-            npair++;
-            if (!PRECISE) {
-              // add back the residuals: d = (x_j - t) + (r_j - T), accurate to a
-              // rounding of d itself
-              const float4 pjr = posr[j];
-              dx += pjr.x - Tx;
-              dy += pjr.y - Ty;
-              dz += pjr.z - Tz;
-              const float r2c = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-              const float inv = __frcp_rn(r2c);
-              const float s2 = pp.sig2 * inv;
-              const float s6 = s2 * s2 * s2;
-              const float fr = pp.eps24 * inv * s6 * (2.0f * s6 - 1.0f);
-              uu += fmaf(pp.eps4 * s6, s6 - 1.0f, -pp.ushift);
-              const float gx = fr * dx, gy = fr * dy, gz = fr * dz;
-              fx -= gx;
-              fy -= gy;
-              fz -= gz;
-              wxx = fmaf(gx, dx, wxx);
-              wyy = fmaf(gy, dy, wyy);
-              wzz = fmaf(gz, dz, wzz);
-              wxy = fmaf(gx, dy, wxy);
-              wxz = fmaf(gx, dz, wxz);
-              wyz = fmaf(gy, dz, wyz);
+            if (PRECISE) {
+              int nn[3];
+              pair_image(g, q, oi, oj, kx, R.ky, R.kz, nn);
+              double dd[3];
+              const double cr2 = canon_r2(g, q, oi, oj, nn[0], nn[1], nn[2], dd);
+              const double inv = 1.0 / cr2;
+              const double s2 = pp.sig2d * inv;
+              const double s6 = s2 * s2 * s2;
+              const double fr = pp.eps24d * inv * s6 * (2.0 * s6 - 1.0);
+              du += pp.eps4d * s6 * (s6 - 1.0) - pp.ushiftd;
+              dfx -= fr * dd[0];
+              dfy -= fr * dd[1];
+              dfz -= fr * dd[2];
+              dwxx += fr * dd[0] * dd[0];
+              dwyy += fr * dd[1] * dd[1];
+              dwzz += fr * dd[2] * dd[2];
+              dwxy += fr * dd[0] * dd[1];
+              dwxz += fr * dd[0] * dd[2];
+              dwyz += fr * dd[1] * dd[2];
+              acc.npair++;
+            } else {
+              acc.add(pp, cx, cy, cz);
             }
-            if (RECORD) {
-              if (is_do && !have_mi) {
-                brick_image(g, q, oi, mi);
-                have_mi = true;
-              }
-              bool canon = (oi < oj) || (oi == oj && (n1 != 0 ? n1 > 0 : (n2 != 0 ? n2 > 0 : n3 > 0)));
-              if (canon) {
-                unsigned long long slot = atomicAdd(pair_count, 1ull);
-                if ((long long)slot < pair_cap) {
-                  int32_t *p = pair_buf + 5 * slot;
-                  p[0] = oi;
-                  p[1] = oj;
-                  p[2] = n1;
-                  p[3] = n2;
-                  p[4] = n3;
-                }
-              }
-            }
+            if (RECORD) record_pair(g, q, oi, oj, kx, R.ky, R.kz, pair_buf, pair_count, pair_cap);
           }
         }
-        tx -= sx;
-        ty -= sy;
-        tz -= sz;
-        Tx -= srx;
-        Ty -= sry;
-        Tz -= srz;
         if (++jx == l1) {
           jx = 0;
           kx++;
@@ -195,9 +127,9 @@ __global__ void __launch_bounds__(NT) k_force_plain(const Geo *__restrict__ g, c
         oz = (float)dfz;
       } else {
         const float *Qm = g->Qf;
-        ox = Qm[0] * fx + Qm[1] * fy + Qm[2] * fz;
-        oy = Qm[3] * fx + Qm[4] * fy + Qm[5] * fz;
-        oz = Qm[6] * fx + Qm[7] * fy + Qm[8] * fz;
+        ox = Qm[0] * acc.fx + Qm[1] * acc.fy + Qm[2] * acc.fz;
+        oy = Qm[3] * acc.fx + Qm[4] * acc.fy + Qm[5] * acc.fz;
+        oz = Qm[6] * acc.fx + Qm[7] * acc.fy + Qm[8] * acc.fz;
       }
       F[3 * (size_t)oi] = ox;
       F[3 * (size_t)oi + 1] = oy;
@@ -214,18 +146,70 @@ __global__ void __launch_bounds__(NT) k_force_plain(const Geo *__restrict__ g, c
     v[5] = dwxz;
     v[6] = dwyz;
   } else {
-    v[0] = uu;
-    v[1] = wxx;
-    v[2] = wyy;
-    v[3] = wzz;
-    v[4] = wxy;
-    v[5] = wxz;
-    v[6] = wyz;
+    v[0] = acc.u;
+    v[1] = acc.wxx;
+    v[2] = acc.wyy;
+    v[3] = acc.wzz;
+    v[4] = acc.wxy;
+    v[5] = acc.wxz;
+    v[6] = acc.wyz;
   }
-  v[7] = npair;
+  v[7] = acc.npair;
   v[8] = ncand;
   v[9] = nre;
   block_reduce_store<NT>(v, partials);
+}
+
+// Float64 fix-up of the candidates the force kernels left within float32
+// rounding of rc: the canonical decision (Sec. 2 images, strict r < rc), and for
+// each accepted pair the force on i (added to F, Cartesian), half of u and of
+// r (x) f (the other half comes from the pair's other orientation, which the
+// full neighbourhood also defers), written as one more block of partials in the
+// variant's frame.  One block; runs after the force kernel.
+__global__ void k_recheck_fixup(const Geo *__restrict__ g, const int4 *__restrict__ list,
+                                const int *__restrict__ count, const float4 *__restrict__ pos,
+                                const double *__restrict__ q, Pot pp, float *__restrict__ F,
+                                double *__restrict__ partial_slot) {
+  double v[kPartials];
+  for (int k = 0; k < kPartials; k++) v[k] = 0.0;
+  const int n = min(*count, kRecheckCap);
+  const bool ok = !(g->error & (ERRB_BOX | ERRB_CAPACITY));
+  for (int e = threadIdx.x; ok && e < n; e += blockDim.x) {
+    const int4 it = list[e];
+    const int oi = __float_as_int(pos[it.x].w), oj = __float_as_int(pos[it.y].w);
+    const int ky = (short)(it.w & 0xffff), kz = it.w >> 16;
+    int nn[3];
+    pair_image(g, q, oi, oj, it.z, ky, kz, nn);
+    double d[3];
+    const double r2 = canon_r2(g, q, oi, oj, nn[0], nn[1], nn[2], d);
+    if (!(r2 < g->rc2)) continue;
+    const double inv = 1.0 / r2, s2 = pp.sig2d * inv, s6 = s2 * s2 * s2;
+    const double fr = pp.eps24d * inv * s6 * (2.0 * s6 - 1.0);
+    if (F)
+      for (int a = 0; a < 3; a++) atomicAdd(&F[3 * (size_t)oi + a], (float)(-fr * d[a]));
+    // frame components: W_frame = Q^T (d d^T) Q fr, d_frame = Q^T d
+    double df[3];
+    for (int a = 0; a < 3; a++) df[a] = g->Q[a] * d[0] + g->Q[3 + a] * d[1] + g->Q[6 + a] * d[2];
+    if (g->variant != NEMD_DO)
+      for (int a = 0; a < 3; a++) df[a] = d[a];
+    v[0] += pp.eps4d * s6 * (s6 - 1.0) - pp.ushiftd;
+    v[1] += fr * df[0] * df[0];
+    v[2] += fr * df[1] * df[1];
+    v[3] += fr * df[2] * df[2];
+    v[4] += fr * df[0] * df[1];
+    v[5] += fr * df[0] * df[2];
+    v[6] += fr * df[1] * df[2];
+    v[7] += 1.0;
+  }
+  __shared__ double sh[256][kPartials];
+  for (int k = 0; k < kPartials; k++) sh[threadIdx.x][k] = v[k];
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s)
+      for (int k = 0; k < kPartials; k++) sh[threadIdx.x][k] += sh[threadIdx.x + s][k];
+    __syncthreads();
+  }
+  if (threadIdx.x < kPartials) partial_slot[threadIdx.x] = (threadIdx.x < 8) ? sh[0][threadIdx.x] : 0.0;
 }
 
 // Single block: sums the per-block partials in a fixed order (deterministic),
@@ -282,7 +266,7 @@ __global__ void k_reduce_final(Geo *__restrict__ g, const double *__restrict__ p
   }
 }
 
-static Pot make_pot(const nemd_ctx *c) {
+Pot make_pot(const nemd_ctx *c) {
   Pot p;
   double eps = c->eps, sig = c->sigma, rc = c->rc;
   double ush = 0.0;
@@ -302,14 +286,20 @@ static Pot make_pot(const nemd_ctx *c) {
   return p;
 }
 
+cudaError_t launch_reduce(nemd_ctx *c, int nblocks, int frame_is_cartesian, double *UW_dev) {
+  k_reduce_final<<<1, 256, 0, c->stream>>>(c->geo, c->partials, nblocks, frame_is_cartesian, UW_dev, c->counters);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
 template <int NT>
 static void launch_plain(nemd_ctx *c, int nblocks, Pot pp, float *F) {
   const bool rec = c->record_cap > 0;
   const bool pre = c->precise != 0;
   const int n = (int)c->n;
-#define NEMD_ARGS                                                                                         \
+#define NEMD_ARGS                                                                                               \
   c->geo, c->pos4, c->posr, c->cell_sorted, c->start, c->rows, c->rowcnt, c->q_dev, n, pp, F, c->partials, \
-      c->pair_buf, c->pair_count, (long long)c->record_cap
+      c->pair_buf, c->pair_count, (long long)c->record_cap, c->recheck, c->nrecheck, &c->geo->error
   if (rec && pre)
     k_force_plain<NT, true, true><<<nblocks, NT, 0, c->stream>>>(NEMD_ARGS);
   else if (rec)
@@ -319,27 +309,45 @@ static void launch_plain(nemd_ctx *c, int nblocks, Pot pp, float *F) {
   else
     k_force_plain<NT, false, false><<<nblocks, NT, 0, c->stream>>>(NEMD_ARGS);
 #undef NEMD_ARGS
+  c->launches += 1;
 }
 
 cudaError_t launch_forces(nemd_ctx *c, float *F_dev, double *UW_dev) {
-  const Pot pp = make_pot(c);
-  const int NT = 128;
-  int nblocks = (int)((c->n + NT - 1) / NT);
-  if (nblocks < 1) nblocks = 1;
   if (c->record_cap > 0) {
     cudaError_t e = cudaMemsetAsync(c->pair_count, 0, sizeof(unsigned long long), c->stream);
     if (e != cudaSuccess) return e;
   }
+  {
+    cudaError_t e = cudaMemsetAsync(c->nrecheck, 0, sizeof(int), c->stream);
+    if (e != cudaSuccess) return e;
+  }
+  // the grouped kernel has no float64 pair path: precise mode runs the plain kernel
+  const bool grouped = c->kernel == 1 && !c->precise && chunk_kernel_applies(c);
+  if (grouped) {
+    cudaError_t e = launch_chunk_build(c);
+    if (e != cudaSuccess) return e;
+  }
   const bool timed = c->timing && c->ev && c->ev_n < c->ev_cap;
   if (timed) cudaEventRecord(c->ev[2 * c->ev_n], c->stream);
-  launch_plain<NT>(c, nblocks, pp, F_dev);
+  int nblocks;
+  if (grouped) {
+    cudaError_t e = launch_force_chunk(c, F_dev, &nblocks);
+    if (e != cudaSuccess) return e;
+  } else {
+    const int NT = 128;
+    nblocks = (int)((c->n + NT - 1) / NT);
+    if (nblocks < 1) nblocks = 1;
+    launch_plain<NT>(c, nblocks, make_pot(c), F_dev);
+  }
   if (timed) {
     cudaEventRecord(c->ev[2 * c->ev_n + 1], c->stream);
     c->ev_n++;
   }
-  c->launches += 2;
-  k_reduce_final<<<1, 256, 0, c->stream>>>(c->geo, c->partials, nblocks, c->precise ? 1 : 0, UW_dev, c->counters);
-  return cudaGetLastError();
+  // the deferred float64 decisions, as one more block of partials
+  k_recheck_fixup<<<1, 256, 0, c->stream>>>(c->geo, c->recheck, c->nrecheck, c->pos4, c->q_dev, make_pot(c), F_dev,
+                                            c->partials + (size_t)nblocks * kPartials);
+  c->launches += 1;
+  return launch_reduce(c, nblocks + 1, c->precise ? 1 : 0, UW_dev);
 }
 
 }  // namespace nemd

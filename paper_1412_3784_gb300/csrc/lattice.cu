@@ -35,15 +35,15 @@ __device__ __forceinline__ void mm3(const double *a, const double *b, double *c,
   __syncwarp();
 }
 
-// Offset split into an exact multiple of the quantum q and a float32 residual.
-__device__ __forceinline__ void set_offset(Row &r, double ox, double oy, double oz, double q) {
+// Row shift split into an exact multiple of the quantum q and a float32 residual.
+__device__ __forceinline__ void set_shift(Row &r, double ox, double oy, double oz, double q) {
   double qx = rint(ox / q) * q, qy = rint(oy / q) * q, qz = rint(oz / q) * q;
-  r.ox = (float)qx;
-  r.oy = (float)qy;
-  r.oz = (float)qz;
-  r.rx = (float)(ox - qx);
-  r.ry = (float)(oy - qy);
-  r.rz = (float)(oz - qz);
+  r.shx = (float)qx;
+  r.shy = (float)qy;
+  r.shz = (float)qz;
+  r.srx = (float)(ox - qx);
+  r.sry = (float)(oy - qy);
+  r.srz = (float)(oz - qz);
 }
 
 }  // namespace
@@ -277,7 +277,8 @@ __global__ void k_grid(Geo *g, GridIn in) {
   double gmax = 0.0;
   for (int a = 0; a < 3; a++) gmax = fmax(gmax, fabs(Gd[3 * a]) + fabs(Gd[3 * a + 1]) + fabs(Gd[3 * a + 2]));
   const int rmax = max(reach[0], max(reach[1], reach[2]));
-  const double M = (double)(rmax + 3) * gmax + 2.0 * rc;
+  // offsets reach (rmax + 2 + span) cells, positions half a cell, distances rc
+  const double M = (double)(rmax + 4 + kMaxSpan) * gmax + 2.0 * rc;
   int e2;
   frexp(M, &e2);             // M < 2^e2
   const double q = ldexp(1.0, e2 - 23);
@@ -289,17 +290,23 @@ __global__ void k_grid(Geo *g, GridIn in) {
     step[a] = (float)sq;
     g->step_r[a] = (float)(sv - sq);
   }
-  // float32 guard band on r^2: the test misses the residuals of rel_i, rel_j and
-  // the accumulated offset residual, at most (2 rmax + 5) q / 2 per component,
-  // plus the float32 rounding of r^2 itself
+  // Coarse band (quantised test): the omitted residuals of x_i, x_j, the row
+  // shift and (dx + sxi) steps, at most (rmax + 6 + span) q / 2 per component,
+  // plus the rounding of r^2.  Fine band (test with residuals added back): one
+  // rounding of each corrected component and of r^2.
   const double u = 5.9604644775390625e-08;  // 2^-24
-  const double E = (double)(2 * rmax + 5) * 0.5 * q;
-  double band = 2.0 * (2.0 * 1.7320508075688772 * rc * E + 3.0 * E * E + 3.0 * u * rc * rc) + 1e-12 * rc * rc;
+  const double E = (double)(rmax + 6 + kMaxSpan) * 0.5 * q;
+  const double s3 = 1.7320508075688772;
+  double band = 2.0 * (2.0 * s3 * rc * E + 3.0 * E * E + 3.0 * u * rc * rc) + 1e-12 * rc * rc;
+  const double E2 = 2.0 * u * (rc + q);
+  double band2 = 2.0 * (2.0 * s3 * rc * E2 + 3.0 * E2 * E2 + 3.0 * u * rc * rc) + 1e-12 * rc * rc;
   for (int a = 0; a < 3; a++) g->step[a] = step[a];
   g->band = (float)band;
   g->rc2 = rc * rc;
   g->rc2f = (float)(rc * rc);
   g->rc2_lo = __double2float_rd(rc * rc - band);
+  g->rc2_lo2 = __double2float_rd(rc * rc - band2);
+  g->rc2_hi2 = __double2float_ru(rc * rc + band2);
   g->rc2_hi = __double2float_ru(rc * rc + band);
 }
 
@@ -323,16 +330,16 @@ __global__ void k_stencil(Geo *g, Row *rows, int *rowcnt) {
           int jyu = iy + dy, jzu = iz + dz;
           int ky = floordiv_i(jyu, l2), kz = floordiv_i(jzu, l3);
           int jy = jyu - ky * l2, jz = jzu - kz * l3;
-          double c0 = -(double)K, c1 = dy, c2 = dz;
+          const double c1 = dy, c2 = dz;
           Row r;
-          set_offset(r, g->G[0] * c0 + g->G[1] * c1 + g->G[2] * c2, g->G[3] * c0 + g->G[4] * c1 + g->G[5] * c2,
-                     g->G[6] * c0 + g->G[7] * c1 + g->G[8] * c2, q);
+          set_shift(r, g->G[1] * c1 + g->G[2] * c2, g->G[4] * c1 + g->G[5] * c2, g->G[7] * c1 + g->G[8] * c2, q);
           r.cbase = l1 * (jy + l2 * jz);
+          r.sxi = 0;
           r.dxlo = -K;
           r.cnt = 2 * K + 1;
           r.ky = (short)ky;
           r.kz = (short)kz;
-          r.pad0 = r.pad1 = 0;
+          r.pad1 = 0;
           if (nr < maxrows) out[nr] = r;
           nr++;
         }
@@ -352,13 +359,15 @@ __global__ void k_stencil(Geo *g, Row *rows, int *rowcnt) {
           int xlo = (int)floor((-rce - sx) / w1);
           int xhi = (int)ceil((w1 + rce - sx) / w1) - 1;
           Row r;
-          set_offset(r, (double)xlo * w1 + sx, (double)(jyu - iy) * w2 + yshift, (double)(jzu - iz) * w3, q);
+          const double sxi = rint(sx / w1);
+          set_shift(r, sx - sxi * w1, (double)(jyu - iy) * w2 + yshift, (double)(jzu - iz) * w3, q);
           r.cbase = l1 * (jy + l2 * jz);
+          r.sxi = (int)sxi;
           r.dxlo = xlo;
           r.cnt = xhi - xlo + 1;
           r.ky = (short)ky;
           r.kz = (short)kz;
-          r.pad0 = r.pad1 = 0;
+          r.pad1 = 0;
           if (nr < maxrows) out[nr] = r;
           nr++;
         }

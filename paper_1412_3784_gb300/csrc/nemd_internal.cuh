@@ -17,6 +17,8 @@ namespace nemd {
 // rounding of positions can never drop a pair.
 constexpr double kMargin = 1e-12;
 constexpr int kMaxFactor = 3;          // largest cell-size factor k
+constexpr int kMaxSpan = 8;            // largest x-span (cells) of a chunk of the grouped kernel
+constexpr int kRecheckCap = 1 << 14;   // fine-band candidates per evaluation (~1e-7 of candidates)
 constexpr int kMaxRowsPerClass = 64;   // (2k+2)^2 for k = 3
 
 // Device error word bits (deferred errors).
@@ -52,7 +54,8 @@ struct Geo {
   float step[3];      // frame vector from one x-cell to the next: quantised part
   float step_r[3];    //   and its residual
   float Qf[9];        // rotation frame -> Cartesian (identity for DS)
-  float rc2_lo, rc2_hi, rc2f;
+  float rc2_lo, rc2_hi, rc2f;   // coarse band: quantised test without residuals
+  float rc2_lo2, rc2_hi2;       // fine band: float32 test with residuals added back
   float band;
   double quantum;     // float32 coordinates and offsets are multiples of this power of 2
   double vol_ds, vol_do;  // neighbourhood volumes (Sec. 5.1, 5.2) of both variants
@@ -76,17 +79,21 @@ struct GridIn {
 
 // One neighbour row of a home (iy, iz) class: the x-cells ix+dxlo ... ix+dxlo+cnt-1
 // of the wrapped row (jy, jz), reached through lattice image (kx, ky, kz) where kx
-// follows from the x wrap.  (ox, oy, oz) is the frame vector from the home cell's
-// centre to the centre of the first cell of the run, split into a part that is an
-// exact multiple of Geo::quantum and a float32 residual (rx, ry, rz).
+// follows from the x wrap.  The frame vector from the home cell's centre to the
+// centre of the cell ix+dx of this row is  shift + (dx + sxi) * step  (step =
+// Geo::step); shift is split into an exact multiple of Geo::quantum (shx, shy,
+// shz) and a float32 residual (srx, sry, srz), and kept within half a cell
+// along x by the integer sxi.  The home cell's own row has shift 0 and sxi 0,
+// so the offset of the home cell itself is exactly 0.
 struct __align__(16) Row {
-  float ox, oy, oz;
+  float shx, shy, shz;
   int cbase;   // l1 * (jy + l2 * jz)
-  float rx, ry, rz;
+  float srx, sry, srz;
   int dxlo;
   int cnt;
   short ky, kz;
-  int pad0, pad1;
+  int sxi;
+  int pad1;
 };
 static_assert(sizeof(Row) == 48, "Row is 48 bytes");
 
@@ -154,6 +161,13 @@ struct nemd_ctx {
   int64_t launches;
   // host staging
   int *h_error;  // pinned
+  // grouped force kernel
+  int4 *chunks;
+  int *nchunks;
+  int group;
+  // candidates left within float32 rounding of rc, decided by the float64 fix-up
+  int4 *recheck;
+  int *nrecheck;
   char msg[512];
   double last_stats_band;
 };
@@ -166,5 +180,10 @@ cudaError_t launch_grid(nemd_ctx *c);
 cudaError_t launch_stencil(nemd_ctx *c);
 cudaError_t launch_bin(nemd_ctx *c);
 cudaError_t launch_forces(nemd_ctx *c, float *F_dev, double *UW_dev);
+// grouped force kernel: chunk list, then the kernel (returns the number of
+// blocks whose partials it wrote)
+bool chunk_kernel_applies(const nemd_ctx *c);
+cudaError_t launch_chunk_build(nemd_ctx *c);
+cudaError_t launch_force_chunk(nemd_ctx *c, float *F_dev, int *nblocks);
 
 }  // namespace nemd

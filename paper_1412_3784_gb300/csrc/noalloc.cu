@@ -28,7 +28,7 @@ constexpr size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign;
 constexpr int64_t kMaxN = NEMD_NOALLOC_MAX_N;
 constexpr int64_t kMaxCells = NEMD_NOALLOC_MAX_CELLS;
 constexpr int64_t kRowStride = 12;  // (2k + 1)(2k + 2) rows per class at cell factor k = 1
-constexpr int64_t kMaxBlocks = (kMaxN + 127) / 128 + 1;
+constexpr int64_t kMaxBlocks = (kMaxN + 127) / 128 + 1;  // force blocks + the fix-up slot
 
 // byte offsets of the buffers inside the array
 constexpr size_t kOffGeo = 0;
@@ -47,7 +47,9 @@ constexpr size_t kOffRows = align_up(kOffRowcnt + 4 * kMaxCells);
 constexpr size_t kOffPartials = align_up(kOffRows + sizeof(nemd::Row) * kRowStride * kMaxCells);
 constexpr size_t kOffCounters = align_up(kOffPartials + 8 * nemd::kPartials * kMaxBlocks);
 constexpr size_t kOffPairCount = align_up(kOffCounters + 8 * 4);
-constexpr size_t kScratchBytes = align_up(kOffPairCount + 8);
+constexpr size_t kOffRecheck = align_up(kOffPairCount + 8);
+constexpr size_t kOffNRecheck = align_up(kOffRecheck + sizeof(int4) * nemd::kRecheckCap);
+constexpr size_t kScratchBytes = align_up(kOffNRecheck + 4);
 static_assert(kScratchBytes == NEMD_NOALLOC_SCRATCH_BYTES, "header constant must match the layout");
 
 // The scratch array.  Shared by every call on a device; it keeps the contents
@@ -158,6 +160,8 @@ extern "C" int nemd_forces_noalloc(const double A[9], const double L0[9], double
   c.cap_partials = kMaxBlocks;
   c.counters = (unsigned long long *)(base + kOffCounters);
   c.pair_count = (unsigned long long *)(base + kOffPairCount);
+  c.recheck = (int4 *)(base + kOffRecheck);
+  c.nrecheck = (int *)(base + kOffNRecheck);
 
   // the geometry record (including its error words) starts from zero every call;
   // the cell counts are cleared by the binning step itself

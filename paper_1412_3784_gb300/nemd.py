@@ -31,6 +31,7 @@ NEMD_DS, NEMD_DO, NEMD_AUTO_HEURISTIC, NEMD_AUTO_LEARNED = 0, 1, 2, 3
 NEMD_LJ, NEMD_WCA = 0, 1
 NEMD_OPT_PRECISE, NEMD_OPT_RECORD_PAIRS, NEMD_OPT_KERNEL, NEMD_OPT_CELL_FACTOR, NEMD_OPT_BLOCK = 1, 2, 3, 4, 5
 NEMD_OPT_TIMING = 6
+NEMD_OPT_GROUP = 7
 
 EXPORTED = ["nemd_create", "nemd_destroy", "nemd_set_flow", "nemd_set_potential", "nemd_set_state",
             "nemd_build_cells", "nemd_compute_forces", "nemd_sync", "nemd_last_error",

@@ -15,7 +15,7 @@ def make_ctx(w, nemd, torch):
     return ctx
 
 
-def run(w, variant, *, precise=False, record=False, kfac=1, ctx=None, q=None, kernel=0):
+def run(w, variant, *, precise=False, record=False, kfac=1, ctx=None, q=None, kernel=(0, 16)):
     """Evaluate workload w on cuda:0; returns dict with F (N,3) float64, U, W, stats, pairs."""
     import torch
 
@@ -27,7 +27,9 @@ def run(w, variant, *, precise=False, record=False, kfac=1, ctx=None, q=None, ke
     dev = torch.device("cuda:0")
     ctx.set_option(nemd.NEMD_OPT_PRECISE, 1 if precise else 0)
     ctx.set_option(nemd.NEMD_OPT_CELL_FACTOR, kfac)
-    ctx.set_option(nemd.NEMD_OPT_KERNEL, kernel)
+    kern, group = kernel if isinstance(kernel, tuple) else (kernel, 16)
+    ctx.set_option(nemd.NEMD_OPT_KERNEL, kern)
+    ctx.set_option(nemd.NEMD_OPT_GROUP, group)
     cap = 0
     if record:
         cap = int(w.n * 40 + 1000)

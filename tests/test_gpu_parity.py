@@ -33,12 +33,15 @@ def keys(p):
     return oracle.canonical_pair_keys(p)
 
 
-def check_against(w, variant, ref, *, pairs=True, precise=True, kfac=1):
+KERNELS = [(0, 16), (1, 16), (1, 4), (1, 32)]   # (kernel, group size): plain, grouped
+
+
+def check_against(w, variant, ref, *, pairs=True, precise=True, kfac=1, kernel=(0, 16)):
     if pairs:
-        g = run(w, variant, record=True, kfac=kfac)
+        g = run(w, variant, record=True, kfac=kfac, kernel=kernel)
         assert g["stats"]["pairs"] == ref.npairs
         assert np.array_equal(keys(g["pairs"]), keys(ref.pairs)), "pair sets differ"
-    g = run(w, variant, kfac=kfac)
+    g = run(w, variant, kfac=kfac, kernel=kernel)
     assert g["stats"]["pairs"] == ref.npairs
     assert force_err(g["F"], ref.F) <= F_TOL
     assert rel(g["U"], ref.U) <= UW_TOL_FAST
@@ -74,45 +77,50 @@ def test_lattice_matches_oracle(M):
 
 # ------------------------------------------------------------- config 0 ----
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("variant", [DS, DO])
-def test_config0_wca_equilibrium(variant):
+def test_config0_wca_equilibrium(variant, kernel):
     w = W.config_equilibrium_wca()
     ref = oracle.evaluate(w, "brute", want_pairs=True)
-    check_against(w, variant, ref)
+    check_against(w, variant, ref, kernel=kernel)
 
 
 # ------------------------------------------------------ flows at strains ----
 
+@pytest.mark.parametrize("kernel", KERNELS[:2])
 @pytest.mark.parametrize("i", [0, 17, 40, 63])
 @pytest.mark.parametrize("variant", [DS, DO])
-def test_planar_flow_strains(i, variant):
+def test_planar_flow_strains(i, variant, kernel):
     w = W.config_planar(i, k=12)   # 6912 particles, several tiles and a ragged tail
     ref = oracle.evaluate(w, "do" if variant else "ds", want_pairs=True)
-    check_against(w, variant, ref)
+    check_against(w, variant, ref, kernel=kernel)
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("t", [0.3, 0.71, W.NEAR_REMAP_T])
 @pytest.mark.parametrize("variant", [DS, DO])
-def test_general_flow_incl_max_skew(t, variant):
+def test_general_flow_incl_max_skew(t, variant, kernel):
     w = W.config_general(t=t, k=11)   # 5324 particles
     ref = oracle.evaluate(w, "ds", want_pairs=True)
-    check_against(w, variant, ref)
+    check_against(w, variant, ref, kernel=kernel)
 
 
+@pytest.mark.parametrize("kernel", KERNELS[:2])
 @pytest.mark.parametrize("variant", [DS, DO])
-def test_planar_config_full_size(variant):
+def test_planar_config_full_size(variant, kernel):
     """The planar-flow configuration at its full size (N = 32000) at two strains."""
     for i in (9, 50):
         w = W.config_planar(i)
         ref = oracle.evaluate(w, "ds", want_pairs=True)
-        check_against(w, variant, ref, precise=(i == 9))
+        check_against(w, variant, ref, precise=(i == 9), kernel=kernel)
 
 
 # ------------------------------------------------------- tiny / ragged ----
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("seed", range(8))
 @pytest.mark.parametrize("kfac", [1, 2])
-def test_tiny_skewed_boxes(seed, kfac):
+def test_tiny_skewed_boxes(seed, kfac, kernel):
     """Boxes with 1-3 cells per direction: multiple images of one partner."""
     rng = np.random.default_rng(500 + seed)
     rc = 1.3
@@ -121,7 +129,7 @@ def test_tiny_skewed_boxes(seed, kfac):
                    q=q, kind=W.POT_LJ, rc=rc)
     ref = oracle.evaluate(w, "brute", want_pairs=True)
     for variant in (DS, DO):
-        check_against(w, variant, ref, kfac=kfac)
+        check_against(w, variant, ref, kfac=kfac, kernel=kernel)
 
 
 def test_edge_cases_small_n():
@@ -148,21 +156,32 @@ def test_edge_cases_small_n():
         assert abs(g["F"][0, 0] - (-du)) < 1e-5 * abs(du)
 
 
-def test_ragged_counts_and_empty_cells():
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_ragged_counts_and_empty_cells(kernel):
     """A dilute random system: many empty cells, uneven occupancy."""
     w = W.uniform_random(777, 30.0 * np.eye(3), seed=3)
     ref = oracle.evaluate(w, "brute", want_pairs=True)
     for v in (DS, DO):
-        check_against(w, v, ref)
+        check_against(w, v, ref, kernel=kernel)
 
 
 # ------------------------------------------------------------ properties ----
 
-def test_deterministic_repeat():
+@pytest.mark.parametrize("kernel", KERNELS[:2])
+def test_deterministic_repeat(kernel):
     w = W.config_planar(23, k=10)
-    a = run(w, DO)
-    b = run(w, DO)
+    a = run(w, DO, kernel=kernel)
+    b = run(w, DO, kernel=kernel)
     assert np.array_equal(a["F"], b["F"]) and a["U"] == b["U"]
+
+
+def test_kernels_agree_bitwise_on_forces():
+    """Same pair arithmetic and per-particle summation order in both kernels."""
+    w = W.config_general(t=0.55, k=12)
+    a = run(w, DO, kernel=(0, 16))
+    b = run(w, DO, kernel=(1, 16))
+    assert a["stats"]["pairs"] == b["stats"]["pairs"]
+    assert force_err(b["F"], a["F"]) <= 1e-6
 
 
 def test_variants_agree_and_newton():
