@@ -79,13 +79,16 @@ typedef enum nemd_option {
     NEMD_OPT_RECORD_PAIRS = 2,  /* > 0: capacity of the pair record (verification mode)   */
     NEMD_OPT_KERNEL = 3,        /* force kernel: 0 plain (one thread per particle),
                                    1 grouped (a group of lanes per chunk of a cell row,
-                                   queued force evaluation; needs N <= 2^21 and k <= 2,
-                                   otherwise the plain kernel runs)                        */
+                                   queued force evaluation), 2 warp (one chunk of 32 per
+                                   warp, uniform loops); 1 and 2 need N <= 2^21 and
+                                   k <= 2, otherwise the plain kernel runs                 */
     NEMD_OPT_CELL_FACTOR = 4,   /* k >= 1: cells at least rc/k wide, stencil reach k    */
     NEMD_OPT_BLOCK = 5,         /* threads per block of the force kernel (multiple of 32) */
     NEMD_OPT_TIMING = 6,        /* 1: record CUDA events around every force-kernel launch
                                    (read with nemd_get_kernel_time)                       */
-    NEMD_OPT_GROUP = 7          /* lanes per group of the grouped kernel: 4, 8, 16 or 32 */
+    NEMD_OPT_GROUP = 7,         /* lanes per group of the grouped kernel: 4, 8, 16 or 32 */
+    NEMD_OPT_AUTOTUNED = 8      /* 1: nemd_build_cells applies the autotuner's choice for
+                                   the current shape class (when it has one)              */
 } nemd_option;
 
 /* Statistics of the last force evaluation (read with nemd_get_stats). */
@@ -178,6 +181,40 @@ int nemd_get_pairs(nemd_ctx *ctx, int32_t *out, int64_t cap, int64_t *count);
  * are recorded on the context's stream, at most 4096 launches are kept.
  * Synchronises. */
 int nemd_get_kernel_time(nemd_ctx *ctx, double *ms_total, int64_t *nlaunch);
+
+/* ---- Autotuner ------------------------------------------------------------
+ *
+ * The paper has no counterpart (its cells are always at least the cut-off
+ * wide, Sec. 4).  Every candidate configuration -- force kernel (plain, warp,
+ * grouped), lanes per group (4, 8, 16), cell-size factor k (1, 2) -- gives the
+ * same pair set and forces; only the time differs. */
+typedef struct nemd_tune_config {
+    int32_t kernel, group, cell_factor, pad;
+} nemd_tune_config;
+
+typedef struct nemd_tune_entry {
+    nemd_tune_config cfg;
+    double ms;  /* mean time of one nemd_build_cells + nemd_compute_forces */
+} nemd_tune_entry;
+
+/* Time every candidate on the current state (after nemd_set_state): one
+ * untimed then `reps` timed repetitions of nemd_build_cells(variant, rc) +
+ * nemd_compute_forces, with CUDA events on the context's stream.  The times
+ * are added to the cache of the current shape class, (round(log2 N),
+ * round(4 log2(rho rc^3))); the class's best mean over all calls so far is
+ * applied to the context (kernel, group, cell factor) and written to *best
+ * (optional).  times[0..cap) (optional) receives each candidate's mean time of
+ * this call, *ntimes (optional) their number.  Leaves the cells built with the
+ * chosen configuration.  Synchronises. */
+int nemd_autotune(nemd_ctx *ctx, int variant, double rc, int reps, nemd_tune_config *best, nemd_tune_entry *times,
+                  int cap, int *ntimes);
+
+/* Save / load the autotuner cache: "NEMDTUNE", version, class count,
+ * candidate count, the entries, and an FNV-1a 64-bit checksum of all of it.
+ * Load rejects (NEMD_ERR_ARG) a file with another magic, version, candidate
+ * count or checksum and then leaves the cache unchanged. */
+int nemd_tune_save(nemd_ctx *ctx, const char *path);
+int nemd_tune_load(nemd_ctx *ctx, const char *path);
 
 /* Measure device peaks with the library's own kernels (synchronises):
  * out[0] FP32 FMA lane-ops/s, out[1] FP32 paired (f32x2) lane-ops/s,

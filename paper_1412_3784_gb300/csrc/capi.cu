@@ -308,6 +308,7 @@ int nemd_build_cells(nemd_ctx *c, int variant, double rc) {
   if (c->pot_kind == NEMD_WCA && fabs(rc - pow(2.0, 1.0 / 6.0) * c->sigma) > 1e-12 * c->sigma)
     return set_err(c, NEMD_ERR_ARG, "build_cells: WCA needs rc = 2^(1/6) sigma");
   CK(cudaSetDevice(c->device));
+  if (c->autotuned) nemd::tune_apply(c, rc);
   // bound on the number of cells: c1 c2 c3 <= k^3 h1 h2 h3 / rc^3 <= k^3 V / rc^3
   const double V = fabs(det3(c->L0));
   const double k3 = (double)c->kfac * c->kfac * c->kfac;
@@ -396,7 +397,7 @@ int nemd_set_option(nemd_ctx *c, int key, int64_t value) {
       return NEMD_OK;
     }
     case NEMD_OPT_KERNEL:
-      if (value < 0 || value > 1) return set_err(c, NEMD_ERR_ARG, "kernel %lld", (long long)value);
+      if (value < 0 || value > 2) return set_err(c, NEMD_ERR_ARG, "kernel %lld", (long long)value);
       c->kernel = (int)value;
       return NEMD_OK;
     case NEMD_OPT_CELL_FACTOR:
@@ -407,6 +408,9 @@ int nemd_set_option(nemd_ctx *c, int key, int64_t value) {
       if (value != 4 && value != 8 && value != 16 && value != 32)
         return set_err(c, NEMD_ERR_ARG, "group size %lld (4, 8, 16 or 32)", (long long)value);
       c->group = (int)value;
+      return NEMD_OK;
+    case NEMD_OPT_AUTOTUNED:
+      c->autotuned = value ? 1 : 0;
       return NEMD_OK;
     case NEMD_OPT_TIMING:
       CK(cudaSetDevice(c->device));

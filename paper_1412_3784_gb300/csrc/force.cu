@@ -321,16 +321,20 @@ cudaError_t launch_forces(nemd_ctx *c, float *F_dev, double *UW_dev) {
     cudaError_t e = cudaMemsetAsync(c->nrecheck, 0, sizeof(int), c->stream);
     if (e != cudaSuccess) return e;
   }
-  // the grouped kernel has no float64 pair path: precise mode runs the plain kernel
+  // the grouped and warp kernels have no float64 pair path: precise mode runs the plain kernel
   const bool grouped = c->kernel == 1 && !c->precise && chunk_kernel_applies(c);
-  if (grouped) {
-    cudaError_t e = launch_chunk_build(c);
+  const bool warped = c->kernel == 2 && !c->precise && warp_kernel_applies(c);
+  if (grouped || warped) {
+    cudaError_t e = launch_chunk_build(c, warped ? 32 : c->group);
     if (e != cudaSuccess) return e;
   }
   const bool timed = c->timing && c->ev && c->ev_n < c->ev_cap;
   if (timed) cudaEventRecord(c->ev[2 * c->ev_n], c->stream);
   int nblocks;
-  if (grouped) {
+  if (warped) {
+    cudaError_t e = launch_force_warp(c, F_dev, &nblocks);
+    if (e != cudaSuccess) return e;
+  } else if (grouped) {
     cudaError_t e = launch_force_chunk(c, F_dev, &nblocks);
     if (e != cudaSuccess) return e;
   } else {

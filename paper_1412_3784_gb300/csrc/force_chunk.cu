@@ -220,13 +220,13 @@ __global__ void __launch_bounds__(kChunkThreads, 4) k_force_chunk(
   block_reduce_store<kChunkThreads>(v, partials);
 }
 
-cudaError_t launch_chunk_build(nemd_ctx *c) {
+cudaError_t launch_chunk_build(nemd_ctx *c, int gs) {
   cudaError_t e = cudaMemsetAsync(c->nchunks, 0, sizeof(int), c->stream);
   if (e != cudaSuccess) return e;
   int64_t blocks = (c->cap_cells + 127) / 128;
   if (blocks > 4 * (int64_t)c->sms) blocks = 4 * (int64_t)c->sms;
   if (blocks < 1) blocks = 1;
-  k_chunks<<<(int)blocks, 128, 0, c->stream>>>(c->geo, c->start, c->chunks, c->nchunks, c->group);
+  k_chunks<<<(int)blocks, 128, 0, c->stream>>>(c->geo, c->start, c->chunks, c->nchunks, gs);
   c->launches += 1;
   return cudaGetLastError();
 }

@@ -101,7 +101,15 @@ static_assert(sizeof(Row) == 48, "Row is 48 bytes");
 // components xx yy zz xy xz yz), interacting pairs, candidates, rechecks.
 constexpr int kPartials = 10;
 
-struct Buffers;
+// Autotuner cache: per shape class, the summed mean time and the number of
+// measurements of every candidate configuration.
+constexpr int kTuneCandidates = 9;
+constexpr int kMaxTuneClasses = 64;
+struct TuneEntry {
+  int32_t key[2];
+  double sum_ms[kTuneCandidates];
+  int64_t count[kTuneCandidates];
+};
 
 }  // namespace nemd
 
@@ -168,6 +176,10 @@ struct nemd_ctx {
   // candidates left within float32 rounding of rc, decided by the float64 fix-up
   int4 *recheck;
   int *nrecheck;
+  // autotuner cache (host)
+  int autotuned;
+  int ntune;
+  nemd::TuneEntry tune[nemd::kMaxTuneClasses];
   char msg[512];
   double last_stats_band;
 };
@@ -183,7 +195,11 @@ cudaError_t launch_forces(nemd_ctx *c, float *F_dev, double *UW_dev);
 // grouped force kernel: chunk list, then the kernel (returns the number of
 // blocks whose partials it wrote)
 bool chunk_kernel_applies(const nemd_ctx *c);
-cudaError_t launch_chunk_build(nemd_ctx *c);
+bool warp_kernel_applies(const nemd_ctx *c);
+cudaError_t launch_chunk_build(nemd_ctx *c, int gs);
+cudaError_t launch_force_warp(nemd_ctx *c, float *F_dev, int *nblocks);
+// autotuner cache lookup (autotune.cu)
+void tune_apply(nemd_ctx *c, double rc);
 cudaError_t launch_force_chunk(nemd_ctx *c, float *F_dev, int *nblocks);
 
 }  // namespace nemd

@@ -32,11 +32,13 @@ NEMD_LJ, NEMD_WCA = 0, 1
 NEMD_OPT_PRECISE, NEMD_OPT_RECORD_PAIRS, NEMD_OPT_KERNEL, NEMD_OPT_CELL_FACTOR, NEMD_OPT_BLOCK = 1, 2, 3, 4, 5
 NEMD_OPT_TIMING = 6
 NEMD_OPT_GROUP = 7
+NEMD_OPT_AUTOTUNED = 8
 
 EXPORTED = ["nemd_create", "nemd_destroy", "nemd_set_flow", "nemd_set_potential", "nemd_set_state",
             "nemd_build_cells", "nemd_compute_forces", "nemd_sync", "nemd_last_error",
             "nemd_set_option", "nemd_get_lattice", "nemd_get_stats", "nemd_get_pairs",
-            "nemd_get_kernel_time", "nemd_measure_peaks", "nemd_forces_noalloc"]
+            "nemd_get_kernel_time", "nemd_measure_peaks", "nemd_forces_noalloc", "nemd_autotune",
+            "nemd_tune_save", "nemd_tune_load"]
 NEMD_NOALLOC_MAX_N = 16384
 NEMD_NOALLOC_MAX_CELLS = 16384
 
@@ -47,6 +49,15 @@ class nemd_stats(ctypes.Structure):
                 ("cell_factor", ctypes.c_int32), ("max_rows", ctypes.c_int32),
                 ("stencil_cells", ctypes.c_int64), ("rechecks", ctypes.c_int64),
                 ("tau", ctypes.c_double), ("band", ctypes.c_double), ("launches", ctypes.c_int64)]
+
+
+class nemd_tune_config(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("group", ctypes.c_int32), ("cell_factor", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
+
+
+class nemd_tune_entry(ctypes.Structure):
+    _fields_ = [("cfg", nemd_tune_config), ("ms", ctypes.c_double)]
 
 
 _vp = ctypes.c_void_p
@@ -67,6 +78,10 @@ _sig = {
     "nemd_get_kernel_time": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
                              ctypes.c_int),
     "nemd_measure_peaks": ([ctypes.c_int, _vp], ctypes.c_int),
+    "nemd_autotune": ([_vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.POINTER(nemd_tune_config),
+                       ctypes.POINTER(nemd_tune_entry), ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "nemd_tune_save": ([_vp, ctypes.c_char_p], ctypes.c_int),
+    "nemd_tune_load": ([_vp, ctypes.c_char_p], ctypes.c_int),
     "nemd_forces_noalloc": ([_vp, _vp, ctypes.c_double, ctypes.c_double, _vp, ctypes.c_int64, ctypes.c_int,
                              ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                              _vp, _vp, _vp, _vp], ctypes.c_int),
@@ -184,6 +199,22 @@ class Context:
                 "counts": list(s.counts), "variant": s.variant, "cell_factor": s.cell_factor,
                 "max_rows": s.max_rows, "stencil_cells": s.stencil_cells, "rechecks": s.rechecks,
                 "tau": s.tau, "band": s.band, "launches": s.launches}
+
+    def autotune(self, variant, rc, reps=3):
+        """Time every candidate configuration; returns (best config dict, list of (config, ms))."""
+        best = nemd_tune_config()
+        times = (nemd_tune_entry * 32)()
+        nt = ctypes.c_int(0)
+        self._check(nemd_autotune(self.h, int(variant), float(rc), int(reps), ctypes.byref(best), times, 32,
+                                  ctypes.byref(nt)))
+        cfg = lambda c: {"kernel": c.kernel, "group": c.group, "cell_factor": c.cell_factor}
+        return cfg(best), [(cfg(times[k].cfg), times[k].ms) for k in range(nt.value)]
+
+    def tune_save(self, path):
+        return self._check(nemd_tune_save(self.h, str(path).encode()))
+
+    def tune_load(self, path):
+        return self._check(nemd_tune_load(self.h, str(path).encode()))
 
     def kernel_time(self):
         """(total ms, launches) of the force kernel since the last call (timing option on)."""

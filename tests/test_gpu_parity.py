@@ -33,7 +33,7 @@ def keys(p):
     return oracle.canonical_pair_keys(p)
 
 
-KERNELS = [(0, 16), (1, 16), (1, 4), (1, 32)]   # (kernel, group size): plain, grouped
+KERNELS = [(0, 16), (2, 32), (1, 16), (1, 4)]   # (kernel, group size): plain, warp, grouped
 
 
 def check_against(w, variant, ref, *, pairs=True, precise=True, kfac=1, kernel=(0, 16)):
@@ -179,9 +179,10 @@ def test_kernels_agree_bitwise_on_forces():
     """Same pair arithmetic and per-particle summation order in both kernels."""
     w = W.config_general(t=0.55, k=12)
     a = run(w, DO, kernel=(0, 16))
-    b = run(w, DO, kernel=(1, 16))
-    assert a["stats"]["pairs"] == b["stats"]["pairs"]
-    assert force_err(b["F"], a["F"]) <= 1e-6
+    for kern in ((1, 16), (2, 32)):
+        b = run(w, DO, kernel=kern)
+        assert a["stats"]["pairs"] == b["stats"]["pairs"]
+        assert force_err(b["F"], a["F"]) <= 1e-6
 
 
 def test_variants_agree_and_newton():
