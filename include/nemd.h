@@ -64,8 +64,9 @@ typedef enum nemd_variant {
     NEMD_AUTO_HEURISTIC = 2,  /* per step, the variant with the smaller neighbourhood
                                  volume V_DS = 27 V / (c1 c2 c3) versus
                                  V_DO = avg r11 r22 r33 / (l1 l2 l3)  (Sec. 5.1, 5.2)     */
-    NEMD_AUTO_LEARNED = 3     /* per step, the choice of a trained cost model
-                                 (nemd_model_load); falls back to the heuristic         */
+    NEMD_AUTO_LEARNED = 3     /* per step, the variant and cell factor of the learned
+                                 selector (nemd_model_train / nemd_model_load); the
+                                 heuristic when no model is set                         */
 } nemd_variant;
 
 typedef enum nemd_potential {
@@ -215,6 +216,59 @@ int nemd_autotune(nemd_ctx *ctx, int variant, double rc, int reps, nemd_tune_con
  * count or checksum and then leaves the cache unchanged. */
 int nemd_tune_save(nemd_ctx *ctx, const char *path);
 int nemd_tune_load(nemd_ctx *ctx, const char *path);
+
+/* ---- Learned cell-list selector -------------------------------------------
+ *
+ * The paper has no counterpart: its own rule for choosing between the two
+ * cell lists is the neighbourhood-volume comparison of Sec. 5.1-5.2
+ * (NEMD_AUTO_HEURISTIC), which remains the fallback.  A small multilayer
+ * perceptron (12 -> 64 -> 64 -> 4, ReLU, float32) predicts, per step, the
+ * normalised ln(time) of the four options o = (variant o & 1, cell factor
+ * 1 + (o >> 1)) from the features of the step:
+ *   x[0..8]  the entries of L(t) / V^(1/3) (row-major)
+ *   x[9]     N / V        x[10]  rc        x[11]  ln N
+ * With a model set, nemd_build_cells(NEMD_AUTO_LEARNED, rc) runs the forward
+ * pass on the device and uses the option with the smallest prediction; the
+ * pair set and forces do not depend on the choice.  All arrays below are host
+ * memory; the training and inference run in the library's own kernels. */
+#define NEMD_MLP_INPUTS 12
+#define NEMD_MLP_OUTPUTS 4
+#define NEMD_MLP_PARAMS 5252
+#define NEMD_MLP_NORM 26   /* input means (12), input std (12), target mean, target std */
+
+/* Features of the current state (after nemd_set_state).  Synchronises. */
+int nemd_features(nemd_ctx *ctx, double rc, float out[12]);
+
+/* Time the four options on the current state (one untimed, then `reps` timed
+ * nemd_build_cells + nemd_compute_forces each, CUDA events): features[12] and
+ * ms[4] (mean milliseconds) form one training row.  Synchronises. */
+int nemd_time_options(nemd_ctx *ctx, double rc, int reps, float features[12], float ms[4]);
+
+/* Train from scratch on `rows` rows (X: rows x 12 features, T_ms: rows x 4
+ * times in ms, all > 0): inputs and ln(time) targets normalised by their mean
+ * and standard deviation, Glorot-uniform weights from `seed`, then `steps`
+ * Adam steps (lr) on mini-batches of `batch` rows drawn with replacement.
+ * loss_hist (optional) receives each step's mini-batch mean squared error.
+ * The trained model becomes this context's selector. */
+int nemd_model_train(nemd_ctx *ctx, const float *X, const float *T_ms, int64_t rows, int steps, int batch, double lr,
+                     uint64_t seed, float *loss_hist);
+
+/* Predicted normalised ln(time) (rows x 4) of raw feature rows X (rows x 12). */
+int nemd_model_predict(nemd_ctx *ctx, const float *X, int64_t rows, float *Y);
+
+/* Gradient (NEMD_MLP_PARAMS floats) and value of L = sum (y - t)^2 / (rows 4)
+ * at the current parameters, for already normalised inputs Xn and targets Tn. */
+int nemd_model_grad(nemd_ctx *ctx, const float *Xn, const float *Tn, int64_t rows, float *grad, double *loss);
+
+/* Parameters: W1[64][12] b1[64] W2[64][64] b2[64] W3[4][64] b3[4] (row-major),
+ * and the NEMD_MLP_NORM normalisation constants. */
+int nemd_model_set_params(nemd_ctx *ctx, const float *params, const float *norm);
+int nemd_model_get_params(nemd_ctx *ctx, float *params, float *norm);
+
+/* Save / load the model: "NEMDMLP1", the three layer widths, parameters,
+ * normalisation and an FNV-1a 64-bit checksum; load rejects any mismatch. */
+int nemd_model_save(nemd_ctx *ctx, const char *path);
+int nemd_model_load(nemd_ctx *ctx, const char *path);
 
 /* Measure device peaks with the library's own kernels (synchronises):
  * out[0] FP32 FMA lane-ops/s, out[1] FP32 paired (f32x2) lane-ops/s,

@@ -56,6 +56,8 @@ def lib():
         L.orc_sample_forces.argtypes = [_dp, ctypes.c_int64, _dp, _dp, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_double, ctypes.c_int, _i64p, ctypes.c_int64, _dp, _i64p, _dp]
         L.orc_sample_forces.restype = None
+        L.orc_mlp_loss_grad.argtypes = [_dp, _dp, _dp, ctypes.c_int64, _dp, _dp]
+        L.orc_mlp_loss_grad.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -170,6 +172,22 @@ def sample_forces(L, s, qp, idx, rc, eps=1.0, sigma=1.0, shift=1):
     lib().orc_sample_forces(pL, s.shape[0], ps, pq, float(rc), float(eps), float(sigma), int(shift), pi,
                             len(idx), F.ctypes.data_as(_dp), cnt.ctypes.data_as(_i64p), uh.ctypes.data_as(_dp))
     return F, cnt, uh
+
+
+MLP_PARAMS = 64 * 12 + 64 + 64 * 64 + 64 + 4 * 64 + 4
+
+
+def mlp_loss_grad(params, X, T, want_grad=True):
+    """The selector network in FP64: (loss, gradient or None, outputs)."""
+    p, pp = _d(params)
+    X, px = _d(X)
+    T, pt = _d(T)
+    rows = X.shape[0]
+    g = np.zeros(MLP_PARAMS) if want_grad else None
+    Y = np.zeros((rows, 4))
+    loss = lib().orc_mlp_loss_grad(pp, px, pt, rows, g.ctypes.data_as(_dp) if want_grad else None,
+                                   Y.ctypes.data_as(_dp))
+    return float(loss), g, Y
 
 
 class Result:

@@ -823,3 +823,75 @@ void orc_sample_forces(const double *L, int64_t n, const double *s, const double
         if (U_half) U_half[t] = u;
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* The learned selector's network, FP64 (test oracle of its training kernels) */
+/* ------------------------------------------------------------------------ */
+
+/* Layers 12 -> 64 (ReLU) -> 64 (ReLU) -> 4; parameters W1[64][12] b1[64]
+ * W2[64][64] b2[64] W3[4][64] b3[4].  Returns L = sum (y - t)^2 / (rows 4) and,
+ * if grad is not NULL, dL/dparams by back-propagation.  Y (optional) receives
+ * the outputs. */
+#define ORC_DI 12
+#define ORC_H 64
+#define ORC_DO 4
+double orc_mlp_loss_grad(const double *p, const double *X, const double *T, int64_t rows, double *grad, double *Y)
+{
+    const double *W1 = p, *b1 = W1 + ORC_H * ORC_DI, *W2 = b1 + ORC_H, *b2 = W2 + ORC_H * ORC_H, *W3 = b2 + ORC_H,
+                 *b3 = W3 + ORC_DO * ORC_H;
+    const int np = ORC_H * ORC_DI + ORC_H + ORC_H * ORC_H + ORC_H + ORC_DO * ORC_H + ORC_DO;
+    double *gW1 = grad, *gb1 = 0, *gW2 = 0, *gb2 = 0, *gW3 = 0, *gb3 = 0;
+    if (grad) {
+        memset(grad, 0, sizeof(double) * np);
+        gb1 = gW1 + ORC_H * ORC_DI;
+        gW2 = gb1 + ORC_H;
+        gb2 = gW2 + ORC_H * ORC_H;
+        gW3 = gb2 + ORC_H;
+        gb3 = gW3 + ORC_DO * ORC_H;
+    }
+    double loss = 0.0;
+    const double scale = 2.0 / (double)(rows * ORC_DO);
+    for (int64_t b = 0; b < rows; b++) {
+        const double *x = X + b * ORC_DI;
+        double h1[ORC_H], h2[ORC_H], y[ORC_DO], d3[ORC_DO], d2[ORC_H], d1[ORC_H];
+        for (int h = 0; h < ORC_H; h++) {
+            double a = b1[h];
+            for (int i = 0; i < ORC_DI; i++) a += W1[h * ORC_DI + i] * x[i];
+            h1[h] = a > 0.0 ? a : 0.0;
+        }
+        for (int h = 0; h < ORC_H; h++) {
+            double a = b2[h];
+            for (int k = 0; k < ORC_H; k++) a += W2[h * ORC_H + k] * h1[k];
+            h2[h] = a > 0.0 ? a : 0.0;
+        }
+        for (int o = 0; o < ORC_DO; o++) {
+            double a = b3[o];
+            for (int k = 0; k < ORC_H; k++) a += W3[o * ORC_H + k] * h2[k];
+            y[o] = a;
+            const double e = a - T[b * ORC_DO + o];
+            loss += e * e;
+            d3[o] = scale * e;
+            if (Y) Y[b * ORC_DO + o] = a;
+        }
+        if (!grad) continue;
+        for (int o = 0; o < ORC_DO; o++) {
+            gb3[o] += d3[o];
+            for (int k = 0; k < ORC_H; k++) gW3[o * ORC_H + k] += d3[o] * h2[k];
+        }
+        for (int h = 0; h < ORC_H; h++) {
+            double a = 0.0;
+            for (int o = 0; o < ORC_DO; o++) a += W3[o * ORC_H + h] * d3[o];
+            d2[h] = h2[h] > 0.0 ? a : 0.0;
+            gb2[h] += d2[h];
+            for (int k = 0; k < ORC_H; k++) gW2[h * ORC_H + k] += d2[h] * h1[k];
+        }
+        for (int k = 0; k < ORC_H; k++) {
+            double a = 0.0;
+            for (int h = 0; h < ORC_H; h++) a += W2[h * ORC_H + k] * d2[h];
+            d1[k] = h1[k] > 0.0 ? a : 0.0;
+            gb1[k] += d1[k];
+            for (int i = 0; i < ORC_DI; i++) gW1[k * ORC_DI + i] += d1[k] * x[i];
+        }
+    }
+    return loss / (double)(rows * ORC_DO);
+}

@@ -187,6 +187,7 @@ int nemd_destroy(nemd_ctx *c) {
   if (!c) return NEMD_OK;
   cudaSetDevice(c->device);
   if (c->stream || true) cudaStreamSynchronize(c->stream);
+  if (c->model) cudaFree(c->model);
   void *ptrs[] = {c->geo,  c->q_copy, c->relc,     c->relr, c->posr, c->rank,     c->count,    c->start, c->chunks, c->nchunks, c->recheck, c->nrecheck,
                   c->block_sums, c->perm, c->pos4, c->cell_sorted, c->rows, c->rowcnt,
                   c->partials, c->uw_out, c->f_dev, c->pair_buf, c->pair_count, c->counters};
@@ -309,16 +310,25 @@ int nemd_build_cells(nemd_ctx *c, int variant, double rc) {
     return set_err(c, NEMD_ERR_ARG, "build_cells: WCA needs rc = 2^(1/6) sigma");
   CK(cudaSetDevice(c->device));
   if (c->autotuned) nemd::tune_apply(c, rc);
+  // the learned selector may pick cell factor 2 on the device: size for it
+  const bool learned = variant == NEMD_AUTO_LEARNED && c->have_model;
+  const int kalloc = learned && c->kfac < 2 ? 2 : c->kfac;
   // bound on the number of cells: c1 c2 c3 <= k^3 h1 h2 h3 / rc^3 <= k^3 V / rc^3
   const double V = fabs(det3(c->L0));
-  const double k3 = (double)c->kfac * c->kfac * c->kfac;
+  const double k3 = (double)kalloc * kalloc * kalloc;
   double bound = k3 * V / (rc * rc * rc) * (1.0 + 1e-9) + 1.0;
   if (bound > 2.0e9) return set_err(c, NEMD_ERR_ARG, "build_cells: %g cells is too many", bound);
-  int r = ensure_cells(c, (int64_t)bound, c->kfac);
+  int r = ensure_cells(c, (int64_t)bound, kalloc);
   if (r) return r;
   c->rc = rc;
   c->variant_req = variant;
-  cudaError_t e = nemd::launch_grid(c);
+  c->kfac_alloc = kalloc;
+  cudaError_t e = cudaSuccess;
+  if (variant == NEMD_AUTO_LEARNED) {
+    e = nemd::launch_learned_choice(c, rc);
+    if (e != cudaSuccess) return cuda_err(c, e, "build_cells learned choice");
+  }
+  e = nemd::launch_grid(c);
   if (e != cudaSuccess) return cuda_err(c, e, "build_cells grid");
   e = nemd::launch_stencil(c);
   if (e != cudaSuccess) return cuda_err(c, e, "build_cells stencil");

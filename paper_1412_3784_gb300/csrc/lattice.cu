@@ -220,10 +220,17 @@ __global__ void k_grid(Geo *g, GridIn in) {
     g->counts_do[a] = cdo1[a];
   }
   int variant = g->req_variant;
-  if (variant != NEMD_DS && variant != NEMD_DO) variant = (vdo < vds) ? NEMD_DO : NEMD_DS;
+  int kf = g->kfac;
+  if (variant == NEMD_AUTO_LEARNED && g->learned_choice >= 0) {
+    // the learned selector's option for this step: variant and cell factor
+    variant = g->learned_choice & 1;
+    kf = 1 + (g->learned_choice >> 1);
+    g->kfac = kf;
+  } else if (variant != NEMD_DS && variant != NEMD_DO) {
+    variant = (vdo < vds) ? NEMD_DO : NEMD_DS;
+  }
   g->variant = variant;
 
-  const int kf = g->kfac;
   int nc[3];
   double Gd[9];
   float step[3];
@@ -402,7 +409,8 @@ cudaError_t launch_grid(nemd_ctx *c) {
   in.variant = c->variant_req;
   in.kfac = c->kfac;
   in.max_cells = (int)c->cap_cells;
-  in.row_stride = (2 * c->kfac + 1) * (2 * c->kfac + 2);
+  const int ka = c->kfac_alloc > c->kfac ? c->kfac_alloc : c->kfac;
+  in.row_stride = (2 * ka + 1) * (2 * ka + 2);
   k_grid<<<1, 32, 0, c->stream>>>(c->geo, in);
   c->launches += 1;
   return cudaGetLastError();

@@ -62,6 +62,8 @@ struct Geo {
   int counts_ds[3], counts_do[3];
   int error;   // this step's error bits
   int sticky;  // error bits accumulated until the host reads them (nemd_sync)
+  int learned_choice;  // option picked by the learned selector this step, -1 if none
+  int pad_lc;
 };
 
 // Launch inputs, passed by value so that asynchronous launches and captured
@@ -101,6 +103,11 @@ static_assert(sizeof(Row) == 48, "Row is 48 bytes");
 // components xx yy zz xy xz yz), interacting pairs, candidates, rechecks.
 constexpr int kPartials = 10;
 
+// Learned selector: 12 inputs -> 64 -> 64 -> 4 outputs (float32).
+constexpr int kMlpIn = 12, kMlpHidden = 64, kMlpOut = 4;
+constexpr int kMlpParams = kMlpHidden * kMlpIn + kMlpHidden + kMlpHidden * kMlpHidden + kMlpHidden +
+                           kMlpOut * kMlpHidden + kMlpOut;
+
 // Autotuner cache: per shape class, the summed mean time and the number of
 // measurements of every candidate configuration.
 constexpr int kTuneCandidates = 9;
@@ -136,6 +143,7 @@ struct nemd_ctx {
   int64_t record_cap;
   int kernel;
   int kfac;
+  int kfac_alloc;  // cell factor the buffers of the current step are sized for
   int block;
   // device memory
   nemd::Geo *geo;
@@ -176,6 +184,10 @@ struct nemd_ctx {
   // candidates left within float32 rounding of rc, decided by the float64 fix-up
   int4 *recheck;
   int *nrecheck;
+  // learned selector: params | input mean, std | target mean, std | Adam state (device)
+  float *model;
+  int have_model;
+  float model_norm_host[2 * nemd::kMlpIn + 2];
   // autotuner cache (host)
   int autotuned;
   int ntune;
@@ -200,6 +212,8 @@ cudaError_t launch_chunk_build(nemd_ctx *c, int gs);
 cudaError_t launch_force_warp(nemd_ctx *c, float *F_dev, int *nblocks);
 // autotuner cache lookup (autotune.cu)
 void tune_apply(nemd_ctx *c, double rc);
+// learned selector inference for this step (mlp.cu)
+cudaError_t launch_learned_choice(nemd_ctx *c, double rc);
 cudaError_t launch_force_chunk(nemd_ctx *c, float *F_dev, int *nblocks);
 
 }  // namespace nemd

@@ -38,7 +38,10 @@ EXPORTED = ["nemd_create", "nemd_destroy", "nemd_set_flow", "nemd_set_potential"
             "nemd_build_cells", "nemd_compute_forces", "nemd_sync", "nemd_last_error",
             "nemd_set_option", "nemd_get_lattice", "nemd_get_stats", "nemd_get_pairs",
             "nemd_get_kernel_time", "nemd_measure_peaks", "nemd_forces_noalloc", "nemd_autotune",
-            "nemd_tune_save", "nemd_tune_load"]
+            "nemd_tune_save", "nemd_tune_load", "nemd_features", "nemd_time_options", "nemd_model_train",
+            "nemd_model_predict", "nemd_model_grad", "nemd_model_set_params", "nemd_model_get_params",
+            "nemd_model_save", "nemd_model_load"]
+NEMD_MLP_INPUTS, NEMD_MLP_OUTPUTS, NEMD_MLP_PARAMS, NEMD_MLP_NORM = 12, 4, 5252, 26
 NEMD_NOALLOC_MAX_N = 16384
 NEMD_NOALLOC_MAX_CELLS = 16384
 
@@ -82,6 +85,16 @@ _sig = {
                        ctypes.POINTER(nemd_tune_entry), ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "nemd_tune_save": ([_vp, ctypes.c_char_p], ctypes.c_int),
     "nemd_tune_load": ([_vp, ctypes.c_char_p], ctypes.c_int),
+    "nemd_features": ([_vp, ctypes.c_double, _vp], ctypes.c_int),
+    "nemd_time_options": ([_vp, ctypes.c_double, ctypes.c_int, _vp, _vp], ctypes.c_int),
+    "nemd_model_train": ([_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint64,
+                          _vp], ctypes.c_int),
+    "nemd_model_predict": ([_vp, _vp, ctypes.c_int64, _vp], ctypes.c_int),
+    "nemd_model_grad": ([_vp, _vp, _vp, ctypes.c_int64, _vp, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "nemd_model_set_params": ([_vp, _vp, _vp], ctypes.c_int),
+    "nemd_model_get_params": ([_vp, _vp, _vp], ctypes.c_int),
+    "nemd_model_save": ([_vp, ctypes.c_char_p], ctypes.c_int),
+    "nemd_model_load": ([_vp, ctypes.c_char_p], ctypes.c_int),
     "nemd_forces_noalloc": ([_vp, _vp, ctypes.c_double, ctypes.c_double, _vp, ctypes.c_int64, ctypes.c_int,
                              ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                              _vp, _vp, _vp, _vp], ctypes.c_int),
@@ -215,6 +228,58 @@ class Context:
 
     def tune_load(self, path):
         return self._check(nemd_tune_load(self.h, str(path).encode()))
+
+    # ---- learned selector ----
+    def features(self, rc):
+        out = np.zeros(NEMD_MLP_INPUTS, dtype=np.float32)
+        self._check(nemd_features(self.h, float(rc), out.ctypes.data))
+        return out
+
+    def time_options(self, rc, reps=2):
+        f = np.zeros(NEMD_MLP_INPUTS, dtype=np.float32)
+        ms = np.zeros(NEMD_MLP_OUTPUTS, dtype=np.float32)
+        self._check(nemd_time_options(self.h, float(rc), int(reps), f.ctypes.data, ms.ctypes.data))
+        return f, ms
+
+    def model_train(self, X, T_ms, steps=2000, batch=128, lr=3e-3, seed=0):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        T = np.ascontiguousarray(T_ms, dtype=np.float32)
+        hist = np.zeros(int(steps), dtype=np.float32)
+        self._check(nemd_model_train(self.h, X.ctypes.data, T.ctypes.data, X.shape[0], int(steps), int(batch),
+                                     float(lr), int(seed), hist.ctypes.data))
+        return hist
+
+    def model_predict(self, X):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.zeros((X.shape[0], NEMD_MLP_OUTPUTS), dtype=np.float32)
+        self._check(nemd_model_predict(self.h, X.ctypes.data, X.shape[0], Y.ctypes.data))
+        return Y
+
+    def model_grad(self, Xn, Tn):
+        Xn = np.ascontiguousarray(Xn, dtype=np.float32)
+        Tn = np.ascontiguousarray(Tn, dtype=np.float32)
+        g = np.zeros(NEMD_MLP_PARAMS, dtype=np.float32)
+        loss = ctypes.c_double(0.0)
+        self._check(nemd_model_grad(self.h, Xn.ctypes.data, Tn.ctypes.data, Xn.shape[0], g.ctypes.data,
+                                    ctypes.byref(loss)))
+        return g, loss.value
+
+    def model_set_params(self, params, norm):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        nrm = np.ascontiguousarray(norm, dtype=np.float32)
+        return self._check(nemd_model_set_params(self.h, p.ctypes.data, nrm.ctypes.data))
+
+    def model_get_params(self):
+        p = np.zeros(NEMD_MLP_PARAMS, dtype=np.float32)
+        nrm = np.zeros(NEMD_MLP_NORM, dtype=np.float32)
+        self._check(nemd_model_get_params(self.h, p.ctypes.data, nrm.ctypes.data))
+        return p, nrm
+
+    def model_save(self, path):
+        return self._check(nemd_model_save(self.h, str(path).encode()))
+
+    def model_load(self, path):
+        return self._check(nemd_model_load(self.h, str(path).encode()))
 
     def kernel_time(self):
         """(total ms, launches) of the force kernel since the last call (timing option on)."""
