@@ -276,6 +276,108 @@ int nemd_model_load(nemd_ctx *ctx, const char *path);
  * out[5] SM clock kHz reported by the device. */
 int nemd_measure_peaks(int device, double *out);
 
+/* ---- Batches of independent systems -------------------------------------
+ *
+ * The paper treats one system at a time; a batch evaluates many independent
+ * systems -- each with its own flow, lattice, potential, cut-off, N and cell
+ * list variant -- in one step whose every stage (lattice, grid and stencil,
+ * binning, chunk lists, force, reductions) is ONE kernel launch over all
+ * systems, the force kernel being a single persistent launch over the chunks
+ * of every system.  The step is captured once into a CUDA graph and replayed
+ * (NEMD_BATCH_OPT_GRAPH).  Per system the results are those of a context with
+ * the same flow, potential, variant and cell factor running the warp kernel
+ * (nemd_compute_forces with NEMD_OPT_KERNEL = 2): same pair set, same forces
+ * per particle; U and W are float64 sums of the same pair terms in another
+ * order.
+ *
+ * Call order: nemd_batch_create, nemd_batch_add (once per system, in order),
+ * nemd_batch_finalize, then per step nemd_batch_set_state and
+ * nemd_batch_compute; nemd_batch_sync returns the deferred device errors.
+ * Particles of all systems are concatenated in system order: system s owns
+ * rows offsets[s] .. offsets[s+1]-1 of q and F (nemd_batch_offsets). */
+typedef struct nemd_batch nemd_batch;
+
+typedef struct nemd_system {
+    double A[9], L0[9];  /* flow and reference lattice, as nemd_set_flow            */
+    int64_t M[9];        /* remap matrix in SL(3,Z), as nemd_set_flow              */
+    double T;            /* period, as nemd_set_flow                               */
+    double eps, sigma;   /* potential, as nemd_set_potential                       */
+    double rc;           /* cut-off; WCA needs rc = 2^(1/6) sigma                   */
+    int64_t n;           /* particles, 0 .. 2^21                                   */
+    int32_t kind;        /* NEMD_LJ or NEMD_WCA                                    */
+    int32_t shift;       /* energy shifted to 0 at rc (required for WCA)           */
+    int32_t variant;     /* NEMD_DS, NEMD_DO or NEMD_AUTO_HEURISTIC (per step)     */
+    int32_t pad;
+} nemd_system;
+
+typedef struct nemd_batch_stats {
+    int64_t pairs;       /* interacting unordered pairs of the last step           */
+    int64_t candidates;  /* distance tests of the last step                        */
+    int64_t band;        /* candidates decided with the float32 residuals added    */
+    int32_t counts[3];   /* cell counts of the last step's grid                    */
+    int32_t variant;     /* cell list used in the last step (NEMD_DS / NEMD_DO)    */
+    int32_t cell_factor; /* cell-size factor of the last step                      */
+    int32_t status;      /* nemd_status of the system's last step                  */
+} nemd_batch_stats;
+
+/* Batch options (nemd_batch_set_option). */
+#define NEMD_BATCH_OPT_CELL_FACTOR 1  /* cells >= rc / k wide, k = 1 or 2 (default 1)   */
+#define NEMD_BATCH_OPT_TILE 2         /* particles per chunk, 16 or 32 (default 32)     */
+#define NEMD_BATCH_OPT_GRAPH 3        /* 1: capture and replay a CUDA graph (default);
+                                         0: launch the kernels one by one             */
+
+/* Create / destroy a batch on `device` working on `stream` (a cudaStream_t,
+ * NULL = the legacy default stream).  Destroy synchronises and frees
+ * everything the batch owns. */
+int nemd_batch_create(nemd_batch **out, int device, void *stream);
+int nemd_batch_destroy(nemd_batch *b);
+const char *nemd_batch_last_error(const nemd_batch *b);
+
+/* Append one system (host struct, copied); *index (optional) receives its
+ * index.  The flow is validated as by nemd_set_flow (NEMD_ERR_NOT_SL3Z,
+ * NEMD_ERR_TRACE, NEMD_ERR_NOT_KR), the potential and cut-off as by
+ * nemd_set_potential / nemd_build_cells; NEMD_ERR_ORDER after finalize. */
+int nemd_batch_add(nemd_batch *b, const nemd_system *sys, int64_t *index);
+
+/* Size and allocate the device tables for the systems added: cell slots
+ * k^3 V / rc^3 per system (k = 2, a bound that holds at every strain);
+ * row-class slots from the largest class count over 257 states of the
+ * period, times 1.25, plus 16 (a state that would need more sets
+ * NEMD_ERR_CAPACITY for its system at that step).  Synchronises. */
+int nemd_batch_finalize(nemd_batch *b);
+
+/* Particle offsets: offsets[0..nsys] (host), offsets[nsys] = total N. */
+int nemd_batch_offsets(const nemd_batch *b, int64_t *offsets, int64_t *nsys);
+
+/* State of every system: q -- total N x 3 float64 (host or device; a device
+ * pointer is read in place by the next nemd_batch_compute and must stay valid
+ * until it has run); t -- nsys float64 times, HOST. */
+int nemd_batch_set_state(nemd_batch *b, const double *q, const double *t);
+
+/* One step for every system: F -- total N x 3 float32 (Cartesian, input
+ * order), UW -- nsys x 10 float64 (U, then W row-major); each host or device
+ * pointer, or NULL to skip.  Asynchronous for device outputs; with a host
+ * output it synchronises before it returns.  A system whose step failed (see
+ * nemd_batch_sync) gets U = W = 0 and unspecified forces. */
+int nemd_batch_compute(nemd_batch *b, float *F, double *UW);
+
+/* Wait for the stream; return the first failing system's status (0 = all
+ * OK).  status (optional, host, nsys ints) receives every system's status
+ * since the previous sync. */
+int nemd_batch_sync(nemd_batch *b, int32_t *status);
+
+int nemd_batch_set_option(nemd_batch *b, int key, int64_t value);
+
+/* Per-system statistics of the last step (host array of nsys entries).
+ * *launches (optional) receives the kernel launches of one step.  Synchronises. */
+int nemd_batch_get_stats(nemd_batch *b, nemd_batch_stats *out, int64_t *launches);
+
+/* Autotuner of a batch: times `reps` steps (after one untimed step) of every
+ * candidate -- cell factor 1, 2 x particles per chunk 16, 32 -- on the current
+ * state and keeps the fastest.  times (optional, cap entries) receives each
+ * candidate as {kernel = 2, group = tile, cell_factor, ms}.  Synchronises. */
+int nemd_batch_autotune(nemd_batch *b, int reps, nemd_tune_entry *times, int cap, int *ntimes);
+
 /* ---- Force evaluation without any memory allocation --------------------
  *
  * The paper has no counterpart to this entry point; it exists for callers that

@@ -15,16 +15,16 @@
 //   k_pack      sorted float4 {rel position, input index}, residuals, cell ids
 #include <math.h>
 
+#include "batch_internal.cuh"
 #include "nemd_device.cuh"
-#include "nemd_internal.cuh"
 
 namespace nemd {
 
-__global__ void k_wrap(Geo *g, const double *__restrict__ q, int n, float4 *__restrict__ relc,
-                       float4 *__restrict__ relr, int *__restrict__ rank, int *__restrict__ count) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
+// One particle: cell_base is the system's first cell slot (0 for a single
+// system); the cell index stored in relc.w and counted is cell_base + local.
+__device__ __forceinline__ void wrap_body(Geo *g, const double *__restrict__ q, int i, int cell_base,
+                                          float4 *__restrict__ relc, float4 *__restrict__ relr,
+                                          int *__restrict__ rank, int *__restrict__ count) {
   double x = q[3 * (size_t)i], y = q[3 * (size_t)i + 1], z = q[3 * (size_t)i + 2];
   if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
     atomicOr(&g->error, ERRB_NONFINITE);
@@ -67,11 +67,19 @@ __global__ void k_wrap(Geo *g, const double *__restrict__ q, int n, float4 *__re
     rq[a] = (float)h;
     rr[a] = (float)(rel[a] - h);
   }
-  const int cell = idx[0] + l1 * (idx[1] + l2 * idx[2]);
+  const int cell = cell_base + idx[0] + l1 * (idx[1] + l2 * idx[2]);
   (void)l3;
   relc[i] = make_float4(rq[0], rq[1], rq[2], __int_as_float(cell));
   relr[i] = make_float4(rr[0], rr[1], rr[2], 0.0f);
   rank[i] = atomicAdd(&count[cell], 1);
+}
+
+__global__ void k_wrap(Geo *g, const double *__restrict__ q, int n, float4 *__restrict__ relc,
+                       float4 *__restrict__ relr, int *__restrict__ rank, int *__restrict__ count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
+  wrap_body(g, q, i, 0, relc, relr, rank, count);
 }
 
 // ---- exclusive scan of count[0..ncells) into start[0..ncells], start[ncells] = n ----
@@ -103,11 +111,10 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *sh, int &total) 
   return incl - v;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const Geo *g, const int *__restrict__ count,
-                                                             int *__restrict__ start, int *__restrict__ tile_sums) {
+// Per tile of kScanTile counts: exclusive scan within the tile, tile total.
+__device__ __forceinline__ void scan_tiles_body(const int *__restrict__ count, int *__restrict__ start,
+                                                int *__restrict__ tile_sums, int ncells) {
   __shared__ int sh[32];
-  if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
-  const int ncells = g->ncells;
   const int base = blockIdx.x * kScanTile;
   if (base >= ncells) return;  // whole block uniform
   int v[kScanItems];
@@ -127,10 +134,15 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const Geo *g, const
   if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_top(const Geo *g, int *__restrict__ tile_sums) {
-  __shared__ int sh[32];
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const Geo *g, const int *__restrict__ count,
+                                                             int *__restrict__ start, int *__restrict__ tile_sums) {
   if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
-  const int ntiles = (g->ncells + kScanTile - 1) / kScanTile;
+  scan_tiles_body(count, start, tile_sums, g->ncells);
+}
+
+// One block: exclusive scan of the tile totals; returns the grand total.
+__device__ __forceinline__ int scan_top_body(int *__restrict__ tile_sums, int ntiles) {
+  __shared__ int sh[32];
   int carry = 0;
   for (int base = 0; base < ntiles; base += kScanThreads) {
     int idx = base + threadIdx.x;
@@ -140,6 +152,12 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_top(const Geo *g, int *__
     if (idx < ntiles) tile_sums[idx] = ex + carry;
     carry += total;
   }
+  return carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(const Geo *g, int *__restrict__ tile_sums) {
+  if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
+  scan_top_body(tile_sums, (g->ncells + kScanTile - 1) / kScanTile);
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_add(const Geo *g, int *__restrict__ start,
@@ -165,21 +183,25 @@ __global__ void k_scatter(const Geo *g, const float4 *__restrict__ relc, const i
   perm[start[cell] + rank[i]] = i;
 }
 
+// Insertion sort of one cell's slice of perm (cells hold a few tens of particles).
+__device__ __forceinline__ void cellsort_body(const int *__restrict__ start, int *__restrict__ perm, int c) {
+  const int b = start[c], e = start[c + 1];
+  for (int k = b + 1; k < e; k++) {
+    int v = perm[k];
+    int j = k - 1;
+    while (j >= b && perm[j] > v) {
+      perm[j + 1] = perm[j];
+      j--;
+    }
+    perm[j + 1] = v;
+  }
+}
+
 __global__ void k_cellsort(const Geo *g, const int *__restrict__ start, int *__restrict__ perm) {
   if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
   const int ncells = g->ncells;
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
-    const int b = start[c], e = start[c + 1];
-    for (int k = b + 1; k < e; k++) {
-      int v = perm[k];
-      int j = k - 1;
-      while (j >= b && perm[j] > v) {
-        perm[j + 1] = perm[j];
-        j--;
-      }
-      perm[j + 1] = v;
-    }
-  }
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x)
+    cellsort_body(start, perm, c);
 }
 
 __global__ void k_pack(const Geo *g, const float4 *__restrict__ relc, const float4 *__restrict__ relr,
@@ -220,6 +242,91 @@ cudaError_t launch_bin(nemd_ctx *c) {
     k_pack<<<nb, tb, 0, c->stream>>>(c->geo, c->relc, c->relr, c->perm, c->pos4, c->posr, c->cell_sorted, n);
     c->launches += 3;
   }
+  return cudaGetLastError();
+}
+
+
+// ---- fixed-length scan: out[0..len) exclusive, out[len] = total ----
+static_assert(kFixedScanTile == kScanTile, "scan tile");
+
+__global__ void __launch_bounds__(kScanThreads) k_fscan_tiles(const int *__restrict__ in, int *__restrict__ out,
+                                                              int *__restrict__ tiles, int len) {
+  scan_tiles_body(in, out, tiles, len);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_fscan_top(int *__restrict__ tiles, int ntiles) {
+  const int total = scan_top_body(tiles, ntiles);
+  if (threadIdx.x == 0) tiles[ntiles] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_fscan_add(int *__restrict__ out, const int *__restrict__ tiles,
+                                                            int len, int ntiles) {
+  const int base = blockIdx.x * kScanTile;
+  const int add = tiles[blockIdx.x];
+  for (int k = 0; k < kScanItems; k++) {
+    int idx = base + threadIdx.x * kScanItems + k;
+    if (idx < len) out[idx] += add;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) out[len] = tiles[ntiles];
+}
+
+cudaError_t launch_fixed_scan(cudaStream_t st, const int *in, int *out, int *tiles, int len) {
+  const int ntiles = len > 0 ? (len + kScanTile - 1) / kScanTile : 1;
+  k_fscan_tiles<<<ntiles, kScanThreads, 0, st>>>(in, out, tiles, len);
+  k_fscan_top<<<1, kScanThreads, 0, st>>>(tiles, ntiles);
+  k_fscan_add<<<ntiles, kScanThreads, 0, st>>>(out, tiles, len, ntiles);
+  return cudaGetLastError();
+}
+
+// ---- batches: every system's particles in one launch per stage ----
+
+__global__ void k_b_wrap(BatchView v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= v.ntot) return;
+  const int s = v.sys_of[i];
+  Geo *g = v.geo + s;
+  if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
+  wrap_body(g, v.q, i, v.sys[s].coff, v.relc, v.relr, v.rank, v.count);
+}
+
+__global__ void k_b_scatter(BatchView v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= v.ntot) return;
+  if (v.geo[v.sys_of[i]].error & (ERRB_BOX | ERRB_CAPACITY)) return;
+  const int cell = __float_as_int(v.relc[i].w);
+  v.perm[v.start[cell] + v.rank[i]] = i;
+}
+
+__global__ void k_b_cellsort(BatchView v) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < v.ncells; c += gridDim.x * blockDim.x)
+    cellsort_body(v.start, v.perm, c);
+}
+
+// Sorted slots [0, start[ncells]): the particles of every system that binned.
+__global__ void k_b_pack(BatchView v) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= v.start[v.ncells]) return;
+  const int i = v.perm[k];
+  const float4 r = v.relc[i];
+  v.pos4[k] = make_float4(r.x, r.y, r.z, __int_as_float(i));
+  v.posr[k] = v.relr[i];
+  v.cell_sorted[k] = __float_as_int(r.w);
+}
+
+cudaError_t launch_batch_bin(cudaStream_t st, const BatchView &v, int sms) {
+  cudaError_t e = cudaMemsetAsync(v.count, 0, sizeof(int) * ((size_t)v.ncells + 1), st);
+  if (e != cudaSuccess) return e;
+  const int tb = 256;
+  const int nb = v.ntot > 0 ? (v.ntot + tb - 1) / tb : 1;
+  k_b_wrap<<<nb, tb, 0, st>>>(v);
+  e = launch_fixed_scan(st, v.count, v.start, v.tiles, v.ncells);
+  if (e != cudaSuccess) return e;
+  k_b_scatter<<<nb, tb, 0, st>>>(v);
+  int cb = (v.ncells + 255) / 256;
+  if (cb > 8 * sms) cb = 8 * sms;
+  if (cb < 1) cb = 1;
+  k_b_cellsort<<<cb, 256, 0, st>>>(v);
+  k_b_pack<<<nb, tb, 0, st>>>(v);
   return cudaGetLastError();
 }
 

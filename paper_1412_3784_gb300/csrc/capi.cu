@@ -110,21 +110,8 @@ int take_device_error(nemd_ctx *c) {
   int bits = *c->h_error;
   *c->h_error = 0;
   if (!bits) return NEMD_OK;
-  int code = NEMD_ERR_CUDA;
-  const char *what = "device error";
-  if (bits & nemd::ERRB_NONFINITE) {
-    code = NEMD_ERR_NONFINITE;
-    what = "non-finite particle coordinate";
-  } else if (bits & nemd::ERRB_BOX) {
-    code = NEMD_ERR_BOX_TOO_SMALL;
-    what = "box too small for the cut-off: a cell count is 0";
-  } else if (bits & nemd::ERRB_CAPACITY) {
-    code = NEMD_ERR_CAPACITY;
-    what = "device table capacity exceeded";
-  } else if (bits & nemd::ERRB_TIMEOUT) {
-    code = NEMD_ERR_TIMEOUT;
-    what = "bounded device wait ran out";
-  }
+  const char *what;
+  const int code = nemd::status_from_bits(bits, &what);
   return set_err(c, code, "%s (device error bits 0x%x)", what, bits);
 }
 
@@ -138,6 +125,32 @@ __global__ void k_fetch_error(Geo *g, int *out, int clear) {
 }
 
 }  // namespace
+
+namespace nemd {
+
+int status_from_bits(int bits, const char **what) {
+  const char *w = "device error";
+  int code = bits ? NEMD_ERR_CUDA : NEMD_OK;
+  if (!bits) {
+    w = "ok";
+  } else if (bits & ERRB_NONFINITE) {
+    code = NEMD_ERR_NONFINITE;
+    w = "non-finite particle coordinate";
+  } else if (bits & ERRB_BOX) {
+    code = NEMD_ERR_BOX_TOO_SMALL;
+    w = "box too small for the cut-off: a cell count is 0";
+  } else if (bits & ERRB_CAPACITY) {
+    code = NEMD_ERR_CAPACITY;
+    w = "device table capacity exceeded";
+  } else if (bits & ERRB_TIMEOUT) {
+    code = NEMD_ERR_TIMEOUT;
+    w = "bounded device wait ran out";
+  }
+  if (what) *what = w;
+  return code;
+}
+
+}  // namespace nemd
 
 extern "C" {
 

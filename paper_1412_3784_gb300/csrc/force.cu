@@ -15,7 +15,7 @@
 // halved.
 #include <math.h>
 
-#include "force_common.cuh"
+#include "batch_internal.cuh"
 
 namespace nemd {
 
@@ -352,6 +352,118 @@ cudaError_t launch_forces(nemd_ctx *c, float *F_dev, double *UW_dev) {
                                             c->partials + (size_t)nblocks * kPartials);
   c->launches += 1;
   return launch_reduce(c, nblocks + 1, c->precise ? 1 : 0, UW_dev);
+}
+
+
+// ---- batches ----
+
+// Float64 fix-up of the deferred candidates of every system (as
+// k_recheck_fixup); the accepted pair terms go to the particle's own sums.
+__global__ void k_b_fixup(BatchView v) {
+  const int n = min(*v.nrecheck, kRecheckCap);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int4 it = v.recheck[e];
+    const int oi = __float_as_int(v.pos4[it.x].w), oj = __float_as_int(v.pos4[it.y].w);
+    const int s = v.sys_of[oi];
+    const Geo *g = v.geo + s;
+    const int ky = (short)(it.w & 0xffff), kz = it.w >> 16;
+    int nn[3];
+    pair_image(g, v.q, oi, oj, it.z, ky, kz, nn);
+    double d[3];
+    const double r2 = canon_r2(g, v.q, oi, oj, nn[0], nn[1], nn[2], d);
+    if (!(r2 < g->rc2)) continue;
+    const Pot pp = v.pot[s];
+    const double inv = 1.0 / r2, s2 = pp.sig2d * inv, s6 = s2 * s2 * s2;
+    const double fr = pp.eps24d * inv * s6 * (2.0 * s6 - 1.0);
+    if (v.F)
+      for (int a = 0; a < 3; a++) atomicAdd(&v.F[3 * (size_t)oi + a], (float)(-fr * d[a]));
+    double df[3];
+    for (int a = 0; a < 3; a++) df[a] = g->Q[a] * d[0] + g->Q[3 + a] * d[1] + g->Q[6 + a] * d[2];
+    if (g->variant != NEMD_DO)
+      for (int a = 0; a < 3; a++) df[a] = d[a];
+    float *p0 = &v.ppart[2 * (size_t)it.x].x, *p1 = &v.ppart[2 * (size_t)it.x + 1].x;
+    atomicAdd(p0, (float)(pp.eps4d * s6 * (s6 - 1.0) - pp.ushiftd));
+    atomicAdd(p0 + 1, (float)(fr * df[0] * df[0]));
+    atomicAdd(p0 + 2, (float)(fr * df[1] * df[1]));
+    atomicAdd(p0 + 3, (float)(fr * df[2] * df[2]));
+    atomicAdd(p1, (float)(fr * df[0] * df[1]));
+    atomicAdd(p1 + 1, (float)(fr * df[0] * df[2]));
+    atomicAdd(p1 + 2, (float)(fr * df[1] * df[2]));
+    atomicAdd(reinterpret_cast<int *>(p1 + 3), 1);
+  }
+}
+
+// One block per system: float64 sums of its particles' pair sums in sorted
+// order (fixed), halved for the full neighbourhoods, the virial rotated back to
+// Cartesian for the dynamic offset frame (W = Q W_R Q^T).
+__global__ void __launch_bounds__(256) k_b_reduce(BatchView v) {
+  constexpr int K = 8;
+  __shared__ double sh[256][K];
+  const int s = blockIdx.x;
+  Geo *g = v.geo + s;
+  const bool ok = !(g->error & (ERRB_BOX | ERRB_CAPACITY));
+  int b = 0, e = 0;
+  if (ok) {
+    const int coff = v.sys[s].coff;
+    b = v.start[coff];
+    e = v.start[coff + g->ncells];
+  }
+  double a[K];
+#pragma unroll
+  for (int k = 0; k < K; k++) a[k] = 0.0;
+  for (int k = b + threadIdx.x; k < e; k += blockDim.x) {
+    const float4 p0 = v.ppart[2 * (size_t)k], p1 = v.ppart[2 * (size_t)k + 1];
+    a[0] += p0.x;
+    a[1] += p0.y;
+    a[2] += p0.z;
+    a[3] += p0.w;
+    a[4] += p1.x;
+    a[5] += p1.y;
+    a[6] += p1.z;
+    a[7] += (double)__float_as_int(p1.w);
+  }
+#pragma unroll
+  for (int k = 0; k < K; k++) sh[threadIdx.x][k] = a[k];
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st)
+#pragma unroll
+      for (int k = 0; k < K; k++) sh[threadIdx.x][k] += sh[threadIdx.x + st][k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double Wr[9];
+    Wr[0] = 0.5 * sh[0][1];
+    Wr[4] = 0.5 * sh[0][2];
+    Wr[8] = 0.5 * sh[0][3];
+    Wr[1] = Wr[3] = 0.5 * sh[0][4];
+    Wr[2] = Wr[6] = 0.5 * sh[0][5];
+    Wr[5] = Wr[7] = 0.5 * sh[0][6];
+    double W[9];
+    if (g->variant == NEMD_DO) {
+      double T9[9];
+      const double *Q = g->Q;
+      for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) T9[3 * i + j] = Q[3 * i] * Wr[j] + Q[3 * i + 1] * Wr[3 + j] + Q[3 * i + 2] * Wr[6 + j];
+      for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++)
+          W[3 * i + j] = T9[3 * i] * Q[3 * j] + T9[3 * i + 1] * Q[3 * j + 1] + T9[3 * i + 2] * Q[3 * j + 2];
+    } else {
+      for (int k = 0; k < 9; k++) W[k] = Wr[k];
+    }
+    if (v.UW) {
+      v.UW[10 * (size_t)s] = ok ? 0.5 * sh[0][0] : 0.0;
+      for (int k = 0; k < 9; k++) v.UW[10 * (size_t)s + 1 + k] = ok ? W[k] : 0.0;
+    }
+    v.sys_pairs[s] = (unsigned long long)(0.5 * sh[0][7] + 0.25);
+    g->sticky |= g->error;
+  }
+}
+
+cudaError_t launch_batch_finish(cudaStream_t st, const BatchView &v) {
+  k_b_fixup<<<4, 256, 0, st>>>(v);
+  k_b_reduce<<<v.nsys, 256, 0, st>>>(v);
+  return cudaGetLastError();
 }
 
 }  // namespace nemd

@@ -21,12 +21,43 @@
 // its own lane in a fixed order, so results are deterministic.
 #include <math.h>
 
-#include "force_common.cuh"
+#include "batch_internal.cuh"
 
 namespace nemd {
 
 constexpr int kQueue = 64;  // queue entries per lane
 constexpr int kChunkThreads = 128;
+
+// Walk one x-row of cells (cells c0 .. c0 + l1 - 1) in order, cutting its
+// particles into chunks of at most gs particles spanning at most kMaxSpan
+// cells; emit(first, count, ixlo, ixhi) for each chunk, in order.
+template <class Emit>
+__device__ __forceinline__ void chunk_walk(const int *__restrict__ start, int c0, int l1, int gs, Emit &&emit) {
+  int first = 0, count = 0, ixlo = 0, ixhi = 0;
+  for (int ix = 0; ix < l1; ix++) {
+    const int b = start[c0 + ix], nc = start[c0 + ix + 1] - b;
+    int off = 0;
+    while (off < nc) {
+      if (count > 0 && ix - ixlo >= kMaxSpan) {
+        emit(first, count, ixlo, ixhi);
+        count = 0;
+      }
+      if (count == 0) {
+        first = b + off;
+        ixlo = ix;
+      }
+      const int take = min(gs - count, nc - off);
+      count += take;
+      off += take;
+      ixhi = ix;
+      if (count == gs) {
+        emit(first, count, ixlo, ixhi);
+        count = 0;
+      }
+    }
+  }
+  if (count > 0) emit(first, count, ixlo, ixhi);
+}
 
 // Chunk descriptor: x = first sorted particle, y = count, z = class (iy + l2 iz),
 // w = ixlo | ixhi << 16.  One thread per row of cells; slots by atomic counter.
@@ -34,33 +65,10 @@ __global__ void k_chunks(const Geo *__restrict__ g, const int *__restrict__ star
                          int *__restrict__ nchunks, int gs) {
   if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
   const int l1 = g->nc[0], ncls = g->nc[1] * g->nc[2];
-  for (int cls = blockIdx.x * blockDim.x + threadIdx.x; cls < ncls; cls += gridDim.x * blockDim.x) {
-    const int c0 = cls * l1;
-    int first = 0, count = 0, ixlo = 0, ixhi = 0;
-    for (int ix = 0; ix < l1; ix++) {
-      const int b = start[c0 + ix], nc = start[c0 + ix + 1] - b;
-      int off = 0;
-      while (off < nc) {
-        if (count > 0 && ix - ixlo >= kMaxSpan) {
-          chunks[atomicAdd(nchunks, 1)] = make_int4(first, count, cls, ixlo | (ixhi << 16));
-          count = 0;
-        }
-        if (count == 0) {
-          first = b + off;
-          ixlo = ix;
-        }
-        const int take = min(gs - count, nc - off);
-        count += take;
-        off += take;
-        ixhi = ix;
-        if (count == gs) {
-          chunks[atomicAdd(nchunks, 1)] = make_int4(first, count, cls, ixlo | (ixhi << 16));
-          count = 0;
-        }
-      }
-    }
-    if (count > 0) chunks[atomicAdd(nchunks, 1)] = make_int4(first, count, cls, ixlo | (ixhi << 16));
-  }
+  for (int cls = blockIdx.x * blockDim.x + threadIdx.x; cls < ncls; cls += gridDim.x * blockDim.x)
+    chunk_walk(start, cls * l1, l1, gs, [&](int first, int count, int ixlo, int ixhi) {
+      chunks[atomicAdd(nchunks, 1)] = make_int4(first, count, cls, ixlo | (ixhi << 16));
+    });
 }
 
 // Queue entry: partner index (21 bits), coarse-band flag (1), row (5),
@@ -280,6 +288,54 @@ cudaError_t launch_force_chunk(nemd_ctx *c, float *F, int *nblocks) {
 #undef NEMD_LAUNCH
 #undef NEMD_ARGS
   c->launches += 1;
+  return cudaGetLastError();
+}
+
+
+// ---- batches: chunk lists in a fixed order (count per class slot, scan, write),
+// so that the chunk of a particle and every sum are the same from run to run ----
+
+__device__ __forceinline__ bool batch_class(const BatchView &v, int slot, const Geo *&g, int &c0, int &l1) {
+  const int s = v.class_sys[slot];
+  g = v.geo + s;
+  if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return false;
+  const SysInfo si = v.sys[s];
+  const int cls = slot - si.clo;
+  if (cls >= g->nc[1] * g->nc[2]) return false;
+  l1 = g->nc[0];
+  c0 = si.coff + cls * l1;
+  return true;
+}
+
+__global__ void k_b_chunk_count(BatchView v) {
+  for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < v.nclasses; slot += gridDim.x * blockDim.x) {
+    const Geo *g;
+    int c0, l1, n = 0;
+    if (batch_class(v, slot, g, c0, l1)) chunk_walk(v.start, c0, l1, v.gs, [&](int, int, int, int) { n++; });
+    v.chunk_cnt[slot] = n;
+  }
+}
+
+__global__ void k_b_chunk_write(BatchView v) {
+  for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < v.nclasses; slot += gridDim.x * blockDim.x) {
+    const Geo *g;
+    int c0, l1;
+    if (!batch_class(v, slot, g, c0, l1)) continue;
+    int k = v.chunk_off[slot];
+    chunk_walk(v.start, c0, l1, v.gs, [&](int first, int count, int ixlo, int ixhi) {
+      v.chunks[k++] = make_int4(first, count, slot, ixlo | (ixhi << 16));
+    });
+  }
+}
+
+cudaError_t launch_batch_chunks(cudaStream_t st, const BatchView &v, int sms) {
+  int blocks = (v.nclasses + 127) / 128;
+  if (blocks > 16 * sms) blocks = 16 * sms;
+  if (blocks < 1) blocks = 1;
+  k_b_chunk_count<<<blocks, 128, 0, st>>>(v);
+  cudaError_t e = launch_fixed_scan(st, v.chunk_cnt, v.chunk_off, v.chunk_tiles, v.nclasses);
+  if (e != cudaSuccess) return e;
+  k_b_chunk_write<<<blocks, 128, 0, st>>>(v);
   return cudaGetLastError();
 }
 

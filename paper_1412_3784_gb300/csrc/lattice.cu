@@ -10,7 +10,7 @@
 //   dynamic offset: l_i = floor((1 - 1e-12) k r_ii / rc)    (Sec. 5.2)
 #include <math.h>
 
-#include "nemd_internal.cuh"
+#include "batch_internal.cuh"
 
 namespace nemd {
 
@@ -48,8 +48,9 @@ __device__ __forceinline__ void set_shift(Row &r, double ox, double oy, double o
 
 }  // namespace
 
-// One warp.  validate != 0: compute exp(tau_in A) L0 only (for the KR check).
-__global__ void k_lattice(Geo *g, LatIn in) {
+// One warp (the whole block).  validate != 0: compute exp(tau_in A) L0 only
+// (for the KR check).
+__device__ __forceinline__ void lattice_body(Geo *g, const LatIn &in) {
   const int validate = in.validate;
   const double tau_in = in.tau;
   __shared__ double B[9], P[9], E[9], Ls[9], Gm[9], Rm[9], Ri[9], Lt[9];
@@ -177,15 +178,15 @@ __global__ void k_lattice(Geo *g, LatIn in) {
   mm3(Ls, Ri, Ri, lane);  // Q = L R^-1
   if (lane < 9) g->Q[lane] = Ri[lane];
   __syncwarp();
-
 }
+
+__global__ void k_lattice(Geo *g, LatIn in) { lattice_body(g, in); }
 
 // Single thread: cell counts of both variants at k = 1, their neighbourhood
 // volumes (Sec. 5.1: V_DS = 27 V / (c1 c2 c3); Sec. 5.2: V_DO = avg r11 r22 r33 /
 // (l1 l2 l3) with avg = 27 + 14/l3 + 6/l2 - 4/(l2 l3)), the variant of this step,
 // its grid at cell factor k, and the float32 guard band.
-__global__ void k_grid(Geo *g, GridIn in) {
-  if (threadIdx.x != 0) return;
+__device__ void grid_body(Geo *g, const GridIn &in) {
   g->rc = in.rc;
   g->req_variant = in.variant;
   g->kfac = in.kfac;
@@ -317,18 +318,21 @@ __global__ void k_grid(Geo *g, GridIn in) {
   g->rc2_hi = __double2float_ru(rc * rc + band);
 }
 
-// One thread per home (iy, iz): the neighbour rows of that class.
-__global__ void k_stencil(Geo *g, Row *rows, int *rowcnt) {
-  if (g->error) return;
+__global__ void k_grid(Geo *g, GridIn in) {
+  if (threadIdx.x == 0) grid_body(g, in);
+}
+
+// The neighbour rows of one home (iy, iz) class, written to out[0..maxrows);
+// returns their number.  cell_base is added to every row's first cell (the
+// system's first cell slot in a batch).
+__device__ int stencil_class(Geo *g, int cls, int cell_base, Row *out) {
   const int l1 = g->nc[0], l2 = g->nc[1], l3 = g->nc[2];
-  const int ncls = l2 * l3;
   const int maxrows = g->maxrows;
   const int variant = g->variant;
   const double rce = g->rc * (1.0 + kMargin);
   const double q = g->quantum;
-  for (int cls = blockIdx.x * blockDim.x + threadIdx.x; cls < ncls; cls += gridDim.x * blockDim.x) {
+  {
     const int iy = cls % l2, iz = cls / l2;
-    Row *out = rows + (size_t)cls * maxrows;
     int nr = 0;
     if (variant == NEMD_DS) {
       const int K = g->kfac;
@@ -340,7 +344,7 @@ __global__ void k_stencil(Geo *g, Row *rows, int *rowcnt) {
           const double c1 = dy, c2 = dz;
           Row r;
           set_shift(r, g->G[1] * c1 + g->G[2] * c2, g->G[4] * c1 + g->G[5] * c2, g->G[7] * c1 + g->G[8] * c2, q);
-          r.cbase = l1 * (jy + l2 * jz);
+          r.cbase = cell_base + l1 * (jy + l2 * jz);
           r.sxi = 0;
           r.dxlo = -K;
           r.cnt = 2 * K + 1;
@@ -368,7 +372,7 @@ __global__ void k_stencil(Geo *g, Row *rows, int *rowcnt) {
           Row r;
           const double sxi = rint(sx / w1);
           set_shift(r, sx - sxi * w1, (double)(jyu - iy) * w2 + yshift, (double)(jzu - iz) * w3, q);
-          r.cbase = l1 * (jy + l2 * jz);
+          r.cbase = cell_base + l1 * (jy + l2 * jz);
           r.sxi = (int)sxi;
           r.dxlo = xlo;
           r.cnt = xhi - xlo + 1;
@@ -384,8 +388,16 @@ __global__ void k_stencil(Geo *g, Row *rows, int *rowcnt) {
       atomicOr(&g->error, ERRB_CAPACITY);
       nr = maxrows;
     }
-    rowcnt[cls] = nr;
+    return nr;
   }
+}
+
+// One thread per home (iy, iz): the neighbour rows of that class.
+__global__ void k_stencil(Geo *g, Row *rows, int *rowcnt) {
+  if (g->error) return;
+  const int ncls = g->nc[1] * g->nc[2];
+  for (int cls = blockIdx.x * blockDim.x + threadIdx.x; cls < ncls; cls += gridDim.x * blockDim.x)
+    rowcnt[cls] = stencil_class(g, cls, 0, rows + (size_t)cls * g->maxrows);
 }
 
 cudaError_t launch_lattice(nemd_ctx *c, int validate, double tau) {
@@ -424,6 +436,61 @@ cudaError_t launch_stencil(nemd_ctx *c) {
   if (blocks < 1) blocks = 1;
   k_stencil<<<(int)blocks, threads, 0, c->stream>>>(c->geo, c->rows, c->rowcnt);
   c->launches += 1;
+  return cudaGetLastError();
+}
+
+
+// ---- batches: one launch over every system (or every sampled state) ----
+
+__global__ void k_b_lattice(Geo *geo, const LatIn *__restrict__ lat, const double *__restrict__ t) {
+  LatIn in = lat[blockIdx.x];
+  if (t) in.t = t[blockIdx.x];
+  lattice_body(geo + blockIdx.x, in);
+}
+
+__global__ void k_b_grid(Geo *geo, const GridIn *__restrict__ grid, const SysInfo *__restrict__ sys, int count) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= count) return;
+  Geo *g = geo + e;
+  grid_body(g, grid[e]);
+  // the batch sizes a system's row classes from its states over one period
+  if (sys && !(g->error & ERRB_BOX) && (long long)g->nc[1] * g->nc[2] > (long long)sys[e].clcap) {
+    g->error |= ERRB_CAPACITY;
+    g->ncells = 0;
+  }
+}
+
+// blockIdx.y = system; threads stride over its classes.
+__global__ void k_b_stencil(BatchView v) {
+  const int s = blockIdx.y;
+  Geo *g = v.geo + s;
+  if (g->error) return;
+  const SysInfo si = v.sys[s];
+  const int ncls = g->nc[1] * g->nc[2];
+  for (int cls = blockIdx.x * blockDim.x + threadIdx.x; cls < ncls; cls += gridDim.x * blockDim.x) {
+    const int slot = si.clo + cls;
+    v.rowcnt[slot] = stencil_class(g, cls, si.coff, v.rows + (size_t)slot * kBatchRowStride);
+  }
+}
+
+cudaError_t launch_batch_lattice(cudaStream_t st, Geo *geo, const LatIn *lat, const double *t, int count) {
+  if (count <= 0) return cudaSuccess;
+  k_b_lattice<<<count, 32, 0, st>>>(geo, lat, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_grid(cudaStream_t st, Geo *geo, const GridIn *grid, const SysInfo *sys, int count) {
+  if (count <= 0) return cudaSuccess;
+  k_b_grid<<<(count + 63) / 64, 64, 0, st>>>(geo, grid, sys, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_stencil(cudaStream_t st, const BatchView &v, int max_clcap) {
+  const int threads = 128;
+  int bx = (max_clcap + threads - 1) / threads;
+  if (bx < 1) bx = 1;
+  if (bx > 64) bx = 64;
+  k_b_stencil<<<dim3(bx, v.nsys), threads, 0, st>>>(v);
   return cudaGetLastError();
 }
 

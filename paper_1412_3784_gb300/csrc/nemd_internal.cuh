@@ -215,5 +215,7 @@ void tune_apply(nemd_ctx *c, double rc);
 // learned selector inference for this step (mlp.cu)
 cudaError_t launch_learned_choice(nemd_ctx *c, double rc);
 cudaError_t launch_force_chunk(nemd_ctx *c, float *F_dev, int *nblocks);
+// status code and message of a set of device error bits (capi.cu)
+int status_from_bits(int bits, const char **what);
 
 }  // namespace nemd

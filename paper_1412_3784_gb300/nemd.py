@@ -40,7 +40,11 @@ EXPORTED = ["nemd_create", "nemd_destroy", "nemd_set_flow", "nemd_set_potential"
             "nemd_get_kernel_time", "nemd_measure_peaks", "nemd_forces_noalloc", "nemd_autotune",
             "nemd_tune_save", "nemd_tune_load", "nemd_features", "nemd_time_options", "nemd_model_train",
             "nemd_model_predict", "nemd_model_grad", "nemd_model_set_params", "nemd_model_get_params",
-            "nemd_model_save", "nemd_model_load"]
+            "nemd_model_save", "nemd_model_load", "nemd_batch_create", "nemd_batch_destroy",
+            "nemd_batch_last_error", "nemd_batch_add", "nemd_batch_finalize", "nemd_batch_offsets",
+            "nemd_batch_set_state", "nemd_batch_compute", "nemd_batch_sync", "nemd_batch_set_option",
+            "nemd_batch_get_stats", "nemd_batch_autotune"]
+NEMD_BATCH_OPT_CELL_FACTOR, NEMD_BATCH_OPT_TILE, NEMD_BATCH_OPT_GRAPH = 1, 2, 3
 NEMD_MLP_INPUTS, NEMD_MLP_OUTPUTS, NEMD_MLP_PARAMS, NEMD_MLP_NORM = 12, 4, 5252, 26
 NEMD_NOALLOC_MAX_N = 16384
 NEMD_NOALLOC_MAX_CELLS = 16384
@@ -61,6 +65,19 @@ class nemd_tune_config(ctypes.Structure):
 
 class nemd_tune_entry(ctypes.Structure):
     _fields_ = [("cfg", nemd_tune_config), ("ms", ctypes.c_double)]
+
+
+class nemd_system(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_double * 9), ("L0", ctypes.c_double * 9), ("M", ctypes.c_int64 * 9),
+                ("T", ctypes.c_double), ("eps", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("rc", ctypes.c_double), ("n", ctypes.c_int64), ("kind", ctypes.c_int32),
+                ("shift", ctypes.c_int32), ("variant", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class nemd_batch_stats(ctypes.Structure):
+    _fields_ = [("pairs", ctypes.c_int64), ("candidates", ctypes.c_int64), ("band", ctypes.c_int64),
+                ("counts", ctypes.c_int32 * 3), ("variant", ctypes.c_int32), ("cell_factor", ctypes.c_int32),
+                ("status", ctypes.c_int32)]
 
 
 _vp = ctypes.c_void_p
@@ -95,6 +112,19 @@ _sig = {
     "nemd_model_get_params": ([_vp, _vp, _vp], ctypes.c_int),
     "nemd_model_save": ([_vp, ctypes.c_char_p], ctypes.c_int),
     "nemd_model_load": ([_vp, ctypes.c_char_p], ctypes.c_int),
+    "nemd_batch_create": ([ctypes.POINTER(_vp), ctypes.c_int, _vp], ctypes.c_int),
+    "nemd_batch_destroy": ([_vp], ctypes.c_int),
+    "nemd_batch_last_error": ([_vp], ctypes.c_char_p),
+    "nemd_batch_add": ([_vp, ctypes.POINTER(nemd_system), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "nemd_batch_finalize": ([_vp], ctypes.c_int),
+    "nemd_batch_offsets": ([_vp, _vp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "nemd_batch_set_state": ([_vp, _vp, _vp], ctypes.c_int),
+    "nemd_batch_compute": ([_vp, _vp, _vp], ctypes.c_int),
+    "nemd_batch_sync": ([_vp, _vp], ctypes.c_int),
+    "nemd_batch_set_option": ([_vp, ctypes.c_int, ctypes.c_int64], ctypes.c_int),
+    "nemd_batch_get_stats": ([_vp, ctypes.POINTER(nemd_batch_stats), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "nemd_batch_autotune": ([_vp, ctypes.c_int, ctypes.POINTER(nemd_tune_entry), ctypes.c_int,
+                             ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "nemd_forces_noalloc": ([_vp, _vp, ctypes.c_double, ctypes.c_double, _vp, ctypes.c_int64, ctypes.c_int,
                              ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                              _vp, _vp, _vp, _vp], ctypes.c_int),
@@ -298,3 +328,91 @@ class Context:
         self._check(nemd_get_pairs(self.h, out.ctypes.data, n, ctypes.byref(cnt)))
         return out[: int(cnt.value)]
 
+
+class Batch:
+    """One nemd_batch: many independent systems evaluated by one launch per stage
+    (a captured CUDA graph).  `systems` is a list of dicts with the keys of
+    nemd_system: A, L0, M, T, rc, n, and optionally kind, eps, sigma, shift,
+    variant."""
+
+    def __init__(self, systems, device=0, stream=None):
+        if stream is None:
+            stream = _current_stream(device)
+        h = _vp()
+        rc = nemd_batch_create(ctypes.byref(h), int(device), _vp(stream))
+        if rc:
+            raise NemdError(rc, "nemd_batch_create")
+        self.h = h
+        self._keep = {}
+        for s in systems:
+            y = nemd_system()
+            y.A[:] = [float(x) for x in np.asarray(s["A"], dtype=np.float64).ravel()]
+            y.L0[:] = [float(x) for x in np.asarray(s["L0"], dtype=np.float64).ravel()]
+            y.M[:] = [int(x) for x in np.asarray(s["M"], dtype=np.int64).ravel()]
+            y.T = float(s["T"])
+            y.eps = float(s.get("eps", 1.0))
+            y.sigma = float(s.get("sigma", 1.0))
+            y.rc = float(s["rc"])
+            y.n = int(s["n"])
+            y.kind = int(s.get("kind", NEMD_LJ))
+            y.shift = int(s.get("shift", 1))
+            y.variant = int(s.get("variant", NEMD_AUTO_HEURISTIC))
+            self._check(nemd_batch_add(self.h, ctypes.byref(y), None))
+        self._check(nemd_batch_finalize(self.h))
+        ns = ctypes.c_int64()
+        nemd_batch_offsets(self.h, None, ctypes.byref(ns))
+        self.nsys = ns.value
+        self.offsets = np.zeros(self.nsys + 1, dtype=np.int64)
+        nemd_batch_offsets(self.h, self.offsets.ctypes.data, ctypes.byref(ns))
+        self.ntot = int(self.offsets[-1])
+
+    def close(self):
+        if self.h:
+            nemd_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc:
+            raise NemdError(rc, nemd_batch_last_error(self.h).decode())
+        return rc
+
+    def set_state(self, q, t):
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        self._keep["q"] = q
+        self._keep["t"] = t
+        return self._check(nemd_batch_set_state(self.h, _ptr(q), t.ctypes.data))
+
+    def compute(self, F=None, UW=None):
+        return self._check(nemd_batch_compute(self.h, _ptr(F), _ptr(UW)))
+
+    def sync(self, status=False):
+        st = np.zeros(self.nsys, dtype=np.int32)
+        rc = nemd_batch_sync(self.h, st.ctypes.data)
+        if status:
+            return st
+        self._check(rc)
+        return st
+
+    def set_option(self, key, value):
+        return self._check(nemd_batch_set_option(self.h, int(key), int(value)))
+
+    def stats(self):
+        arr = (nemd_batch_stats * self.nsys)()
+        nl = ctypes.c_int64()
+        self._check(nemd_batch_get_stats(self.h, arr, ctypes.byref(nl)))
+        out = [{"pairs": a.pairs, "candidates": a.candidates, "band": a.band, "counts": tuple(a.counts),
+                "variant": a.variant, "cell_factor": a.cell_factor, "status": a.status} for a in arr]
+        return out, nl.value
+
+    def autotune(self, reps=3):
+        times = (nemd_tune_entry * 8)()
+        nt = ctypes.c_int()
+        self._check(nemd_batch_autotune(self.h, int(reps), times, 8, ctypes.byref(nt)))
+        return [({"tile": times[k].cfg.group, "cell_factor": times[k].cfg.cell_factor}, times[k].ms)
+                for k in range(nt.value)]
