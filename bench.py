@@ -9,12 +9,22 @@ N = 1,048,576 perturbed-FCC LJ system (rc = 2.5).  Every strain has its own
 24 MB position array, so a step streams inputs far larger than L2.
 
 Printed as one JSON line (rank 0):
-  value        pairs/s of the tuned form (per-step variant choice, tuned kernel)
+  value        pairs/s of the tuned form: the library's autotuner picks the
+               force kernel, lanes per group and cell factor; the cell list of
+               each strain is the paper's neighbourhood-volume choice
   plain        pairs/s of the plain fixed-variant cell lists on the same steps
   e2e          pairs/s through the C ABI with pinned host buffers, copies timed
   roofline     force kernel: algorithmic FP32 instructions / launch time against
                the FP32 issue peak (bound "alu")
   cpu_baseline the FP64 oracle on a bounded sample, on the host cores
+  batched      256 independent systems (N ~ U[1000, 20000], planar or general
+               flow, WCA or LJ) as one batch: one launch per stage, replayed
+               CUDA graph, autotuned cell factor and tile; against a loop of
+               per-system contexts with the plain kernel
+  learned      the learned cell-list selector, trained on timings of the
+               N = 32000 planar, N = 256000 general and batched systems, driving
+               the N = 2,097,152 general-flow system: regret against the
+               exhaustive choice, pairs/s against the plain fixed variants
 
 --impl reference times the oracle (the reference arm of this project) on the
 same workload, one strain per step.
@@ -39,7 +49,7 @@ WORKLOADS = {
     # name: (k for N = 4k^3, strains per period)
     "general_n1m": (64, 128),
     "general_n256k": (40, 128),
-    "general_n2m": (80, 256),
+    "general_n2m": (0, 256),   # N = 2^21: FCC 81^3 with vacancies
 }
 C_TEST = 7     # FP32 instructions per candidate test: 3 FADD, 1 FMUL, 2 FFMA, 1 FSETP
 C_PAIR = 24    # FP32 instructions per interacting pair (force, energy, virial, both sides)
@@ -55,9 +65,16 @@ def parse():
     p.add_argument("--strains", type=int, default=0, help="strains per step (default: the workload's)")
     p.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle sample")
     p.add_argument("--e2e-strains", type=int, default=16)
-    p.add_argument("--kernel", type=int, default=1, help="force kernel of the tuned form (0 plain, 1 grouped)")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="tuned form with --kernel/--group/--kfac instead of the autotuner's choice")
+    p.add_argument("--kernel", type=int, default=2, help="force kernel without autotuning (0 plain, 1 grouped, 2 warp)")
     p.add_argument("--group", type=int, default=16, help="lanes per group of the grouped kernel")
-    p.add_argument("--kfac", type=int, default=1, help="cell-size factor of the tuned form")
+    p.add_argument("--kfac", type=int, default=1, help="cell-size factor without autotuning")
+    p.add_argument("--sections", default="main,batched,learned",
+                   help="comma list of main, batched, learned")
+    p.add_argument("--batch-steps", type=int, default=10)
+    p.add_argument("--learned-strains", type=int, default=64,
+                   help="strains of the N = 2^21 system in the learned section (256 = one per period step)")
     return p.parse_args()
 
 
@@ -160,7 +177,7 @@ def run_reference(args, rank, world):
     import oracle
     from paper_1412_3784_gb300 import workloads as W
     k, nstrain = WORKLOADS[args.workload]
-    ser = W.general_series(k=k)
+    ser = series_for(W, k)
     ts = [i / nstrain for i in range(nstrain)]
     pairs = 0
     elapsed = 0.0
@@ -188,6 +205,10 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def series_for(W, k):
+    return W.general_series_2m() if k == 0 else W.general_series(k=k)
+
+
 def cpu_baseline_sample(ser, t):
     import oracle
     w = ser.workload(t)
@@ -199,28 +220,30 @@ def cpu_baseline_sample(ser, t):
                       f"general-flow system at t={t:.4f}: {r.npairs} pairs in {dt:.2f} s"}
 
 
-def main():
-    args = parse()
-    rank, world, local = dist_init(args)
-    if args.impl == "reference":
-        run_reference(args, rank, world)
-        barrier(world)
-        return
+def timed_loop(torch, dev, world, fn, steps, warmup):
+    """CUDA-event time (ms) of `steps` calls of fn after `warmup` untimed ones,
+    bracketed by a barrier and a device synchronise on both sides."""
+    for _ in range(warmup):
+        fn()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    return e0.elapsed_time(e1)
 
-    import torch
 
-    import __graft_entry__
-    __graft_entry__.build()
-    from paper_1412_3784_gb300 import nemd
-    from paper_1412_3784_gb300 import workloads as W
-
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
+def section_main(args, rank, world, dev, torch, nemd, W):
     k, nstrain = WORKLOADS[args.workload]
     S = args.strains or nstrain
-    ser = W.general_series(k=k)
+    ser = series_for(W, k)
     n = ser.n
-    ts = [i / S for i in range(S)]
+    ts = [i / S * ser.period for i in range(S)]
     q_all = torch.empty((S, n, 3), dtype=torch.float64, device=dev)
     for i, t in enumerate(ts):
         q_all[i].copy_(torch.from_numpy(ser.positions(t)))
@@ -228,18 +251,33 @@ def main():
     U = torch.zeros(1, dtype=torch.float64, device=dev)
     Wv = torch.zeros(9, dtype=torch.float64, device=dev)
 
-    ctx = nemd.Context(local)
+    ctx = nemd.Context(dev.index)
     ctx.set_flow(ser.A, ser.L0, ser.M, ser.period)
     ctx.set_potential(nemd.NEMD_LJ, 1.0, 1.0, 1)
 
+    # the tuned form: the autotuner's choice on three strains (start, middle,
+    # just before the remap), applied from its cache at every build
+    tune = None
+    if not args.no_autotune:
+        ctx.set_option(nemd.NEMD_OPT_AUTOTUNED, 0)
+        for t in (0.0, 0.5 * ser.period, W.NEAR_REMAP_T * ser.period):
+            ctx.set_state(torch.from_numpy(ser.positions(t)).to(dev), t)
+            best, times = ctx.autotune(nemd.NEMD_AUTO_HEURISTIC, ser.rc, reps=2)
+        tune = {"choice": best, "last_call_ms": [[c["kernel"], c["group"], c["cell_factor"], round(ms, 4)]
+                                                 for c, ms in times]}
+
     def configure(kind):
+        ctx.set_option(nemd.NEMD_OPT_AUTOTUNED, 0)
         if kind == "plain_ds" or kind == "plain_do":
             ctx.set_option(nemd.NEMD_OPT_KERNEL, 0)
             ctx.set_option(nemd.NEMD_OPT_CELL_FACTOR, 1)
             return nemd.NEMD_DS if kind == "plain_ds" else nemd.NEMD_DO
-        ctx.set_option(nemd.NEMD_OPT_KERNEL, args.kernel)
-        ctx.set_option(nemd.NEMD_OPT_GROUP, args.group)
-        ctx.set_option(nemd.NEMD_OPT_CELL_FACTOR, args.kfac)
+        if tune is not None:
+            ctx.set_option(nemd.NEMD_OPT_AUTOTUNED, 1)
+        else:
+            ctx.set_option(nemd.NEMD_OPT_KERNEL, args.kernel)
+            ctx.set_option(nemd.NEMD_OPT_GROUP, args.group)
+            ctx.set_option(nemd.NEMD_OPT_CELL_FACTOR, args.kfac)
         return nemd.NEMD_AUTO_HEURISTIC
 
     def one_step(variant):
@@ -252,7 +290,7 @@ def main():
     per = {}
     for kind in ("plain_ds", "plain_do", "tuned"):
         variant = configure(kind)
-        pairs, cands, variants, rech = [], [], [], []
+        pairs, cands, variants, rech, kf = [], [], [], [], []
         for i in range(S):
             ctx.set_state(q_all[i], ts[i])
             ctx.build_cells(variant, ser.rc)
@@ -263,7 +301,8 @@ def main():
             cands.append(st["candidates"])
             variants.append(st["variant"])
             rech.append(st["rechecks"])
-        per[kind] = {"pairs": pairs, "cands": cands, "variants": variants, "rechecks": rech}
+            kf.append(st["cell_factor"])
+        per[kind] = {"pairs": pairs, "cands": cands, "variants": variants, "rechecks": rech, "kfac": kf}
     pairs_per_step = sum(per["tuned"]["pairs"])
     assert pairs_per_step == sum(per["plain_ds"]["pairs"]) == sum(per["plain_do"]["pairs"])
     # algorithmic FP32 instructions of the tuned step, per the k = 1 stencil of the
@@ -274,45 +313,34 @@ def main():
         cand_k1 = (per["plain_do"] if v == 1 else per["plain_ds"])["cands"][i]
         ops_step += 0.5 * C_TEST * cand_k1 + C_PAIR * per["tuned"]["pairs"][i]
 
-    def timed(kind, steps, warmup, timing=False):
-        variant = configure(kind)
-        for _ in range(warmup):
-            one_step(variant)
-        ctx.sync()
-        if timing:
-            ctx.set_option(nemd.NEMD_OPT_TIMING, 1)
-        launches0 = ctx.stats()["launches"]
-        barrier(world)
-        torch.cuda.synchronize(dev)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(steps):
-            one_step(variant)
-        e1.record()
-        torch.cuda.synchronize(dev)
-        barrier(world)
-        ms = e0.elapsed_time(e1)
-        launches = ctx.stats()["launches"] - launches0
-        ctx.sync()
-        kt = None
-        if timing:
-            kt = ctx.kernel_time()
-            ctx.set_option(nemd.NEMD_OPT_TIMING, 0)
-        return ms, launches, kt
-
-    clocks = Clocks(local)
+    clocks = Clocks(dev.index)
+    variant = configure("tuned")
+    for _ in range(args.warmup):
+        one_step(variant)
+    ctx.sync()
+    ctx.set_option(nemd.NEMD_OPT_TIMING, 1)
+    launches0 = ctx.stats()["launches"]
     clocks.start()
-    ms_tuned, launches, ktime = timed("tuned", args.steps, args.warmup, timing=True)
+    torch.cuda.nvtx.range_push("timed_tuned")   # marks the timed region for profilers
+    ms_tuned = timed_loop(torch, dev, world, lambda: one_step(variant), args.steps, 0)
+    torch.cuda.nvtx.range_pop()
     clk = clocks.stop()
-    ms_ds, _, _ = timed("plain_ds", args.steps, 1)
-    ms_do, _, _ = timed("plain_do", args.steps, 1)
+    launches = ctx.stats()["launches"] - launches0
+    ctx.sync()
+    k_ms, k_n = ctx.kernel_time()
+    ctx.set_option(nemd.NEMD_OPT_TIMING, 0)
+    kernel_name = {0: "k_force_plain", 1: "k_force_chunk", 2: "k_force_warp"}
+    tuned_kernel = tune["choice"]["kernel"] if tune is not None else args.kernel
+    v_ds = configure("plain_ds")
+    ms_ds = timed_loop(torch, dev, world, lambda: one_step(v_ds), args.steps, 1)
+    v_do = configure("plain_do")
+    ms_do = timed_loop(torch, dev, world, lambda: one_step(v_do), args.steps, 1)
 
     ms_tuned_max = max_over_ranks(ms_tuned, world, dev)
     total_pairs = sum_over_ranks(float(pairs_per_step * args.steps), world, dev)
     value = total_pairs / (ms_tuned_max * 1e-3)
-    plain_ds = sum_over_ranks(float(pairs_per_step * args.steps), world, dev) / (max_over_ranks(ms_ds, world, dev) * 1e-3)
-    plain_do = sum_over_ranks(float(pairs_per_step * args.steps), world, dev) / (max_over_ranks(ms_do, world, dev) * 1e-3)
+    plain_ds = total_pairs / (max_over_ranks(ms_ds, world, dev) * 1e-3)
+    plain_do = total_pairs / (max_over_ranks(ms_do, world, dev) * 1e-3)
 
     # roofline of the force kernel (FP32 issue bound)
     props = torch.cuda.get_device_properties(dev)
@@ -324,15 +352,15 @@ def main():
     except (OSError, ValueError):
         pass
     peak = fp32_issue_peak(sms, peak_mhz)
-    k_ms, k_n = ktime
     avg_launch_s = (k_ms / k_n) * 1e-3
     ops_per_launch = ops_step / S
     achieved = ops_per_launch / avg_launch_s
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
-                "kernel": "k_force_chunk" if args.kernel == 1 else "k_force_plain", "ops_per_launch": ops_per_launch,
+                "kernel": kernel_name.get(tuned_kernel, "?"), "ops_per_launch": ops_per_launch,
                 "avg_launch_ms": avg_launch_s * 1e3,
-                "peak_basis": f"{sms} SMs x 128 FP32 lanes x {peak_mhz:.0f} MHz (FP32 instruction lane-ops/s)"}
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x {peak_mhz:.0f} MHz (FP32 instruction "
+                              f"lane-ops/s; derived from unit counts and the clock, not measured)"}
 
     # end to end through the C ABI with pinned host buffers
     Se = min(args.e2e_strains, S)
@@ -358,6 +386,8 @@ def main():
     e2e = {"value": e2e_pairs / e2e_s, "unit": "pairs/s",
            "h2d_bytes_per_step": int(S * n * 3 * 8), "d2h_bytes_per_step": int(S * (n * 3 * 4 + 80)),
            "strains_timed": Se}
+    ctx.close()
+    del q_all
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_baseline:
@@ -365,32 +395,214 @@ def main():
 
     eta_ds = 2 * sum(per["plain_ds"]["pairs"]) / sum(per["plain_ds"]["cands"])
     eta_do = 2 * sum(per["plain_do"]["pairs"]) / sum(per["plain_do"]["cands"])
+    ndo = sum(1 for v in per["tuned"]["variants"] if v == 1)
+    return {
+        "value": value, "ms_per_step": ms_tuned_max / args.steps,
+        "config": {"workload": f"{args.workload}: general 3D flow M=[[3,2,1],[2,2,1],[1,1,1]], "
+                               f"perturbed FCC N={n}, rho=0.8442, LJ rc=2.5, {S} strains per step "
+                               f"(one period), one force evaluation per strain",
+                   "n": n, "strains_per_step": S, "pairs_per_step": pairs_per_step,
+                   "tuned": (f"autotuned: kernel {tune['choice']['kernel']}, group {tune['choice']['group']}, "
+                             f"cell factor {tune['choice']['cell_factor']}" if tune is not None else
+                             f"kernel {args.kernel} (group {args.group}), cell factor {args.kfac}") +
+                            f"; cell list per strain by neighbourhood volume (dynamic offset at {ndo} of {S})",
+                   "coarse_band_candidates_per_step": int(sum(per["tuned"]["rechecks"])),
+                   "l2": "inputs larger than L2: a distinct 24 MB position array per strain",
+                   "parallelism": f"replicas x{world}"},
+        "plain": {"dynamic_size_pairs_per_s": plain_ds, "dynamic_offset_pairs_per_s": plain_do,
+                  "tuned_over_best_plain": value / max(plain_ds, plain_do),
+                  "search_efficiency_ds": eta_ds, "search_efficiency_do": eta_do},
+        "autotune": tune,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+    }
+
+
+def section_batched(args, world, dev, torch, nemd, W):
+    """256 independent systems: one batch (graph replay) against per-system contexts."""
+    ws = W.batched_systems()
+    kinds = [nemd.NEMD_WCA if w.kind == W.POT_WCA else nemd.NEMD_LJ for w in ws]
+    specs = [{"A": w.A, "L0": w.L0, "M": w.M, "T": w.T, "rc": w.rc, "n": w.n, "kind": kd,
+              "variant": nemd.NEMD_AUTO_HEURISTIC} for w, kd in zip(ws, kinds)]
+    t0 = time.perf_counter()
+    b = nemd.Batch(specs, device=dev.index)
+    t_final = time.perf_counter() - t0
+    q = torch.from_numpy(np.concatenate([w.q for w in ws])).to(dev)
+    ts = [w.t for w in ws]
+    F = torch.zeros((b.ntot, 3), dtype=torch.float32, device=dev)
+    UW = torch.zeros((b.nsys, 10), dtype=torch.float64, device=dev)
+    b.set_state(q, ts)
+    times = b.autotune(reps=3)
+    b.compute(F, UW)
+    b.sync()
+    st, launches = b.stats()
+    pairs = sum(x["pairs"] for x in st)
+    ms = timed_loop(torch, dev, world, lambda: b.compute(F, UW), args.batch_steps, 3) / args.batch_steps
+    b.sync()
+    best = min(times, key=lambda x: x[1])[0]
+    b.close()
+    # the same systems through per-system contexts: plain kernel, fixed dynamic size cell list
+    ctxs = []
+    for w, kd in zip(ws, kinds):
+        c = nemd.Context(dev.index)
+        c.set_flow(w.A, w.L0, w.M, w.T)
+        c.set_potential(kd, 1.0, 1.0, 1)
+        ctxs.append(c)
+    qs = [q[b.offsets[s]:b.offsets[s + 1]] for s in range(len(ws))]
+    Fs = [F[b.offsets[s]:b.offsets[s + 1]] for s in range(len(ws))]
+
+    def loop():
+        for s, c in enumerate(ctxs):
+            c.set_state(qs[s], ts[s])
+            c.build_cells(nemd.NEMD_DS, ws[s].rc)
+            c.compute_forces(Fs[s])
+    ms_loop = timed_loop(torch, dev, world, loop, 2, 1) / 2
+    pairs_loop = sum(c.stats()["pairs"] for c in ctxs)
+    for c in ctxs:
+        c.close()
+    assert pairs_loop == pairs
+    return {"workload": f"{len(ws)} systems, N ~ U[1000, 20000] (total {b.ntot}), density ~ U(0.8, 0.9), "
+                        "planar or general flow at rate ~ U(0.5, 2) and random phase, WCA or LJ rc 2.5",
+            "pairs_per_step": pairs, "ms_per_step": ms, "pairs_per_s": pairs / ms * 1e3,
+            "kernel_launches_per_step": launches,
+            "autotuned": {"cell_factor": best["cell_factor"], "tile": best["tile"],
+                          "candidates_ms": [[c["cell_factor"], c["tile"], round(t, 4)] for c, t in times]},
+            "finalize_s": t_final,
+            "per_system_loop": {"ms_per_step": ms_loop, "pairs_per_s": pairs / ms_loop * 1e3,
+                                "form": "one context per system, plain kernel, dynamic size cell list"},
+            "speedup_over_loop": ms_loop / ms}
+
+
+def section_learned(args, dev, torch, nemd, W):
+    """Learned selector: trained on timing rows of the N = 32000 planar, N = 256000
+    general and batched systems; judged on the N = 2^21 general-flow system."""
+    ctx = nemd.Context(dev.index)
+    ctx.set_option(nemd.NEMD_OPT_KERNEL, 2)
+    X, T = [], []
+    t0 = time.perf_counter()
+    for ser, m in ((W.planar_series(k=20), 32), (W.general_series(k=40), 32)):
+        ctx.set_flow(ser.A, ser.L0, ser.M, ser.period)
+        ctx.set_potential(nemd.NEMD_LJ, 1.0, 1.0, 1)
+        for i in range(m):
+            t = (i + 0.5) / m * ser.period
+            ctx.set_state(torch.from_numpy(ser.positions(t)).to(dev), t)
+            f, ms = ctx.time_options(ser.rc, reps=2)
+            X.append(f)
+            T.append(ms)
+    for w in W.batched_systems()[:64]:
+        ctx.set_flow(w.A, w.L0, w.M, w.T)
+        ctx.set_potential(nemd.NEMD_WCA if w.kind == W.POT_WCA else nemd.NEMD_LJ, 1.0, 1.0, 1)
+        ctx.set_state(torch.from_numpy(w.q).to(dev), w.t)
+        try:
+            f, ms = ctx.time_options(w.rc, reps=2)
+        except nemd.NemdError:
+            continue                  # an option whose box is too small for the cut-off
+        X.append(f)
+        T.append(ms)
+    t_rows = time.perf_counter() - t0
+    X = np.array(X)
+    T = np.array(T)
+    t0 = time.perf_counter()
+    hist = ctx.model_train(X, T, steps=3000, batch=128, lr=3e-3, seed=0)
+    t_train = time.perf_counter() - t0
+
+    ser = W.general_series_2m()
+    S4 = args.learned_strains
+    ts = [i / S4 * ser.period for i in range(S4)]
+    ctx.set_flow(ser.A, ser.L0, ser.M, ser.period)
+    ctx.set_potential(nemd.NEMD_LJ, 1.0, 1.0, 1)
+    q_all = torch.empty((S4, ser.n, 3), dtype=torch.float64, device=dev)
+    for i, t in enumerate(ts):
+        q_all[i].copy_(torch.from_numpy(ser.positions(t)))
+    table, feats, rule = [], [], []
+    for i in range(S4):
+        ctx.set_state(q_all[i], ts[i])
+        f, ms = ctx.time_options(ser.rc, reps=2)
+        table.append(ms)
+        feats.append(f)
+        ctx.set_option(nemd.NEMD_OPT_CELL_FACTOR, 1)
+        ctx.build_cells(nemd.NEMD_AUTO_HEURISTIC, ser.rc)
+        ctx.compute_forces()
+        ctx.sync()
+        rule.append(ctx.stats()["variant"])         # option index of the volume rule at k = 1
+    table = np.array(table)
+    pick = np.argmin(ctx.model_predict(np.array(feats)), axis=1)
+    best = table.min(axis=1)
+    idx = np.arange(S4)
+    regret_learned = float((table[idx, pick] - best).sum() / best.sum())
+    regret_rule = float((table[idx, np.array(rule)] - best).sum() / best.sum())
+
+    F = torch.empty((ser.n, 3), dtype=torch.float32, device=dev)
+    pairs = 0
+    for i in range(S4):
+        ctx.set_state(q_all[i], ts[i])
+        ctx.build_cells(nemd.NEMD_DS, ser.rc)
+        ctx.compute_forces(F)
+        ctx.sync()
+        pairs += ctx.stats()["pairs"]
+
+    def step(variant, kernel):
+        ctx.set_option(nemd.NEMD_OPT_KERNEL, kernel)
+        ctx.set_option(nemd.NEMD_OPT_CELL_FACTOR, 1)
+
+        def fn():
+            for i in range(S4):
+                ctx.set_state(q_all[i], ts[i])
+                ctx.build_cells(variant, ser.rc)
+                ctx.compute_forces(F)
+        return fn
+    out = {}
+    for name, variant, kernel in (("learned", nemd.NEMD_AUTO_LEARNED, 2), ("rule", nemd.NEMD_AUTO_HEURISTIC, 2),
+                                  ("plain_ds", nemd.NEMD_DS, 0), ("plain_do", nemd.NEMD_DO, 0)):
+        ms = timed_loop(torch, dev, 1, step(variant, kernel), 2, 1) / 2
+        out[name] = pairs / ms * 1e3
+    ctx.close()
+    del q_all
+    return {"workload": f"general 3D flow, N={ser.n} (FCC 81^3 with vacancies), LJ rc 2.5, {S4} strains "
+                        f"of one period",
+            "training_rows": int(len(X)), "rows_s": t_rows, "train_s": t_train,
+            "train_loss_first_last": [float(hist[:50].mean()), float(hist[-50:].mean())],
+            "options": "o = (variant o & 1, cell factor 1 + (o >> 1)), warp kernel",
+            "regret_vs_exhaustive": {"learned": regret_learned, "volume_rule_k1": regret_rule},
+            "learned_choices": np.bincount(pick, minlength=4).tolist(),
+            "exhaustive_choices": np.bincount(table.argmin(axis=1), minlength=4).tolist(),
+            "pairs_per_s": out,
+            "learned_over_best_plain": out["learned"] / max(out["plain_ds"], out["plain_do"])}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        barrier(world)
+        return
+
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1412_3784_gb300 import nemd
+    from paper_1412_3784_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sections = set(args.sections.split(","))
+    main_part = section_main(args, rank, world, dev, torch, nemd, W)
+    batched = section_batched(args, world, dev, torch, nemd, W) if "batched" in sections else None
+    learned = section_learned(args, dev, torch, nemd, W) if "learned" in sections else None
     if rank == 0:
         line = {
-            "metric": "interacting pairs/s per force eval", "value": value, "unit": "pairs/s",
+            "metric": "interacting pairs/s per force eval", "value": main_part["value"], "unit": "pairs/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms_tuned_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": main_part["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 pair math, f64 lattice/wrap/reductions",
             "data": "synthetic",
-            "config": {"workload": f"{args.workload}: general 3D flow M=[[3,2,1],[2,2,1],[1,1,1]], "
-                                   f"perturbed FCC N={n}, rho=0.8442, LJ rc=2.5, {S} strains per step "
-                                   f"(one period), one force evaluation per strain",
-                       "n": n, "strains_per_step": S, "pairs_per_step": pairs_per_step,
-                       "tuned": f"per-strain variant by neighbourhood volume, kernel {args.kernel} "
-                                f"(group {args.group}), cell factor {args.kfac}",
-                       "coarse_band_candidates_per_step": int(sum(per["tuned"]["rechecks"])),
-                       "l2": "inputs larger than L2: a distinct 24 MB position array per strain",
-                       "parallelism": f"replicas x{world}"},
-            "plain": {"dynamic_size_pairs_per_s": plain_ds, "dynamic_offset_pairs_per_s": plain_do,
-                      "search_efficiency_ds": eta_ds, "search_efficiency_do": eta_do},
-            "roofline": roofline,
-            "cpu_baseline": cpu,
-            "e2e": e2e,
-            "gpu_launches": int(launches),
-            "clocks": clk,
         }
+        for key in ("config", "plain", "autotune", "roofline", "cpu_baseline", "e2e", "gpu_launches", "clocks"):
+            line[key] = main_part[key]
+        line["batched"] = batched
+        line["learned"] = learned
         print(json.dumps(line), flush=True)
-    ctx.close()
     barrier(world)
     if world > 1:
         import torch.distributed as dist

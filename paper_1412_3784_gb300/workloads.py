@@ -171,10 +171,16 @@ def config_flow(M: np.ndarray, k: int, t: float, seed: int, *, T: float = 1.0,
 def general_series(k: int = 64, seed: int = 4) -> StrainSeries:
     """General 3D flow (M = [[3,2,1],[2,2,1],[1,1,1]]) on N = 4k^3 LJ particles, rc = 2.5.
 
-    k = 64 gives the N = 1,048,576 system, k = 80 the N = 2,097,152 one, k = 40
-    the N = 256,000 one.
+    k = 64 gives the N = 1,048,576 system, k = 40 the N = 256,000 one.
     """
     return StrainSeries(M_GENERAL, k, seed, name=f"general_N{4 * k ** 3}")
+
+
+def general_series_2m(seed: int = 5) -> StrainSeries:
+    """General 3D flow on N = 2,097,152 = 2^21 LJ particles, rc = 2.5: an FCC block
+    of 81^3 cells (2,125,764 sites) with 28,612 random vacancies."""
+    n = 1 << 21
+    return StrainSeries(M_GENERAL, 81, seed, vacancies=4 * 81 ** 3 - n, name=f"general_N{n}")
 
 
 def planar_series(k: int = 20, seed: int = 1) -> StrainSeries:
