@@ -107,8 +107,11 @@ struct Acc {
   // LJ force on i from j for displacement d = x_j - x_i (Sec. 5 potential):
   // F_i = -fr d, fr = 24 eps / r^2 [2 (sigma^2/r^2)^6 - (sigma^2/r^2)^3]
   __device__ __forceinline__ void add(const Pot &pp, float dx, float dy, float dz) {
-    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-    const float inv = __frcp_rn(r2);
+    add_r2(pp, dx, dy, dz, fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+  }
+  // the same with r^2 already formed; 1 / r^2 by the fast reciprocal (2 ulp)
+  __device__ __forceinline__ void add_r2(const Pot &pp, float dx, float dy, float dz, float r2) {
+    const float inv = __fdividef(1.0f, r2);
     const float s2 = pp.sig2 * inv;
     const float s6 = s2 * s2 * s2;
     const float fr = pp.eps24 * inv * s6 * (2.0f * s6 - 1.0f);

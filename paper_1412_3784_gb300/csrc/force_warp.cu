@@ -1,190 +1,217 @@
-// force_warp.cu -- warp force kernel: the grouped kernel's algorithm with one
-// chunk per warp (Sec. 3 and 5: neighbourhood cells only, distance check
-// before force; same pair set and pair arithmetic as the other kernels).
+// force_warp.cu -- warp force kernel (Sec. 3 and 5: neighbourhood cells only,
+// distance check before force; same pair set and pair arithmetic as the other
+// kernels).
 //
 // A warp takes a chunk of at most 32 consecutive particles of one x-row of
-// cells, one particle per lane.  Every loop bound is uniform across the warp
-// (one chunk, one cell at a time), so the test loop carries no per-candidate
-// bookkeeping: it is unrolled four-fold, inactive lanes are switched off by a
-// threshold that no r^2 can pass, and every tested candidate is written to the
-// lane's queue slot unconditionally -- the slot only advances when the test
-// passes -- so accepting costs no branch.  The chunk's rows are staged in
-// shared memory for the force phase (flush), which reads them per queued pair.
+// cells, one particle per lane, and walks the neighbour rows of the chunk's
+// (iy, iz) class.  For each row, the particles of the union of the lanes'
+// x-windows are staged in shared memory already moved into the chunk's frame:
+// a particle j of a cell A cells from the chunk's first cell is staged as
+//     X_j = x_j + shift + A step        exact (multiples of the quantum)
+//     R_j = r_j + shift_r + A step_r    float32 residual part
+// and lane i holds X_i = x_i + a_i step, R_i = r_i + a_i step_r, a_i being its
+// own cell's distance from the chunk's first cell.  Then X_j - X_i is exactly
+// the quantised displacement the other kernels form, and (X_j - X_i) + (R_j - R_i)
+// the displacement with the residuals added back.
+//
+// Test loop: every bound is uniform across the warp, staged X_j are read as
+// shared-memory broadcasts, and a lane writes the slot of every tested
+// candidate to its queue unconditionally, advancing only when the coarse test
+// passes, so accepting costs no branch.  Flush: queued pairs are decided with
+// the residuals added back (the float64 fix-up pass takes the few within float32
+// rounding of rc) and their forces computed -- all from shared memory.  A flush
+// runs when the stage is full, when a queue could overflow, and at the end of
+// the chunk; each lane accumulates its particle's force in queue order, so
+// results are deterministic.
 #include <math.h>
 
 #include "batch_internal.cuh"
 
 namespace nemd {
 
-#ifndef NEMD_WARP_QUEUE
-#define NEMD_WARP_QUEUE 64
-#endif
-#ifndef NEMD_FLUSH_UNROLL
-#define NEMD_FLUSH_UNROLL 1
-#endif
-constexpr int kWarpQueue = NEMD_WARP_QUEUE;   // queue entries per lane
-constexpr int kFlushUnroll = NEMD_FLUSH_UNROLL;  // queued pairs gathered at once in a flush
 constexpr int kWarpThreads = 128;  // 4 warps per block
 constexpr int kRowsStaged = 32;    // rows per class the kernel stages (cell factor <= 2)
-constexpr int kWJBits = 21;
-constexpr unsigned kWJMask = (1u << kWJBits) - 1u;
-constexpr unsigned kWBandFlag = 1u << kWJBits;
+constexpr int kStage = 256;        // staged particles per warp: a queue entry is one byte
+constexpr int kWarpQueue = 64;     // queue entries per lane
+constexpr int kTestBlock = 32;     // candidates tested between two queue checks
+constexpr int kMetaBias = 1 << 12;  // R_j.w = row | (unwrapped x-cell + kMetaBias) << 5
 
-// One queued pair: displacement with the residuals added back, coarse-band
-// decision, force.
-template <bool RECORD>
-__device__ __forceinline__ void warp_pair(unsigned int ent, const float4 &pj, const float4 &pjr, int &nre, const float4 &pi,
-                                          const float4 &pir, int ki, int ix, int jbase, const float4 (*rs)[3], const Geo *g,
-                                          const Pot &pp, Acc &acc, const double *q, int32_t *pair_buf,
-                                          unsigned long long *pair_count, long long pair_cap, int4 *rlist,
-                                          int *rcount, int *err) {
-  const int j = jbase + (int)(ent & kWJMask), r = (ent >> 22) & 31, nidx = (int)(ent >> 27) - 16;
-  const float4 sh = rs[r][0], sr = rs[r][1];
-  const float cx = (pj.x - sub_offset(pi.x, sh.x, nidx, g->step[0])) + (pjr.x - sub_residual(pir.x, sr.x, nidx, g->step_r[0]));
-  const float cy = (pj.y - sub_offset(pi.y, sh.y, nidx, g->step[1])) + (pjr.y - sub_residual(pir.y, sr.y, nidx, g->step_r[1]));
-  const float cz = (pj.z - sub_offset(pi.z, sh.z, nidx, g->step[2])) + (pjr.z - sub_residual(pir.z, sr.z, nidx, g->step_r[2]));
-  bool accept = true;
-  if (ent & kWBandFlag) {
-    nre++;
-    const float r2c = fmaf(cz, cz, fmaf(cy, cy, cx * cx));
-    accept = r2c < g->rc2_lo2;
-    if (!accept && r2c < g->rc2_hi2) {
-      const float4 r2w = rs[r][2];
-      const int sxi = __float_as_int(r2w.z), kyz = __float_as_int(r2w.y);
-      const int kx = floordiv_dev(ix + nidx - sxi, g->nc[0]);
-      const int ky = (short)(kyz & 0xffff), kz = kyz >> 16;
-      if (RECORD)
-        accept = guard_band_accept(g, q, __float_as_int(pi.w), __float_as_int(pj.w), kx, ky, kz);
-      else
-        defer_recheck(rlist, rcount, err, ki, j, kx, ky, kz);  // decided by the fix-up pass
-    }
-  }
-  // the particle itself: offset 0 and identical coordinates give exactly 0
-  if (accept && !(j == ki && cx == 0.f && cy == 0.f && cz == 0.f)) {
-    acc.add(pp, cx, cy, cz);
-    if (RECORD) {
-      const float4 r2w = rs[r][2];
-      const int sxi = __float_as_int(r2w.z), kyz = __float_as_int(r2w.y);
-      record_pair(g, q, __float_as_int(pi.w), __float_as_int(pj.w), floordiv_dev(ix + nidx - sxi, g->nc[0]),
-                  (short)(kyz & 0xffff), kyz >> 16, pair_buf, pair_count, pair_cap);
-    }
-  }
-}
+struct WarpStage {
+  float4 X[kStage];  // .w: sorted index of j (bits)
+  float4 R[kStage];  // .w: row and unwrapped x-cell of j (bits)
+  unsigned char q[kWarpQueue][32];
+  float4 rows[kRowsStaged][3];
+};
 
-// Forces of the queued pairs of every lane; the warp takes kFlushUnroll
-// entries per lane at a time so that their gathers overlap.
+// Forces of the queued pairs of every lane.
 template <bool RECORD>
-__device__ __forceinline__ void warp_flush(unsigned int (*myq)[32], int &qn, int &nre, int lane, const float4 &pi,
-                                           int ki, int ix, int jbase, const float4 (*rs)[3], const Geo *g, const float4 *pos,
-                                           const float4 *posr, const Pot &pp, Acc &acc, const double *q,
-                                           int32_t *pair_buf, unsigned long long *pair_count, long long pair_cap,
-                                           int4 *rlist, int *rcount, int *err) {
+__device__ __forceinline__ void warp_flush(WarpStage &S, int &qn, int &nre, int lane, int ki, const float4 &pi,
+                                           const float3 &Xi, const float3 &Ri, const Geo *g,
+                                           const float4 *__restrict__ pos, const Pot &pp, Acc &acc,
+                                           const double *q, int32_t *pair_buf, unsigned long long *pair_count,
+                                           long long pair_cap, int4 *rlist, int *rcount, int *err) {
   const int m = __reduce_max_sync(0xffffffffu, qn);
-  if (m == 0) return;
-  const float4 pir = posr[ki];
-  for (int s = 0; s < m; s += kFlushUnroll) {
-    unsigned int ent[kFlushUnroll];
-    float4 pj[kFlushUnroll], pjr[kFlushUnroll];
-#pragma unroll
-    for (int u = 0; u < kFlushUnroll; u++) {
-      // past the lane's own entries: a harmless stand-in (entry 0, or the lane's own particle)
-      ent[u] = myq[min(s + u, kWarpQueue - 1)][lane];
-      const int j = (s + u < qn) ? jbase + (int)(ent[u] & kWJMask) : ki;
-      pj[u] = pos[j];
-      pjr[u] = posr[j];
+  const float lo = g->rc2_lo, lo2 = g->rc2_lo2, hi2 = g->rc2_hi2;
+  for (int s = 0; s < m; s++) {
+    if (s < qn) {
+      const int slot = S.q[s][lane];
+      const float4 X = S.X[slot], R = S.R[slot];
+      const float cx = (X.x - Xi.x) + (R.x - Ri.x);
+      const float cy = (X.y - Xi.y) + (R.y - Ri.y);
+      const float cz = (X.z - Xi.z) + (R.z - Ri.z);
+      const float r2c = fmaf(cz, cz, fmaf(cy, cy, cx * cx));
+      const int j = __float_as_int(X.w);
+      bool accept = r2c < lo2;
+      if (!(r2c < lo)) nre++;
+      if (!accept && r2c < hi2) {
+        const int meta = __float_as_int(R.w);
+        const int kyz = __float_as_int(S.rows[meta & 31][2].y);
+        const int kx = floordiv_dev((meta >> 5) - kMetaBias, g->nc[0]);
+        const int ky = (short)(kyz & 0xffff), kz = kyz >> 16;
+        if (RECORD)
+          accept = guard_band_accept(g, q, __float_as_int(pi.w), __float_as_int(pos[j].w), kx, ky, kz);
+        else
+          defer_recheck(rlist, rcount, err, ki, j, kx, ky, kz);  // decided by the fix-up pass
+      }
+      // the particle itself: the same sorted index at exactly zero distance
+      if (accept && !(j == ki && r2c == 0.f)) {
+        acc.add_r2(pp, cx, cy, cz, r2c);
+        if (RECORD) {
+          const int meta = __float_as_int(R.w);
+          const int kyz = __float_as_int(S.rows[meta & 31][2].y);
+          record_pair(g, q, __float_as_int(pi.w), __float_as_int(pos[j].w),
+                      floordiv_dev((meta >> 5) - kMetaBias, g->nc[0]), (short)(kyz & 0xffff), kyz >> 16, pair_buf,
+                      pair_count, pair_cap);
+        }
+      }
     }
-#pragma unroll
-    for (int u = 0; u < kFlushUnroll; u++)
-      if (s + u < qn)
-        warp_pair<RECORD>(ent[u], pj[u], pjr[u], nre, pi, pir, ki, ix, jbase, rs, g, pp, acc, q, pair_buf, pair_count,
-                          pair_cap, rlist, rcount, err);
   }
   qn = 0;
 }
 
-// Everything one warp does for one chunk cd (Sec. 3 and 5): stage the rows of
-// the chunk's class, test every particle of the union of the lanes' windows,
-// queue and flush.  On return acc.fx, fy, fz hold the force on the lane's
-// particle pi (index ki; act is false for lanes past the chunk's count) in the
-// variant's frame, and its pair sums have been added to acc.  cell_base and
-// jbase are the system's first cell slot and first sorted particle (0 for a
-// single system): queue entries hold partner indices relative to jbase.
+// Everything one warp does for one chunk cd: stage the rows of the chunk's
+// class (crow, nr of them), then per row stage, test and queue, flushing as
+// needed.  On return acc.fx, fy, fz hold the force on the lane's particle pi
+// (sorted index ki; act is false for lanes past the chunk's count) in the
+// variant's frame, and its pair sums have been added to acc.  cell_base is the
+// system's first cell slot (0 for a single system).
 template <bool RECORD>
 __device__ __forceinline__ void warp_chunk(const int4 cd, const Row *__restrict__ crow, int nr, int cell_base,
-                                           int jbase, const Geo *g, const float4 *__restrict__ pos,
+                                           const Geo *g, const float4 *__restrict__ pos,
                                            const float4 *__restrict__ posr, const int *__restrict__ cell_sorted,
-                                           const int *__restrict__ start, unsigned int (*myq)[32],
-                                           float4 (*rs)[3], const Pot &pp, const double *q, Acc &acc, int &ncand,
-                                           int &nre, bool &act, float4 &pi, int &ki, int32_t *pair_buf,
-                                           unsigned long long *pair_count, long long pair_cap, int4 *rlist,
-                                           int *rcount, int *err) {
+                                           const int *__restrict__ start, WarpStage &S, const Pot &pp,
+                                           const double *q, Acc &acc, int &ncand, int &nre, bool &act, float4 &pi,
+                                           int &ki, int32_t *pair_buf, unsigned long long *pair_count,
+                                           long long pair_cap, int4 *rlist, int *rcount, int *err) {
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int l1 = g->nc[0];
-  const float lo = g->rc2_lo, hi = g->rc2_hi;
   const float sx = g->step[0], sy = g->step[1], sz = g->step[2];
+  const float srx = g->step_r[0], sry = g->step_r[1], srz = g->step_r[2];
   act = lane < cd.y;
   ki = act ? cd.x + lane : cd.x;  // inactive lanes shadow a valid particle
   pi = pos[ki];
-  const int ix = (cell_sorted[ki] - cell_base) % l1;
+  const float4 pir = posr[ki];
   const int ixlo = cd.w & 0xffff, ixhi = cd.w >> 16;
+  const float ai = (float)((cell_sorted[ki] - cell_base) % l1 - ixlo);
+  const float3 Xi = make_float3(fmaf(ai, sx, pi.x), fmaf(ai, sy, pi.y), fmaf(ai, sz, pi.z));
+  const float3 Ri = make_float3(fmaf(ai, srx, pir.x), fmaf(ai, sry, pir.y), fmaf(ai, srz, pir.z));
   {
     const float4 *src = reinterpret_cast<const float4 *>(crow);
     __syncwarp();
-    for (int e = lane; e < 3 * nr; e += 32) rs[e / 3][e % 3] = src[e];
+    for (int e = lane; e < 3 * nr; e += 32) S.rows[e / 3][e % 3] = src[e];
     __syncwarp();
   }
-  const float hil = act ? hi : -1.0f;  // an inactive lane accepts nothing
+  const float hil = act ? g->rc2_hi : -1.0f;  // an inactive lane accepts nothing
   acc.fx = acc.fy = acc.fz = 0.f;
-  int qn = 0;
+  int qn = 0, fill = 0;
+  // extent of the lanes along the row (cell units from the chunk's first cell):
+  // a staged cell whose kappa range lies farther than rho1 from every lane
+  // holds no partner of any lane and is skipped
+  const float kx0 = g->kap[0], ky0 = g->kap[1], kz0 = g->kap[2];
+  const float P = ai + fmaf(kz0, pi.z, fmaf(ky0, pi.y, kx0 * pi.x));
+  float pmin = act ? P : 1e30f, pmax = act ? P : -1e30f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    pmin = fminf(pmin, __shfl_xor_sync(FULL, pmin, o));
+    pmax = fmaxf(pmax, __shfl_xor_sync(FULL, pmax, o));
+  }
+  const float reach1 = g->rho1 + 0.5f + 1e-4f;
 
   for (int r = 0; r < nr; r++) {
-    const float4 s0 = rs[r][0];
-    const int cbase = __float_as_int(s0.w), dxlo = __float_as_int(rs[r][1].w);
-    const int rcnt = __float_as_int(rs[r][2].x), sxi = __float_as_int(rs[r][2].z);
+    const float4 s0 = S.rows[r][0], s1 = S.rows[r][1], s2 = S.rows[r][2];
+    const int cbase = __float_as_int(s0.w), dxlo = __float_as_int(s1.w);
+    const int rcnt = __float_as_int(s2.x), sxi = __float_as_int(s2.z);
     const int ulo = ixlo + dxlo, nu = ixhi - ixlo + rcnt;
-    int jx = ulo - floordiv_dev(ulo, l1) * l1;
-    for (int u = 0; u < nu; u++) {
-      const int b = start[cbase + jx], e = start[cbase + jx + 1];
-      const int nidx = ulo + u - ix + sxi;
-      const float tx = sub_offset(pi.x, s0.x, nidx, sx), ty = sub_offset(pi.y, s0.y, nidx, sy),
-                  tz = sub_offset(pi.z, s0.z, nidx, sz);
-      const unsigned int tag = ((unsigned)r << 22) | ((unsigned)(nidx + 16) << 27);
+    // the row shift along the row, and the window cells u whose A = dxlo + sxi + u can hold a partner
+    const float sh1 = fmaf(kz0, s0.z + s1.z, fmaf(ky0, s0.y + s1.y, kx0 * (s0.x + s1.x)));
+    const float a0 = (float)(dxlo + sxi) + sh1;
+    const int ufirst = max(0, (int)ceilf(pmin - reach1 - a0));
+    const int ulast = min(nu - 1, (int)floorf(pmax + reach1 - a0));
+    const int ustart = ulo + ufirst;
+    int jx = ustart - floordiv_dev(ustart, l1) * l1;
+    // runs of consecutive cells without an x-wrap: contiguous particles
+    for (int u = ufirst; u <= ulast;) {
+      const int len = min(ulast + 1 - u, l1 - jx);
+      const int b = start[cbase + jx], e = start[cbase + jx + len];
+      const int arun = dxlo + sxi + u - jx;  // A of a particle of cell jx' of this run: arun + jx'
+      const int meta_run = r + ((ulo + u - jx + kMetaBias) << 5);
       if (act) ncand += e - b;
-      // segments of at most kWarpQueue - 1 candidates: the unconditional store
-      // of a test must always land inside the queue
-      for (int seg = b; seg < e; seg += kWarpQueue - 1) {
-        const int send = min(e, seg + kWarpQueue - 1);
-        if (__any_sync(FULL, qn + (send - seg) > kWarpQueue - 1))
-          warp_flush<RECORD>(myq, qn, nre, lane, pi, ki, ix, jbase, rs, g, pos, posr, pp, acc, q, pair_buf,
-                             pair_count, pair_cap, rlist, rcount, err);
-#define NEMD_TEST(P, J)                                                                   \
-  {                                                                                       \
-    const float ddx = (P).x - tx, ddy = (P).y - ty, ddz = (P).z - tz;                     \
-    const float r2 = fmaf(ddz, ddz, fmaf(ddy, ddy, ddx * ddx));                           \
-    myq[qn][lane] = (unsigned)(J) | tag | (r2 < lo ? 0u : kWBandFlag);                    \
-    qn += (r2 < hil) ? 1 : 0;                                                             \
+      for (int p = b; p < e;) {
+        if (fill == kStage) {
+          warp_flush<RECORD>(S, qn, nre, lane, ki, pi, Xi, Ri, g, pos, pp, acc, q, pair_buf, pair_count, pair_cap,
+                             rlist, rcount, err);
+          fill = 0;
+        }
+        const int take = min(e - p, kStage - fill);
+        __syncwarp();  // slots about to be overwritten are no longer read
+        for (int t = lane; t < take; t += 32) {
+          const int j = p + t;
+          const float4 pj = pos[j], pjr = posr[j];
+          const int cjx = cell_sorted[j] - cbase;
+          const float A = (float)(arun + cjx);
+          S.X[fill + t] = make_float4(fmaf(A, sx, pj.x + s0.x), fmaf(A, sy, pj.y + s0.y), fmaf(A, sz, pj.z + s0.z),
+                                      __int_as_float(j));
+          S.R[fill + t] = make_float4(fmaf(A, srx, pjr.x + s1.x), fmaf(A, sry, pjr.y + s1.y),
+                                      fmaf(A, srz, pjr.z + s1.z), __int_as_float(meta_run + (cjx << 5)));
+        }
+        __syncwarp();
+        for (int k0 = fill; k0 < fill + take; k0 += kTestBlock) {
+          const int k1 = min(fill + take, k0 + kTestBlock);
+          if (__any_sync(FULL, qn > kWarpQueue - kTestBlock))
+            warp_flush<RECORD>(S, qn, nre, lane, ki, pi, Xi, Ri, g, pos, pp, acc, q, pair_buf, pair_count, pair_cap,
+                               rlist, rcount, err);
+#define NEMD_TEST(P, K)                                                       \
+  {                                                                           \
+    const float ddx = (P).x - Xi.x, ddy = (P).y - Xi.y, ddz = (P).z - Xi.z;   \
+    const float r2 = fmaf(ddz, ddz, fmaf(ddy, ddy, ddx * ddx));               \
+    S.q[qn][lane] = (unsigned char)(K);                                       \
+    qn += (r2 < hil) ? 1 : 0;                                                 \
   }
-        int j = seg;
-        for (; j + 4 <= send; j += 4) {
-          const float4 p0 = pos[j], p1 = pos[j + 1], p2 = pos[j + 2], p3 = pos[j + 3];
-          const int jr = j - jbase;
-          NEMD_TEST(p0, jr);
-          NEMD_TEST(p1, jr + 1);
-          NEMD_TEST(p2, jr + 2);
-          NEMD_TEST(p3, jr + 3);
-        }
-        for (; j < send; j++) {
-          const float4 p0 = pos[j];
-          NEMD_TEST(p0, j - jbase);
-        }
+          int k = k0;
+          for (; k + 4 <= k1; k += 4) {
+            const float4 p0 = S.X[k], p1 = S.X[k + 1], p2 = S.X[k + 2], p3 = S.X[k + 3];
+            NEMD_TEST(p0, k);
+            NEMD_TEST(p1, k + 1);
+            NEMD_TEST(p2, k + 2);
+            NEMD_TEST(p3, k + 3);
+          }
+          for (; k < k1; k++) {
+            const float4 p0 = S.X[k];
+            NEMD_TEST(p0, k);
+          }
 #undef NEMD_TEST
+        }
+        fill += take;
+        p += take;
       }
-      if (++jx == l1) jx = 0;
+      u += len;
+      jx += len;
+      if (jx == l1) jx = 0;
     }
   }
-  warp_flush<RECORD>(myq, qn, nre, lane, pi, ki, ix, jbase, rs, g, pos, posr, pp, acc, q, pair_buf, pair_count,
-                     pair_cap, rlist, rcount, err);
+  warp_flush<RECORD>(S, qn, nre, lane, ki, pi, Xi, Ri, g, pos, pp, acc, q, pair_buf, pair_count, pair_cap, rlist,
+                     rcount, err);
 }
 
 // F (Cartesian) of a lane's particle from its frame force: F = Q F_frame.
@@ -205,8 +232,7 @@ __global__ void __launch_bounds__(kWarpThreads) k_force_warp(
     int32_t *__restrict__ pair_buf, unsigned long long *__restrict__ pair_count, long long pair_cap,
     int4 *__restrict__ rlist, int *__restrict__ rcount, int *__restrict__ err) {
   constexpr int kWarps = kWarpThreads / 32;
-  __shared__ unsigned int qbuf[kWarps][kWarpQueue][32];
-  __shared__ float4 rstage[kWarps][kRowsStaged][3];
+  __shared__ WarpStage stage[kWarps];
   const int warp = threadIdx.x >> 5;
 
   Acc acc;  // U, W and the pair count accumulate over every particle this lane owns
@@ -221,9 +247,9 @@ __global__ void __launch_bounds__(kWarpThreads) k_force_warp(
     bool act;
     float4 pi;
     int ki;
-    warp_chunk<RECORD>(cd, rows + (size_t)cd.z * maxrows, rowcnt[cd.z], 0, 0, g, pos, posr, cell_sorted, start,
-                       qbuf[warp], rstage[warp], pp, q, acc, ncand, nre, act, pi, ki, pair_buf, pair_count, pair_cap,
-                       rlist, rcount, err);
+    warp_chunk<RECORD>(cd, rows + (size_t)cd.z * maxrows, rowcnt[cd.z], 0, g, pos, posr, cell_sorted, start,
+                       stage[warp], pp, q, acc, ncand, nre, act, pi, ki, pair_buf, pair_count, pair_cap, rlist,
+                       rcount, err);
     if (act && F) store_force(F, g, pi, acc);
   }
   double v[kPartials] = {acc.u, acc.wxx, acc.wyy, acc.wzz, acc.wxy, acc.wxz, acc.wyz,
@@ -244,7 +270,7 @@ static int warp_resident_blocks(int sms) {
   return per_sm * sms;
 }
 
-bool warp_kernel_applies(const nemd_ctx *c) { return c->n <= (1 << kWJBits) && c->kfac <= 2; }
+bool warp_kernel_applies(const nemd_ctx *c) { return c->kfac <= 2; }
 
 cudaError_t launch_force_warp(nemd_ctx *c, float *F, int *nblocks) {
   const Pot pp = make_pot(c);
@@ -274,8 +300,7 @@ cudaError_t launch_force_warp(nemd_ctx *c, float *F, int *nblocks) {
 __global__ void __launch_bounds__(kWarpThreads) k_b_force_warp(BatchView v) {
   constexpr int kWarps = kWarpThreads / 32;
   constexpr unsigned FULL = 0xffffffffu;
-  __shared__ unsigned int qbuf[kWarps][kWarpQueue][32];
-  __shared__ float4 rstage[kWarps][kRowsStaged][3];
+  __shared__ WarpStage stage[kWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nch = v.chunk_off[v.nclasses];
   for (;;) {
@@ -287,7 +312,6 @@ __global__ void __launch_bounds__(kWarpThreads) k_b_force_warp(BatchView v) {
     const int s = v.class_sys[cd.z];
     Geo *g = v.geo + s;
     const int coff = v.sys[s].coff;
-    const int jbase = v.start[coff];
     const Pot pp = v.pot[s];
     Acc acc;
     acc.zero();
@@ -295,9 +319,9 @@ __global__ void __launch_bounds__(kWarpThreads) k_b_force_warp(BatchView v) {
     bool act;
     float4 pi;
     int ki;
-    warp_chunk<false>(cd, v.rows + (size_t)cd.z * kBatchRowStride, v.rowcnt[cd.z], coff, jbase, g, v.pos4, v.posr,
-                      v.cell_sorted, v.start, qbuf[warp], rstage[warp], pp, v.q, acc, ncand, nre, act, pi, ki,
-                      nullptr, nullptr, 0, v.recheck, v.nrecheck, &g->error);
+    warp_chunk<false>(cd, v.rows + (size_t)cd.z * kBatchRowStride, v.rowcnt[cd.z], coff, g, v.pos4, v.posr,
+                      v.cell_sorted, v.start, stage[warp], pp, v.q, acc, ncand, nre, act, pi, ki, nullptr, nullptr, 0,
+                      v.recheck, v.nrecheck, &g->error);
     if (act) {
       if (v.F) store_force(v.F, g, pi, acc);
       v.ppart[2 * (size_t)ki] = make_float4(acc.u, acc.wxx, acc.wyy, acc.wzz);

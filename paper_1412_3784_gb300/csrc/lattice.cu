@@ -285,8 +285,10 @@ __device__ void grid_body(Geo *g, const GridIn &in) {
   double gmax = 0.0;
   for (int a = 0; a < 3; a++) gmax = fmax(gmax, fabs(Gd[3 * a]) + fabs(Gd[3 * a + 1]) + fabs(Gd[3 * a + 2]));
   const int rmax = max(reach[0], max(reach[1], reach[2]));
-  // offsets reach (rmax + 2 + span) cells, positions half a cell, distances rc
-  const double M = (double)(rmax + 4 + kMaxSpan) * gmax + 2.0 * rc;
+  // offsets reach (rmax + 2 + span) cells and the warp kernel's staged
+  // positions (Sec. 3 union windows) up to (span + 2 rmax + 3) cells from a
+  // chunk's first cell; positions half a cell, distances rc
+  const double M = (double)(3 * rmax + 6 + kMaxSpan) * gmax + 2.0 * rc;
   int e2;
   frexp(M, &e2);             // M < 2^e2
   const double q = ldexp(1.0, e2 - 23);
@@ -310,6 +312,20 @@ __device__ void grid_body(Geo *g, const GridIn &in) {
   double band2 = 2.0 * (2.0 * s3 * rc * E2 + 3.0 * E2 * E2 + 3.0 * u * rc * rc) + 1e-12 * rc * rc;
   for (int a = 0; a < 3; a++) g->step[a] = step[a];
   g->band = (float)band;
+  {
+    // kappa = (G^-1 rel)_1: dynamic size c1 (row 1 of L^-1) . rel, dynamic offset x / w1
+    double k3[3];
+    if (variant == NEMD_DS) {
+      for (int a = 0; a < 3; a++) k3[a] = (double)nc[0] * g->Linv[a];
+    } else {
+      k3[0] = nc[0] > 0 ? 1.0 / g->w[0] : 0.0;
+      k3[1] = k3[2] = 0.0;
+    }
+    const double kn = sqrt(k3[0] * k3[0] + k3[1] * k3[1] + k3[2] * k3[2]);
+    for (int a = 0; a < 3; a++) g->kap[a] = (float)k3[a];
+    // |d . n1| = |delta kappa| h_cell <= |d| < rc, with room for float32 rounding
+    g->rho1 = (float)(rc * kn * (1.0 + 1e-4) + 1e-4);
+  }
   g->rc2 = rc * rc;
   g->rc2f = (float)(rc * rc);
   g->rc2_lo = __double2float_rd(rc * rc - band);

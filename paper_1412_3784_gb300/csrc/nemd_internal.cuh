@@ -57,6 +57,12 @@ struct Geo {
   float rc2_lo, rc2_hi, rc2f;   // coarse band: quantised test without residuals
   float rc2_lo2, rc2_hi2;       // fine band: float32 test with residuals added back
   float band;
+  // coordinate along the x-rows in cell units: kappa = kap . rel is in
+  // [-1/2, 1/2] inside a cell (dynamic size: u1 - 1/2; dynamic offset: x / w1);
+  // two particles whose kappa positions along a row differ by more than rho1
+  // are farther apart than rc
+  float kap[3];
+  float rho1;
   double quantum;     // float32 coordinates and offsets are multiples of this power of 2
   double vol_ds, vol_do;  // neighbourhood volumes (Sec. 5.1, 5.2) of both variants
   int counts_ds[3], counts_do[3];
