@@ -47,11 +47,11 @@ __device__ __forceinline__ void wrap_body(Geo *g, const double *__restrict__ q, 
       idx[a] = k;
       u[a] = (v - (double)k) - 0.5;
     }
-    for (int a = 0; a < 3; a++) rel[a] = g->G[3 * a] * u[0] + g->G[3 * a + 1] * u[1] + g->G[3 * a + 2] * u[2];
+    for (int a = 0; a < 3; a++) rel[a] = fma(g->G[3 * a], u[0], fma(g->G[3 * a + 1], u[1], g->G[3 * a + 2] * u[2]));
   } else {
     double b[3];
     int m[3];
-    brick_wrap(g->R, s, b, m);
+    brick_wrap(g->R, g->rinv, s, b, m);
     for (int a = 0; a < 3; a++) {
       int k = (int)floor(b[a] * g->Ginv_scale[a]);
       k = min(max(k, 0), g->nc[a] - 1);

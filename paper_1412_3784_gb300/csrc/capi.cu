@@ -101,6 +101,9 @@ int ensure_cells(nemd_ctx *c, int64_t cells, int kfac) {
   if ((r = grow(c, &c->block_sums, cap / 4096 + 2, "block_sums"))) return r;
   if ((r = grow(c, &c->rowcnt, cap, "rowcnt"))) return r;
   if ((r = grow(c, &c->rows, cap * stride, "rows"))) return r;
+  if ((r = grow(c, &c->chunk_cnt, cap + 1, "chunk counts"))) return r;
+  if ((r = grow(c, &c->chunk_off, cap + 1, "chunk offsets"))) return r;
+  if ((r = grow(c, &c->chunk_tiles, cap / 4096 + 2, "chunk scan tiles"))) return r;
   c->cap_cells = cap;
   c->cap_rows = cap * stride;
   return NEMD_OK;
@@ -203,7 +206,8 @@ int nemd_destroy(nemd_ctx *c) {
   if (c->model) cudaFree(c->model);
   void *ptrs[] = {c->geo,  c->q_copy, c->relc,     c->relr, c->posr, c->rank,     c->count,    c->start, c->chunks, c->nchunks, c->recheck, c->nrecheck,
                   c->block_sums, c->perm, c->pos4, c->cell_sorted, c->rows, c->rowcnt,
-                  c->partials, c->uw_out, c->f_dev, c->pair_buf, c->pair_count, c->counters};
+                  c->partials, c->uw_out, c->f_dev, c->pair_buf, c->pair_count, c->counters,
+                  c->chunk_cnt, c->chunk_off, c->chunk_tiles};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_error) cudaFreeHost(c->h_error);

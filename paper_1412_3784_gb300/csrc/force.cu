@@ -164,8 +164,8 @@ __global__ void __launch_bounds__(NT) k_force_plain(const Geo *__restrict__ g, c
 // rounding of rc: the canonical decision (Sec. 2 images, strict r < rc), and for
 // each accepted pair the force on i (added to F, Cartesian), half of u and of
 // r (x) f (the other half comes from the pair's other orientation, which the
-// full neighbourhood also defers), written as one more block of partials in the
-// variant's frame.  One block; runs after the force kernel.
+// full neighbourhood also defers), written as one more block of partials per
+// block in the variant's frame.  Runs after the force kernel.
 __global__ void k_recheck_fixup(const Geo *__restrict__ g, const int4 *__restrict__ list,
                                 const int *__restrict__ count, const float4 *__restrict__ pos,
                                 const double *__restrict__ q, Pot pp, float *__restrict__ F,
@@ -174,7 +174,7 @@ __global__ void k_recheck_fixup(const Geo *__restrict__ g, const int4 *__restric
   for (int k = 0; k < kPartials; k++) v[k] = 0.0;
   const int n = min(*count, kRecheckCap);
   const bool ok = !(g->error & (ERRB_BOX | ERRB_CAPACITY));
-  for (int e = threadIdx.x; ok && e < n; e += blockDim.x) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; ok && e < n; e += gridDim.x * blockDim.x) {
     const int4 it = list[e];
     const int oi = __float_as_int(pos[it.x].w), oj = __float_as_int(pos[it.y].w);
     const int ky = (short)(it.w & 0xffff), kz = it.w >> 16;
@@ -209,7 +209,8 @@ __global__ void k_recheck_fixup(const Geo *__restrict__ g, const int4 *__restric
       for (int k = 0; k < kPartials; k++) sh[threadIdx.x][k] += sh[threadIdx.x + s][k];
     __syncthreads();
   }
-  if (threadIdx.x < kPartials) partial_slot[threadIdx.x] = (threadIdx.x < 8) ? sh[0][threadIdx.x] : 0.0;
+  if (threadIdx.x < kPartials)
+    partial_slot[(size_t)blockIdx.x * kPartials + threadIdx.x] = (threadIdx.x < 8) ? sh[0][threadIdx.x] : 0.0;
 }
 
 // Single block: sums the per-block partials in a fixed order (deterministic),
@@ -347,11 +348,14 @@ cudaError_t launch_forces(nemd_ctx *c, float *F_dev, double *UW_dev) {
     cudaEventRecord(c->ev[2 * c->ev_n + 1], c->stream);
     c->ev_n++;
   }
-  // the deferred float64 decisions, as one more block of partials
-  k_recheck_fixup<<<1, 256, 0, c->stream>>>(c->geo, c->recheck, c->nrecheck, c->pos4, c->q_dev, make_pot(c), F_dev,
-                                            c->partials + (size_t)nblocks * kPartials);
+  // the deferred float64 decisions, as a few more blocks of partials (at least
+  // one slot is always left after the force kernel's)
+  int nfix = kFixupBlocks;
+  if (nblocks + nfix > c->cap_partials) nfix = (int)(c->cap_partials - nblocks);
+  k_recheck_fixup<<<nfix, 256, 0, c->stream>>>(c->geo, c->recheck, c->nrecheck, c->pos4, c->q_dev, make_pot(c),
+                                               F_dev, c->partials + (size_t)nblocks * kPartials);
   c->launches += 1;
-  return launch_reduce(c, nblocks + 1, c->precise ? 1 : 0, UW_dev);
+  return launch_reduce(c, nblocks + nfix, c->precise ? 1 : 0, UW_dev);
 }
 
 

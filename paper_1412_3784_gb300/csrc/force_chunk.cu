@@ -60,15 +60,62 @@ __device__ __forceinline__ void chunk_walk(const int *__restrict__ start, int c0
 }
 
 // Chunk descriptor: x = first sorted particle, y = count, z = class (iy + l2 iz),
-// w = ixlo | ixhi << 16.  One thread per row of cells; slots by atomic counter.
-__global__ void k_chunks(const Geo *__restrict__ g, const int *__restrict__ start, int4 *__restrict__ chunks,
-                         int *__restrict__ nchunks, int gs) {
+// w = ixlo | ixhi << 16.  Built in a fixed order: chunks per class, their
+// exclusive scan, and the descriptors at the scanned offsets -- so the chunk
+// list, and every sum of the force kernels that walk it, are the same from run
+// to run.  One warp per class: the lanes stage the row's cell starts in shared
+// memory and one lane walks them.
+constexpr int kWalkCells = 512;  // row lengths staged in shared memory (longer rows walk global memory)
+constexpr int kWalkWarps = 4;
+
+template <class Emit>
+__device__ __forceinline__ void chunk_walk_warp(const int *__restrict__ start, int c0, int l1, int gs, int *sm,
+                                                int lane, Emit &&emit) {
+  const bool staged = l1 < kWalkCells;
+  __syncwarp();
+  if (staged)
+    for (int k = lane; k <= l1; k += 32) sm[k] = start[c0 + k];
+  __syncwarp();
+  if (lane == 0) {
+    if (staged)
+      chunk_walk(sm, 0, l1, gs, emit);
+    else
+      chunk_walk(start, c0, l1, gs, emit);
+  }
+}
+
+__global__ void __launch_bounds__(32 * kWalkWarps) k_chunk_count(const Geo *__restrict__ g,
+                                                                 const int *__restrict__ start,
+                                                                 int *__restrict__ cnt, int gs, int cap) {
+  __shared__ int sm[kWalkWarps][kWalkCells + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool ok = !(g->error & (ERRB_BOX | ERRB_CAPACITY));
+  const int l1 = g->nc[0], ncls = ok ? g->nc[1] * g->nc[2] : 0;
+  // unused class slots count no chunks
+  for (int k = ncls + blockIdx.x * blockDim.x + threadIdx.x; k < cap; k += gridDim.x * blockDim.x) cnt[k] = 0;
+  const int nw = gridDim.x * kWalkWarps;
+  for (int cls = blockIdx.x * kWalkWarps + warp; cls < ncls; cls += nw) {
+    int n = 0;
+    chunk_walk_warp(start, cls * l1, l1, gs, sm[warp], lane, [&](int, int, int, int) { n++; });
+    if (lane == 0) cnt[cls] = n;
+  }
+}
+
+__global__ void __launch_bounds__(32 * kWalkWarps) k_chunk_write(const Geo *__restrict__ g,
+                                                                 const int *__restrict__ start,
+                                                                 const int *__restrict__ off,
+                                                                 int4 *__restrict__ chunks, int gs) {
+  __shared__ int sm[kWalkWarps][kWalkCells + 1];
   if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int l1 = g->nc[0], ncls = g->nc[1] * g->nc[2];
-  for (int cls = blockIdx.x * blockDim.x + threadIdx.x; cls < ncls; cls += gridDim.x * blockDim.x)
-    chunk_walk(start, cls * l1, l1, gs, [&](int first, int count, int ixlo, int ixhi) {
-      chunks[atomicAdd(nchunks, 1)] = make_int4(first, count, cls, ixlo | (ixhi << 16));
+  const int nw = gridDim.x * kWalkWarps;
+  for (int cls = blockIdx.x * kWalkWarps + warp; cls < ncls; cls += nw) {
+    int k = off[cls];
+    chunk_walk_warp(start, cls * l1, l1, gs, sm[warp], lane, [&](int first, int count, int ixlo, int ixhi) {
+      chunks[k++] = make_int4(first, count, cls, ixlo | (ixhi << 16));
     });
+  }
 }
 
 // Queue entry: partner index (21 bits), coarse-band flag (1), row (5),
@@ -229,13 +276,15 @@ __global__ void __launch_bounds__(kChunkThreads, 4) k_force_chunk(
 }
 
 cudaError_t launch_chunk_build(nemd_ctx *c, int gs) {
-  cudaError_t e = cudaMemsetAsync(c->nchunks, 0, sizeof(int), c->stream);
-  if (e != cudaSuccess) return e;
-  int64_t blocks = (c->cap_cells + 127) / 128;
-  if (blocks > 4 * (int64_t)c->sms) blocks = 4 * (int64_t)c->sms;
+  const int cap = (int)c->cap_cells;
+  int64_t blocks = (c->cap_cells + kWalkWarps - 1) / kWalkWarps;
+  if (blocks > 16 * (int64_t)c->sms) blocks = 16 * (int64_t)c->sms;
   if (blocks < 1) blocks = 1;
-  k_chunks<<<(int)blocks, 128, 0, c->stream>>>(c->geo, c->start, c->chunks, c->nchunks, gs);
-  c->launches += 1;
+  k_chunk_count<<<(int)blocks, 32 * kWalkWarps, 0, c->stream>>>(c->geo, c->start, c->chunk_cnt, gs, cap);
+  cudaError_t e = launch_fixed_scan(c->stream, c->chunk_cnt, c->chunk_off, c->chunk_tiles, cap);
+  if (e != cudaSuccess) return e;
+  k_chunk_write<<<(int)blocks, 32 * kWalkWarps, 0, c->stream>>>(c->geo, c->start, c->chunk_off, c->chunks, gs);
+  c->launches += 5;
   return cudaGetLastError();
 }
 
@@ -270,7 +319,7 @@ cudaError_t launch_force_chunk(nemd_ctx *c, float *F, int *nblocks) {
   if (blocks > (int)(c->cap_partials - 1)) blocks = (int)(c->cap_partials - 1);
   *nblocks = blocks;
 #define NEMD_ARGS                                                                                                \
-  c->geo, c->pos4, c->posr, c->cell_sorted, c->start, c->rows, c->rowcnt, c->chunks, c->nchunks, c->q_dev, pp, \
+  c->geo, c->pos4, c->posr, c->cell_sorted, c->start, c->rows, c->rowcnt, c->chunks, c->chunk_off + c->cap_cells, c->q_dev, pp, \
       F, c->partials, c->pair_buf, c->pair_count, (long long)c->record_cap, c->recheck, c->nrecheck, &c->geo->error
 #define NEMD_LAUNCH(GS)                                                                              \
   do {                                                                                               \
@@ -307,35 +356,42 @@ __device__ __forceinline__ bool batch_class(const BatchView &v, int slot, const 
   return true;
 }
 
-__global__ void k_b_chunk_count(BatchView v) {
-  for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < v.nclasses; slot += gridDim.x * blockDim.x) {
+__global__ void __launch_bounds__(32 * kWalkWarps) k_b_chunk_count(BatchView v) {
+  __shared__ int sm[kWalkWarps][kWalkCells + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = gridDim.x * kWalkWarps;
+  for (int slot = blockIdx.x * kWalkWarps + warp; slot < v.nclasses; slot += nw) {
     const Geo *g;
     int c0, l1, n = 0;
-    if (batch_class(v, slot, g, c0, l1)) chunk_walk(v.start, c0, l1, v.gs, [&](int, int, int, int) { n++; });
-    v.chunk_cnt[slot] = n;
+    if (batch_class(v, slot, g, c0, l1))
+      chunk_walk_warp(v.start, c0, l1, v.gs, sm[warp], lane, [&](int, int, int, int) { n++; });
+    if (lane == 0) v.chunk_cnt[slot] = n;
   }
 }
 
-__global__ void k_b_chunk_write(BatchView v) {
-  for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < v.nclasses; slot += gridDim.x * blockDim.x) {
+__global__ void __launch_bounds__(32 * kWalkWarps) k_b_chunk_write(BatchView v) {
+  __shared__ int sm[kWalkWarps][kWalkCells + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = gridDim.x * kWalkWarps;
+  for (int slot = blockIdx.x * kWalkWarps + warp; slot < v.nclasses; slot += nw) {
     const Geo *g;
     int c0, l1;
     if (!batch_class(v, slot, g, c0, l1)) continue;
     int k = v.chunk_off[slot];
-    chunk_walk(v.start, c0, l1, v.gs, [&](int first, int count, int ixlo, int ixhi) {
+    chunk_walk_warp(v.start, c0, l1, v.gs, sm[warp], lane, [&](int first, int count, int ixlo, int ixhi) {
       v.chunks[k++] = make_int4(first, count, slot, ixlo | (ixhi << 16));
     });
   }
 }
 
 cudaError_t launch_batch_chunks(cudaStream_t st, const BatchView &v, int sms) {
-  int blocks = (v.nclasses + 127) / 128;
+  int blocks = (v.nclasses + kWalkWarps - 1) / kWalkWarps;
   if (blocks > 16 * sms) blocks = 16 * sms;
   if (blocks < 1) blocks = 1;
-  k_b_chunk_count<<<blocks, 128, 0, st>>>(v);
+  k_b_chunk_count<<<blocks, 32 * kWalkWarps, 0, st>>>(v);
   cudaError_t e = launch_fixed_scan(st, v.chunk_cnt, v.chunk_off, v.chunk_tiles, v.nclasses);
   if (e != cudaSuccess) return e;
-  k_b_chunk_write<<<blocks, 128, 0, st>>>(v);
+  k_b_chunk_write<<<blocks, 32 * kWalkWarps, 0, st>>>(v);
   return cudaGetLastError();
 }
 

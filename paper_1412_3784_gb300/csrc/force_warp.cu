@@ -279,7 +279,7 @@ cudaError_t launch_force_warp(nemd_ctx *c, float *F, int *nblocks) {
   if (blocks > (int)(c->cap_partials - 1)) blocks = (int)(c->cap_partials - 1);
   *nblocks = blocks;
 #define NEMD_ARGS                                                                                                \
-  c->geo, c->pos4, c->posr, c->cell_sorted, c->start, c->rows, c->rowcnt, c->chunks, c->nchunks, c->q_dev, pp, \
+  c->geo, c->pos4, c->posr, c->cell_sorted, c->start, c->rows, c->rowcnt, c->chunks, c->chunk_off + c->cap_cells, c->q_dev, pp, \
       F, c->partials, c->pair_buf, c->pair_count, (long long)c->record_cap, c->recheck, c->nrecheck, &c->geo->error
   if (rec)
     k_force_warp<true><<<blocks, kWarpThreads, 0, c->stream>>>(NEMD_ARGS);

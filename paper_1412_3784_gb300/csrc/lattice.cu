@@ -175,6 +175,7 @@ __device__ __forceinline__ void lattice_body(Geo *g, const LatIn &in) {
   }
   __syncwarp();
   if (lane < 9) g->R[lane] = Rm[lane];
+  if (lane < 3) g->rinv[lane] = 1.0 / Rm[4 * lane];
   mm3(Ls, Ri, Ri, lane);  // Q = L R^-1
   if (lane < 9) g->Q[lane] = Ri[lane];
   __syncwarp();
@@ -338,82 +339,98 @@ __global__ void k_grid(Geo *g, GridIn in) {
   if (threadIdx.x == 0) grid_body(g, in);
 }
 
-// The neighbour rows of one home (iy, iz) class, written to out[0..maxrows);
-// returns their number.  cell_base is added to every row's first cell (the
-// system's first cell slot in a batch).
-__device__ int stencil_class(Geo *g, int cls, int cell_base, Row *out) {
+// The neighbour rows of one home (iy, iz) class, written to out[0..maxrows) by
+// the lanes of one warp (one row per lane); returns their number on every
+// lane.  Row order: dz (jz) outer, dy (jy) inner.  cell_base is added to every
+// row's first cell (the system's first cell slot in a batch).
+__device__ int stencil_class_warp(Geo *g, int cls, int cell_base, Row *out, int lane) {
+  constexpr int kMaxZ = 2 * kMaxFactor + 4;  // bound on the z-rows of a dynamic offset class
   const int l1 = g->nc[0], l2 = g->nc[1], l3 = g->nc[2];
   const int maxrows = g->maxrows;
-  const int variant = g->variant;
   const double rce = g->rc * (1.0 + kMargin);
   const double q = g->quantum;
-  {
-    const int iy = cls % l2, iz = cls / l2;
-    int nr = 0;
-    if (variant == NEMD_DS) {
-      const int K = g->kfac;
-      for (int dz = -K; dz <= K; dz++)
-        for (int dy = -K; dy <= K; dy++) {
-          int jyu = iy + dy, jzu = iz + dz;
-          int ky = floordiv_i(jyu, l2), kz = floordiv_i(jzu, l3);
-          int jy = jyu - ky * l2, jz = jzu - kz * l3;
-          const double c1 = dy, c2 = dz;
-          Row r;
-          set_shift(r, g->G[1] * c1 + g->G[2] * c2, g->G[4] * c1 + g->G[5] * c2, g->G[7] * c1 + g->G[8] * c2, q);
-          r.cbase = cell_base + l1 * (jy + l2 * jz);
-          r.sxi = 0;
-          r.dxlo = -K;
-          r.cnt = 2 * K + 1;
-          r.ky = (short)ky;
-          r.kz = (short)kz;
-          r.pad1 = 0;
-          if (nr < maxrows) out[nr] = r;
-          nr++;
-        }
-    } else {
-      const double w1 = g->w[0], w2 = g->w[1], w3 = g->w[2];
-      const double r12 = g->R[1], r13 = g->R[2], r23 = g->R[5];
-      int zlo = (int)floor(((double)iz * w3 - rce) / w3);
-      int zhi = (int)ceil(((double)(iz + 1) * w3 + rce) / w3) - 1;
-      for (int jzu = zlo; jzu <= zhi; jzu++) {
-        int kz = floordiv_i(jzu, l3), jz = jzu - kz * l3;
-        double yshift = (double)kz * r23;
-        int ylo = (int)floor(((double)iy * w2 - rce - yshift) / w2);
-        int yhi = (int)ceil(((double)(iy + 1) * w2 + rce - yshift) / w2) - 1;
-        for (int jyu = ylo; jyu <= yhi; jyu++) {
-          int ky = floordiv_i(jyu, l2), jy = jyu - ky * l2;
-          double sx = (double)ky * r12 + (double)kz * r13;
-          int xlo = (int)floor((-rce - sx) / w1);
-          int xhi = (int)ceil((w1 + rce - sx) / w1) - 1;
-          Row r;
-          const double sxi = rint(sx / w1);
-          set_shift(r, sx - sxi * w1, (double)(jyu - iy) * w2 + yshift, (double)(jzu - iz) * w3, q);
-          r.cbase = cell_base + l1 * (jy + l2 * jz);
-          r.sxi = (int)sxi;
-          r.dxlo = xlo;
-          r.cnt = xhi - xlo + 1;
-          r.ky = (short)ky;
-          r.kz = (short)kz;
-          r.pad1 = 0;
-          if (nr < maxrows) out[nr] = r;
-          nr++;
-        }
-      }
+  const int iy = cls % l2, iz = cls / l2;
+  int nr;
+  if (g->variant == NEMD_DS) {
+    const int K = g->kfac, side = 2 * K + 1;
+    nr = side * side;
+    for (int e = lane; e < nr && e < maxrows; e += 32) {
+      const int dz = e / side - K, dy = e % side - K;
+      const int jyu = iy + dy, jzu = iz + dz;
+      const int ky = floordiv_i(jyu, l2), kz = floordiv_i(jzu, l3);
+      const int jy = jyu - ky * l2, jz = jzu - kz * l3;
+      const double c1 = dy, c2 = dz;
+      Row r;
+      set_shift(r, g->G[1] * c1 + g->G[2] * c2, g->G[4] * c1 + g->G[5] * c2, g->G[7] * c1 + g->G[8] * c2, q);
+      r.cbase = cell_base + l1 * (jy + l2 * jz);
+      r.sxi = 0;
+      r.dxlo = -K;
+      r.cnt = 2 * K + 1;
+      r.ky = (short)ky;
+      r.kz = (short)kz;
+      r.pad1 = 0;
+      out[e] = r;
     }
-    if (nr > maxrows) {
-      atomicOr(&g->error, ERRB_CAPACITY);
-      nr = maxrows;
+  } else {
+    const double w1 = g->w[0], w2 = g->w[1], w3 = g->w[2];
+    const double r12 = g->R[1], r13 = g->R[2], r23 = g->R[5];
+    const int zlo = (int)floor(((double)iz * w3 - rce) / w3);
+    int zhi = (int)ceil(((double)(iz + 1) * w3 + rce) / w3) - 1;
+    if (zhi - zlo + 1 > kMaxZ) {
+      if (lane == 0) atomicOr(&g->error, ERRB_CAPACITY);
+      zhi = zlo + kMaxZ - 1;
     }
-    return nr;
+    int ylo[kMaxZ], ycnt[kMaxZ];
+    nr = 0;
+    for (int jzu = zlo; jzu <= zhi; jzu++) {
+      const int kz = floordiv_i(jzu, l3);
+      const double yshift = (double)kz * r23;
+      const int lo = (int)floor(((double)iy * w2 - rce - yshift) / w2);
+      const int hi = (int)ceil(((double)(iy + 1) * w2 + rce - yshift) / w2) - 1;
+      ylo[jzu - zlo] = lo;
+      ycnt[jzu - zlo] = hi - lo + 1;
+      nr += hi - lo + 1;
+    }
+    for (int e = lane; e < nr && e < maxrows; e += 32) {
+      int z = 0, base = 0;
+      while (e >= base + ycnt[z]) base += ycnt[z++];
+      const int jzu = zlo + z, jyu = ylo[z] + (e - base);
+      const int kz = floordiv_i(jzu, l3), jz = jzu - kz * l3;
+      const int ky = floordiv_i(jyu, l2), jy = jyu - ky * l2;
+      const double yshift = (double)kz * r23;
+      const double sx = (double)ky * r12 + (double)kz * r13;
+      const int xlo = (int)floor((-rce - sx) / w1);
+      const int xhi = (int)ceil((w1 + rce - sx) / w1) - 1;
+      Row r;
+      const double sxi = rint(sx / w1);
+      set_shift(r, sx - sxi * w1, (double)(jyu - iy) * w2 + yshift, (double)(jzu - iz) * w3, q);
+      r.cbase = cell_base + l1 * (jy + l2 * jz);
+      r.sxi = (int)sxi;
+      r.dxlo = xlo;
+      r.cnt = xhi - xlo + 1;
+      r.ky = (short)ky;
+      r.kz = (short)kz;
+      r.pad1 = 0;
+      out[e] = r;
+    }
   }
+  if (nr > maxrows) {
+    if (lane == 0) atomicOr(&g->error, ERRB_CAPACITY);
+    nr = maxrows;
+  }
+  return nr;
 }
 
-// One thread per home (iy, iz): the neighbour rows of that class.
+// One warp per home (iy, iz) class: the neighbour rows of that class.
 __global__ void k_stencil(Geo *g, Row *rows, int *rowcnt) {
   if (g->error) return;
   const int ncls = g->nc[1] * g->nc[2];
-  for (int cls = blockIdx.x * blockDim.x + threadIdx.x; cls < ncls; cls += gridDim.x * blockDim.x)
-    rowcnt[cls] = stencil_class(g, cls, 0, rows + (size_t)cls * g->maxrows);
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int cls = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; cls < ncls; cls += nw) {
+    const int nr = stencil_class_warp(g, cls, 0, rows + (size_t)cls * g->maxrows, lane);
+    if (lane == 0) rowcnt[cls] = nr;
+  }
 }
 
 cudaError_t launch_lattice(nemd_ctx *c, int validate, double tau) {
@@ -446,9 +463,9 @@ cudaError_t launch_grid(nemd_ctx *c) {
 
 cudaError_t launch_stencil(nemd_ctx *c) {
   int64_t classes = c->cap_cells;  // l2 * l3 <= ncells <= cap
-  int threads = 128;
-  int64_t blocks = (classes + threads - 1) / threads;
-  if (blocks > 4 * (int64_t)c->sms) blocks = 4 * (int64_t)c->sms;
+  int threads = 128;               // four classes per block
+  int64_t blocks = (classes + 3) / 4;
+  if (blocks > 8 * (int64_t)c->sms) blocks = 8 * (int64_t)c->sms;
   if (blocks < 1) blocks = 1;
   k_stencil<<<(int)blocks, threads, 0, c->stream>>>(c->geo, c->rows, c->rowcnt);
   c->launches += 1;
@@ -476,16 +493,19 @@ __global__ void k_b_grid(Geo *geo, const GridIn *__restrict__ grid, const SysInf
   }
 }
 
-// blockIdx.y = system; threads stride over its classes.
+// blockIdx.y = system; warps stride over its classes.
 __global__ void k_b_stencil(BatchView v) {
   const int s = blockIdx.y;
   Geo *g = v.geo + s;
   if (g->error) return;
   const SysInfo si = v.sys[s];
   const int ncls = g->nc[1] * g->nc[2];
-  for (int cls = blockIdx.x * blockDim.x + threadIdx.x; cls < ncls; cls += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int cls = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; cls < ncls; cls += nw) {
     const int slot = si.clo + cls;
-    v.rowcnt[slot] = stencil_class(g, cls, si.coff, v.rows + (size_t)slot * kBatchRowStride);
+    const int nr = stencil_class_warp(g, cls, si.coff, v.rows + (size_t)slot * kBatchRowStride, lane);
+    if (lane == 0) v.rowcnt[slot] = nr;
   }
 }
 
@@ -502,8 +522,8 @@ cudaError_t launch_batch_grid(cudaStream_t st, Geo *geo, const GridIn *grid, con
 }
 
 cudaError_t launch_batch_stencil(cudaStream_t st, const BatchView &v, int max_clcap) {
-  const int threads = 128;
-  int bx = (max_clcap + threads - 1) / threads;
+  const int threads = 128;  // four classes per block
+  int bx = (max_clcap + 3) / 4;
   if (bx < 1) bx = 1;
   if (bx > 64) bx = 64;
   k_b_stencil<<<dim3(bx, v.nsys), threads, 0, st>>>(v);

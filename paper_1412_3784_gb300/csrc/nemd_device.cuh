@@ -36,19 +36,23 @@ __device__ __forceinline__ void frac_to_cart(const double *L, const double s[3],
 // Rectangular rearrangement of the rotated box (Sec. 4.2): the point R s is
 // moved by lattice vectors into the brick [0,r11) x [0,r22) x [0,r33) --
 // first along z (shifting x and y by the third column of R), then y (shifting
-// x by r12), then x modulo r11.  b = R (s - m).
-__device__ __forceinline__ void brick_wrap(const double *R, const double s[3], double b[3], int m[3]) {
+// x by r12), then x modulo r11.  b = R (s - m).  The quotients use the
+// reciprocals rinv = 1 / r_ii; every caller uses this one function, so the
+// binning and the image of a pair agree even for points on a brick face (b
+// may then lie a rounding outside the brick; the cell index is clamped).
+__device__ __forceinline__ void brick_wrap(const double *R, const double *rinv, const double s[3], double b[3],
+                                           int m[3]) {
   double x = R[0] * s[0] + R[1] * s[1] + R[2] * s[2];
   double y = R[4] * s[1] + R[5] * s[2];
   double z = R[8] * s[2];
-  double m3 = floor(z / R[8]);
+  double m3 = floor(z * rinv[2]);
   z -= m3 * R[8];
   y -= m3 * R[5];
   x -= m3 * R[2];
-  double m2 = floor(y / R[4]);
+  double m2 = floor(y * rinv[1]);
   y -= m2 * R[4];
   x -= m2 * R[1];
-  double m1 = floor(x / R[0]);
+  double m1 = floor(x * rinv[0]);
   x -= m1 * R[0];
   b[0] = x;
   b[1] = y;
@@ -83,7 +87,7 @@ __device__ __forceinline__ double canon_r2(const Geo *g, const double *q, int oi
 __device__ __forceinline__ void brick_image(const Geo *g, const double *q, int oi, int m[3]) {
   double s[3], b[3];
   frac_wrap(g->Linv, q[3 * (size_t)oi], q[3 * (size_t)oi + 1], q[3 * (size_t)oi + 2], s);
-  brick_wrap(g->R, s, b, m);
+  brick_wrap(g->R, g->rinv, s, b, m);
 }
 
 }  // namespace nemd

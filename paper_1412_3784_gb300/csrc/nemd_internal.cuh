@@ -19,6 +19,7 @@ constexpr double kMargin = 1e-12;
 constexpr int kMaxFactor = 3;          // largest cell-size factor k
 constexpr int kMaxSpan = 8;            // largest x-span (cells) of a chunk of the grouped kernel
 constexpr int kRecheckCap = 1 << 14;   // fine-band candidates per evaluation (~1e-7 of candidates)
+constexpr int kFixupBlocks = 16;       // blocks of the float64 fix-up pass (when partial slots allow)
 constexpr int kMaxRowsPerClass = 64;   // (2k+2)^2 for k = 3
 
 // Device error word bits (deferred errors).
@@ -42,6 +43,7 @@ struct Geo {
   // ---- lattice (a1) ----
   double tau;
   double L[9], Linv[9], V, h[3], Q[9], R[9];
+  double rinv[3];  // 1 / r_ii
   // ---- grid (a3) ----
   int nc[3];
   int ncells;
@@ -186,6 +188,7 @@ struct nemd_ctx {
   // grouped force kernel
   int4 *chunks;
   int *nchunks;
+  int *chunk_cnt, *chunk_off, *chunk_tiles;  // per class slot: chunks, their scan (cap_cells + 1)
   int group;
   // candidates left within float32 rounding of rc, decided by the float64 fix-up
   int4 *recheck;
