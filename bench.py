@@ -54,6 +54,22 @@ WORKLOADS = {
 C_TEST = 7     # FP32 instructions per candidate test: 3 FADD, 1 FMUL, 2 FFMA, 1 FSETP
 C_PAIR = 24    # FP32 instructions per interacting pair (force, energy, virial, both sides)
 
+# DRAM bytes (read + write) of one k_force_warp launch on the N = 2^20 system,
+# from the ncu capture summarised in profiles/k_force_warp_general_n1m.md; valid
+# only while the kernel's sources are the ones captured (sha1 prefixes).
+WARP_TRAFFIC = {"bytes": 39.403008e6 + 0.265984e6,
+                "sha1": {"paper_1412_3784_gb300/csrc/force_warp.cu": "65169c16eaef",
+                         "paper_1412_3784_gb300/csrc/force_common.cuh": "137892eaafbd"}}
+
+
+def warp_traffic():
+    import hashlib
+    for rel, prefix in WARP_TRAFFIC["sha1"].items():
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            if not hashlib.sha1(f.read()).hexdigest().startswith(prefix):
+                return None
+    return WARP_TRAFFIC["bytes"]
+
 
 def parse():
     p = argparse.ArgumentParser()
@@ -356,7 +372,7 @@ def section_main(args, rank, world, dev, torch, nemd, W):
     ops_per_launch = ops_step / S
     achieved = ops_per_launch / avg_launch_s
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": warp_traffic() if tuned_kernel == 2 else None,
                 "kernel": kernel_name.get(tuned_kernel, "?"), "ops_per_launch": ops_per_launch,
                 "avg_launch_ms": avg_launch_s * 1e3,
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x {peak_mhz:.0f} MHz (FP32 instruction "

@@ -35,9 +35,11 @@ __device__ __forceinline__ void mm3(const double *a, const double *b, double *c,
   __syncwarp();
 }
 
-// Row shift split into an exact multiple of the quantum q and a float32 residual.
+// Row shift split into an exact multiple of the quantum q (a power of two, so
+// scaling by 1/q is exact) and a float32 residual.
 __device__ __forceinline__ void set_shift(Row &r, double ox, double oy, double oz, double q) {
-  double qx = rint(ox / q) * q, qy = rint(oy / q) * q, qz = rint(oz / q) * q;
+  const double qi = 1.0 / q;
+  double qx = rint(ox * qi) * q, qy = rint(oy * qi) * q, qz = rint(oz * qi) * q;
   r.shx = (float)qx;
   r.shy = (float)qy;
   r.shz = (float)qz;
@@ -372,10 +374,14 @@ __device__ int stencil_class_warp(Geo *g, int cls, int cell_base, Row *out, int 
       out[e] = r;
     }
   } else {
+    // window bounds by reciprocals of the cell sides: a bound that moves by a
+    // rounding only adds or drops a cell lying at distance rc (1 + 1e-12) or
+    // more, which holds no partner
     const double w1 = g->w[0], w2 = g->w[1], w3 = g->w[2];
+    const double iw1 = 1.0 / w1, iw2 = 1.0 / w2, iw3 = 1.0 / w3;
     const double r12 = g->R[1], r13 = g->R[2], r23 = g->R[5];
-    const int zlo = (int)floor(((double)iz * w3 - rce) / w3);
-    int zhi = (int)ceil(((double)(iz + 1) * w3 + rce) / w3) - 1;
+    const int zlo = (int)floor(((double)iz * w3 - rce) * iw3);
+    int zhi = (int)ceil(((double)(iz + 1) * w3 + rce) * iw3) - 1;
     if (zhi - zlo + 1 > kMaxZ) {
       if (lane == 0) atomicOr(&g->error, ERRB_CAPACITY);
       zhi = zlo + kMaxZ - 1;
@@ -385,8 +391,8 @@ __device__ int stencil_class_warp(Geo *g, int cls, int cell_base, Row *out, int 
     for (int jzu = zlo; jzu <= zhi; jzu++) {
       const int kz = floordiv_i(jzu, l3);
       const double yshift = (double)kz * r23;
-      const int lo = (int)floor(((double)iy * w2 - rce - yshift) / w2);
-      const int hi = (int)ceil(((double)(iy + 1) * w2 + rce - yshift) / w2) - 1;
+      const int lo = (int)floor(((double)iy * w2 - rce - yshift) * iw2);
+      const int hi = (int)ceil(((double)(iy + 1) * w2 + rce - yshift) * iw2) - 1;
       ylo[jzu - zlo] = lo;
       ycnt[jzu - zlo] = hi - lo + 1;
       nr += hi - lo + 1;
@@ -399,10 +405,10 @@ __device__ int stencil_class_warp(Geo *g, int cls, int cell_base, Row *out, int 
       const int ky = floordiv_i(jyu, l2), jy = jyu - ky * l2;
       const double yshift = (double)kz * r23;
       const double sx = (double)ky * r12 + (double)kz * r13;
-      const int xlo = (int)floor((-rce - sx) / w1);
-      const int xhi = (int)ceil((w1 + rce - sx) / w1) - 1;
+      const int xlo = (int)floor((-rce - sx) * iw1);
+      const int xhi = (int)ceil((w1 + rce - sx) * iw1) - 1;
       Row r;
-      const double sxi = rint(sx / w1);
+      const double sxi = rint(sx * iw1);
       set_shift(r, sx - sxi * w1, (double)(jyu - iy) * w2 + yshift, (double)(jzu - iz) * w3, q);
       r.cbase = cell_base + l1 * (jy + l2 * jz);
       r.sxi = (int)sxi;
