@@ -80,9 +80,13 @@ typedef enum nemd_option {
     NEMD_OPT_RECORD_PAIRS = 2,  /* > 0: capacity of the pair record (verification mode)   */
     NEMD_OPT_KERNEL = 3,        /* force kernel: 0 plain (one thread per particle),
                                    1 grouped (a group of lanes per chunk of a cell row,
-                                   queued force evaluation), 2 warp (one chunk of 32 per
-                                   warp, uniform loops); 1 and 2 need N <= 2^21 and
-                                   k <= 2, otherwise the plain kernel runs                 */
+                                   queued force evaluation; N <= 2^21), 2 warp (one chunk
+                                   of 32 per warp, neighbour rows staged in shared
+                                   memory), 3 warp with half neighbourhoods (each
+                                   unordered pair evaluated once, partner forces added
+                                   with atomics: F is not bitwise reproducible from run
+                                   to run; pair records use kernel 2).  1-3 need k <= 2,
+                                   otherwise the plain kernel runs                         */
     NEMD_OPT_CELL_FACTOR = 4,   /* k >= 1: cells at least rc/k wide, stencil reach k    */
     NEMD_OPT_BLOCK = 5,         /* threads per block of the force kernel (multiple of 32) */
     NEMD_OPT_TIMING = 6,        /* 1: record CUDA events around every force-kernel launch
@@ -187,8 +191,9 @@ int nemd_get_kernel_time(nemd_ctx *ctx, double *ms_total, int64_t *nlaunch);
  *
  * The paper has no counterpart (its cells are always at least the cut-off
  * wide, Sec. 4).  Every candidate configuration -- force kernel (plain, warp,
- * grouped), lanes per group (4, 8, 16), cell-size factor k (1, 2) -- gives the
- * same pair set and forces; only the time differs. */
+ * warp with half neighbourhoods, grouped), lanes per group (4, 8, 16),
+ * cell-size factor k (1, 2) -- gives the same pair set and, up to rounding,
+ * the same forces; only the time differs. */
 typedef struct nemd_tune_config {
     int32_t kernel, group, cell_factor, pad;
 } nemd_tune_config;

@@ -20,9 +20,10 @@ struct Candidate {
   int kernel, group, kfac;
 };
 
-// plain kernel; warp kernel at k = 1, 2; grouped kernel with 4, 8, 16 lanes at k = 1, 2
-const Candidate kCandidates[] = {{0, 16, 1}, {2, 32, 1}, {2, 32, 2}, {1, 4, 1},  {1, 8, 1},
-                                 {1, 16, 1}, {1, 4, 2},  {1, 8, 2},  {1, 16, 2}};
+// plain kernel; warp kernel at k = 1, 2; grouped kernel with 4, 8, 16 lanes at
+// k = 1, 2; warp kernel with half neighbourhoods at k = 1, 2
+const Candidate kCandidates[] = {{0, 16, 1}, {2, 32, 1}, {2, 32, 2}, {1, 4, 1}, {1, 8, 1},  {1, 16, 1},
+                                 {1, 4, 2},  {1, 8, 2},  {1, 16, 2}, {3, 32, 1}, {3, 32, 2}};
 constexpr int kNumCandidates = sizeof(kCandidates) / sizeof(kCandidates[0]);
 static_assert(kNumCandidates == nemd::kTuneCandidates, "cache layout");
 

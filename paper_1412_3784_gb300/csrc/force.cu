@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(NT) k_force_plain(const Geo *__restrict__ g, c
 __global__ void k_recheck_fixup(const Geo *__restrict__ g, const int4 *__restrict__ list,
                                 const int *__restrict__ count, const float4 *__restrict__ pos,
                                 const double *__restrict__ q, Pot pp, float *__restrict__ F,
-                                double *__restrict__ partial_slot) {
+                                double *__restrict__ partial_slot, int half) {
   double v[kPartials];
   for (int k = 0; k < kPartials; k++) v[k] = 0.0;
   const int n = min(*count, kRecheckCap);
@@ -186,7 +186,11 @@ __global__ void k_recheck_fixup(const Geo *__restrict__ g, const int4 *__restric
     const double inv = 1.0 / r2, s2 = pp.sig2d * inv, s6 = s2 * s2 * s2;
     const double fr = pp.eps24d * inv * s6 * (2.0 * s6 - 1.0);
     if (F)
-      for (int a = 0; a < 3; a++) atomicAdd(&F[3 * (size_t)oi + a], (float)(-fr * d[a]));
+      for (int a = 0; a < 3; a++) {
+        atomicAdd(&F[3 * (size_t)oi + a], (float)(-fr * d[a]));
+        // half neighbourhoods defer only one orientation of the pair
+        if (half) atomicAdd(&F[3 * (size_t)oj + a], (float)(fr * d[a]));
+      }
     // frame components: W_frame = Q^T (d d^T) Q fr, d_frame = Q^T d
     double df[3];
     for (int a = 0; a < 3; a++) df[a] = g->Q[a] * d[0] + g->Q[3 + a] * d[1] + g->Q[6 + a] * d[2];
@@ -219,7 +223,7 @@ __global__ void k_recheck_fixup(const Geo *__restrict__ g, const int4 *__restric
 // U, W and the counters.
 __global__ void k_reduce_final(Geo *__restrict__ g, const double *__restrict__ partials, int nblocks,
                                int frame_is_cartesian, double *__restrict__ uw,
-                               unsigned long long *__restrict__ counters) {
+                               unsigned long long *__restrict__ counters, double hf) {
   __shared__ double sh[256][kPartials];
   double acc[kPartials];
 #pragma unroll
@@ -238,14 +242,15 @@ __global__ void k_reduce_final(Geo *__restrict__ g, const double *__restrict__ p
   }
   if (threadIdx.x == 0) {
     const bool ok = !(g->error & (ERRB_BOX | ERRB_CAPACITY));
-    double U = 0.5 * sh[0][0];
+    // hf: 1/2 for full neighbourhoods (every pair met from both sides), 1 for half
+    double U = hf * sh[0][0];
     double Wr[9];
-    Wr[0] = 0.5 * sh[0][1];
-    Wr[4] = 0.5 * sh[0][2];
-    Wr[8] = 0.5 * sh[0][3];
-    Wr[1] = Wr[3] = 0.5 * sh[0][4];
-    Wr[2] = Wr[6] = 0.5 * sh[0][5];
-    Wr[5] = Wr[7] = 0.5 * sh[0][6];
+    Wr[0] = hf * sh[0][1];
+    Wr[4] = hf * sh[0][2];
+    Wr[8] = hf * sh[0][3];
+    Wr[1] = Wr[3] = hf * sh[0][4];
+    Wr[2] = Wr[6] = hf * sh[0][5];
+    Wr[5] = Wr[7] = hf * sh[0][6];
     double W[9];
     if (!frame_is_cartesian && g->variant == NEMD_DO) {
       double T9[9];
@@ -260,7 +265,7 @@ __global__ void k_reduce_final(Geo *__restrict__ g, const double *__restrict__ p
     }
     uw[0] = ok ? U : 0.0;
     for (int k = 0; k < 9; k++) uw[1 + k] = ok ? W[k] : 0.0;
-    counters[0] = (unsigned long long)(0.5 * sh[0][7] + 0.25);
+    counters[0] = (unsigned long long)(hf * sh[0][7] + 0.25);
     counters[1] = (unsigned long long)(sh[0][8] + 0.5);
     counters[2] = (unsigned long long)(sh[0][9] + 0.5);
     g->sticky |= g->error;
@@ -287,8 +292,9 @@ Pot make_pot(const nemd_ctx *c) {
   return p;
 }
 
-cudaError_t launch_reduce(nemd_ctx *c, int nblocks, int frame_is_cartesian, double *UW_dev) {
-  k_reduce_final<<<1, 256, 0, c->stream>>>(c->geo, c->partials, nblocks, frame_is_cartesian, UW_dev, c->counters);
+cudaError_t launch_reduce(nemd_ctx *c, int nblocks, int frame_is_cartesian, double *UW_dev, bool half) {
+  k_reduce_final<<<1, 256, 0, c->stream>>>(c->geo, c->partials, nblocks, frame_is_cartesian, UW_dev, c->counters,
+                                           half ? 1.0 : 0.5);
   c->launches += 1;
   return cudaGetLastError();
 }
@@ -322,9 +328,16 @@ cudaError_t launch_forces(nemd_ctx *c, float *F_dev, double *UW_dev) {
     cudaError_t e = cudaMemsetAsync(c->nrecheck, 0, sizeof(int), c->stream);
     if (e != cudaSuccess) return e;
   }
-  // the grouped and warp kernels have no float64 pair path: precise mode runs the plain kernel
+  // the grouped and warp kernels have no float64 pair path: precise mode runs the
+  // plain kernel; pair records take the full-neighbourhood warp kernel
   const bool grouped = c->kernel == 1 && !c->precise && chunk_kernel_applies(c);
-  const bool warped = c->kernel == 2 && !c->precise && warp_kernel_applies(c);
+  const bool warped = (c->kernel == 2 || c->kernel == 3) && !c->precise && warp_kernel_applies(c);
+  const bool half = warped && c->kernel == 3 && c->record_cap == 0;
+  if (half && F_dev && c->n > 0) {
+    // half neighbourhoods add the partners' forces with atomics: start from zero
+    cudaError_t e = cudaMemsetAsync(F_dev, 0, sizeof(float) * 3 * (size_t)c->n, c->stream);
+    if (e != cudaSuccess) return e;
+  }
   if (grouped || warped) {
     cudaError_t e = launch_chunk_build(c, warped ? 32 : c->group);
     if (e != cudaSuccess) return e;
@@ -333,7 +346,7 @@ cudaError_t launch_forces(nemd_ctx *c, float *F_dev, double *UW_dev) {
   if (timed) cudaEventRecord(c->ev[2 * c->ev_n], c->stream);
   int nblocks;
   if (warped) {
-    cudaError_t e = launch_force_warp(c, F_dev, &nblocks);
+    cudaError_t e = launch_force_warp(c, F_dev, &nblocks, half);
     if (e != cudaSuccess) return e;
   } else if (grouped) {
     cudaError_t e = launch_force_chunk(c, F_dev, &nblocks);
@@ -353,9 +366,9 @@ cudaError_t launch_forces(nemd_ctx *c, float *F_dev, double *UW_dev) {
   int nfix = kFixupBlocks;
   if (nblocks + nfix > c->cap_partials) nfix = (int)(c->cap_partials - nblocks);
   k_recheck_fixup<<<nfix, 256, 0, c->stream>>>(c->geo, c->recheck, c->nrecheck, c->pos4, c->q_dev, make_pot(c),
-                                               F_dev, c->partials + (size_t)nblocks * kPartials);
+                                               F_dev, c->partials + (size_t)nblocks * kPartials, half ? 1 : 0);
   c->launches += 1;
-  return launch_reduce(c, nblocks + nfix, c->precise ? 1 : 0, UW_dev);
+  return launch_reduce(c, nblocks + nfix, c->precise ? 1 : 0, UW_dev, half);
 }
 
 

@@ -15,8 +15,9 @@ struct Pot {
 
 Pot make_pot(const nemd_ctx *c);
 
-// FP64 reductions of the per-block partials (force.cu).
-cudaError_t launch_reduce(nemd_ctx *c, int nblocks, int frame_is_cartesian, double *UW_dev);
+// FP64 reductions of the per-block partials (force.cu); half: the partials hold
+// every unordered pair once (half neighbourhoods) instead of twice.
+cudaError_t launch_reduce(nemd_ctx *c, int nblocks, int frame_is_cartesian, double *UW_dev, bool half = false);
 
 // Per-block sums of the per-thread values (float64, fixed order within the
 // block) -> partials[blockIdx.x * kPartials + k].
@@ -111,12 +112,20 @@ struct Acc {
   }
   // the same with r^2 already formed; 1 / r^2 by the fast reciprocal (2 ulp)
   __device__ __forceinline__ void add_r2(const Pot &pp, float dx, float dy, float dz, float r2) {
+    float gx, gy, gz;
+    add_pair(pp, dx, dy, dz, r2, gx, gy, gz);
+  }
+  // ... also returning the force on the partner j, g = fr d (the force on i is -g)
+  __device__ __forceinline__ void add_pair(const Pot &pp, float dx, float dy, float dz, float r2, float &gx,
+                                           float &gy, float &gz) {
     const float inv = __fdividef(1.0f, r2);
     const float s2 = pp.sig2 * inv;
     const float s6 = s2 * s2 * s2;
     const float fr = pp.eps24 * inv * s6 * (2.0f * s6 - 1.0f);
     u += fmaf(pp.eps4 * s6, s6 - 1.0f, -pp.ushift);
-    const float gx = fr * dx, gy = fr * dy, gz = fr * dz;
+    gx = fr * dx;
+    gy = fr * dy;
+    gz = fr * dz;
     fx -= gx;
     fy -= gy;
     fz -= gz;

@@ -31,36 +31,62 @@ namespace nemd {
 
 constexpr int kWarpThreads = 128;  // 4 warps per block
 constexpr int kRowsStaged = 32;    // rows per class the kernel stages (cell factor <= 2)
-constexpr int kStage = 256;        // staged particles per warp: a queue entry is one byte
 constexpr int kWarpQueue = 64;     // queue entries per lane
 constexpr int kTestBlock = 32;     // candidates tested between two queue checks
 constexpr int kMetaBias = 1 << 12;  // R_j.w = row | (unwrapped x-cell + kMetaBias) << 5
 
-struct WarpStage {
-  float4 X[kStage];  // .w: sorted index of j (bits)
-  float4 R[kStage];  // .w: row and unwrapped x-cell of j (bits)
+// Shared memory of one warp.  HALF (half neighbourhoods) also accumulates the
+// force on every staged partner (Fj), and stages fewer particles so that four
+// blocks still fit an SM.
+template <bool HALF>
+struct WarpStageT {
+  static constexpr int kSlots = HALF ? 192 : 256;  // a queue entry (slot) is one byte
+  float4 X[kSlots];  // .w: sorted index of j (bits)
+  float4 R[kSlots];  // .w: row and unwrapped x-cell of j (bits)
+  float Fj[HALF ? 3 : 1][HALF ? kSlots : 1];
   unsigned char q[kWarpQueue][32];
   float4 rows[kRowsStaged][3];
 };
+using WarpStage = WarpStageT<false>;
 
-// Forces of the queued pairs of every lane.
-template <bool RECORD>
-__device__ __forceinline__ void warp_flush(WarpStage &S, int &qn, int &nre, int lane, int ki, const float4 &pi,
-                                           const float3 &Xi, const float3 &Ri, const Geo *g,
-                                           const float4 *__restrict__ pos, const Pot &pp, Acc &acc,
+// Shared-memory reduction without a returned value.
+__device__ __forceinline__ void red_shared_add(float *p, float v) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+
+// Forces of the queued pairs of every lane.  HALF: entries of the home row
+// (row rhome) count only towards partners ahead of the lane's particle --
+// a larger unwrapped x-cell, or the same cell and a larger sorted index --
+// and each accepted pair also adds its force to the partner's slot.
+template <bool RECORD, bool HALF>
+__device__ __forceinline__ void warp_flush(WarpStageT<HALF> &S, int &qn, int &nre, int lane, int ki,
+                                           const float4 &pi, const float3 &Xi, const float3 &Ri, int ixu, int rhome,
+                                           const Geo *g, const float4 *__restrict__ pos, const Pot &pp, Acc &acc,
                                            const double *q, int32_t *pair_buf, unsigned long long *pair_count,
                                            long long pair_cap, int4 *rlist, int *rcount, int *err) {
   const int m = __reduce_max_sync(0xffffffffu, qn);
   const float lo = g->rc2_lo, lo2 = g->rc2_lo2, hi2 = g->rc2_hi2;
+  // HALF: lanes start at different points of their queues, so that one step of
+  // the flush rarely adds to the same partner slot from several lanes
+  int e = HALF && qn > 0 ? (7 * lane) % qn : 0;
   for (int s = 0; s < m; s++) {
     if (s < qn) {
-      const int slot = S.q[s][lane];
+      const int slot = S.q[HALF ? e : s][lane];
+      if (HALF && ++e == qn) e = 0;
       const float4 X = S.X[slot], R = S.R[slot];
+      const int j = __float_as_int(X.w);
+      if (HALF) {
+        const int meta = __float_as_int(R.w);
+        if ((meta & 31) == rhome) {
+          const int jxu = (meta >> 5) - kMetaBias;
+          if (!(jxu > ixu || (jxu == ixu && j > ki))) continue;
+        }
+      }
       const float cx = (X.x - Xi.x) + (R.x - Ri.x);
       const float cy = (X.y - Xi.y) + (R.y - Ri.y);
       const float cz = (X.z - Xi.z) + (R.z - Ri.z);
       const float r2c = fmaf(cz, cz, fmaf(cy, cy, cx * cx));
-      const int j = __float_as_int(X.w);
       bool accept = r2c < lo2;
       if (!(r2c < lo)) nre++;
       if (!accept && r2c < hi2) {
@@ -75,7 +101,15 @@ __device__ __forceinline__ void warp_flush(WarpStage &S, int &qn, int &nre, int 
       }
       // the particle itself: the same sorted index at exactly zero distance
       if (accept && !(j == ki && r2c == 0.f)) {
-        acc.add_r2(pp, cx, cy, cz, r2c);
+        if (HALF) {
+          float gx, gy, gz;
+          acc.add_pair(pp, cx, cy, cz, r2c, gx, gy, gz);
+          red_shared_add(&S.Fj[0][slot], gx);
+          red_shared_add(&S.Fj[HALF ? 1 : 0][slot], gy);
+          red_shared_add(&S.Fj[HALF ? 2 : 0][slot], gz);
+        } else {
+          acc.add_r2(pp, cx, cy, cz, r2c);
+        }
         if (RECORD) {
           const int meta = __float_as_int(R.w);
           const int kyz = __float_as_int(S.rows[meta & 31][2].y);
@@ -89,21 +123,46 @@ __device__ __forceinline__ void warp_flush(WarpStage &S, int &qn, int &nre, int 
   qn = 0;
 }
 
+// HALF: add the forces accumulated on staged partners [0, fill) to F
+// (Cartesian, F = Q F_frame), then the slots may be reused.
+template <bool HALF>
+__device__ __forceinline__ void flush_partners(WarpStageT<HALF> &S, int fill, int lane, const Geo *g,
+                                               const float4 *__restrict__ pos, float *F) {
+  if (!HALF) return;
+  __syncwarp();
+  if (F) {
+    const float *Qm = g->Qf;
+    for (int t = lane; t < fill; t += 32) {
+      const float fx = S.Fj[0][t], fy = S.Fj[HALF ? 1 : 0][t], fz = S.Fj[HALF ? 2 : 0][t];
+      if (fx != 0.f || fy != 0.f || fz != 0.f) {
+        const int oj = __float_as_int(pos[__float_as_int(S.X[t].w)].w);
+        atomicAdd(&F[3 * (size_t)oj], Qm[0] * fx + Qm[1] * fy + Qm[2] * fz);
+        atomicAdd(&F[3 * (size_t)oj + 1], Qm[3] * fx + Qm[4] * fy + Qm[5] * fz);
+        atomicAdd(&F[3 * (size_t)oj + 2], Qm[6] * fx + Qm[7] * fy + Qm[8] * fz);
+      }
+    }
+  }
+  __syncwarp();
+}
+
 // Everything one warp does for one chunk cd: stage the rows of the chunk's
 // class (crow, nr of them), then per row stage, test and queue, flushing as
 // needed.  On return acc.fx, fy, fz hold the force on the lane's particle pi
 // (sorted index ki; act is false for lanes past the chunk's count) in the
 // variant's frame, and its pair sums have been added to acc.  cell_base is the
-// system's first cell slot (0 for a single system).
-template <bool RECORD>
+// system's first cell slot (0 for a single system).  HALF visits only the rows
+// ahead of the home row and the forward half of the home row, and adds the
+// partners' forces to F (which must start at zero) as it goes.
+template <bool RECORD, bool HALF>
 __device__ __forceinline__ void warp_chunk(const int4 cd, const Row *__restrict__ crow, int nr, int cell_base,
                                            const Geo *g, const float4 *__restrict__ pos,
                                            const float4 *__restrict__ posr, const int *__restrict__ cell_sorted,
-                                           const int *__restrict__ start, WarpStage &S, const Pot &pp,
-                                           const double *q, Acc &acc, int &ncand, int &nre, bool &act, float4 &pi,
-                                           int &ki, int32_t *pair_buf, unsigned long long *pair_count,
+                                           const int *__restrict__ start, WarpStageT<HALF> &S, const Pot &pp,
+                                           const double *q, float *F, Acc &acc, int &ncand, int &nre, bool &act,
+                                           float4 &pi, int &ki, int32_t *pair_buf, unsigned long long *pair_count,
                                            long long pair_cap, int4 *rlist, int *rcount, int *err) {
   constexpr unsigned FULL = 0xffffffffu;
+  constexpr int kStage = WarpStageT<HALF>::kSlots;
   const int lane = threadIdx.x & 31;
   const int l1 = g->nc[0];
   const float sx = g->step[0], sy = g->step[1], sz = g->step[2];
@@ -113,7 +172,8 @@ __device__ __forceinline__ void warp_chunk(const int4 cd, const Row *__restrict_
   pi = pos[ki];
   const float4 pir = posr[ki];
   const int ixlo = cd.w & 0xffff, ixhi = cd.w >> 16;
-  const float ai = (float)((cell_sorted[ki] - cell_base) % l1 - ixlo);
+  const int ixu = (cell_sorted[ki] - cell_base) % l1;
+  const float ai = (float)(ixu - ixlo);
   const float3 Xi = make_float3(fmaf(ai, sx, pi.x), fmaf(ai, sy, pi.y), fmaf(ai, sz, pi.z));
   const float3 Ri = make_float3(fmaf(ai, srx, pir.x), fmaf(ai, sry, pir.y), fmaf(ai, srz, pir.z));
   {
@@ -122,6 +182,10 @@ __device__ __forceinline__ void warp_chunk(const int4 cd, const Row *__restrict_
     for (int e = lane; e < 3 * nr; e += 32) S.rows[e / 3][e % 3] = src[e];
     __syncwarp();
   }
+  int rhome = -1;
+  if (HALF)
+    for (int r = 0; r < nr; r++)
+      if (__float_as_int(S.rows[r][2].w) == 0) rhome = r;
   const float hil = act ? g->rc2_hi : -1.0f;  // an inactive lane accepts nothing
   acc.fx = acc.fy = acc.fz = 0.f;
   int qn = 0, fill = 0;
@@ -140,6 +204,7 @@ __device__ __forceinline__ void warp_chunk(const int4 cd, const Row *__restrict_
 
   for (int r = 0; r < nr; r++) {
     const float4 s0 = S.rows[r][0], s1 = S.rows[r][1], s2 = S.rows[r][2];
+    if (HALF && __float_as_int(s2.w) < 0) continue;  // met from the partner's side
     const int cbase = __float_as_int(s0.w), dxlo = __float_as_int(s1.w);
     const int rcnt = __float_as_int(s2.x), sxi = __float_as_int(s2.z);
     const int ulo = ixlo + dxlo, nu = ixhi - ixlo + rcnt;
@@ -159,8 +224,9 @@ __device__ __forceinline__ void warp_chunk(const int4 cd, const Row *__restrict_
       if (act) ncand += e - b;
       for (int p = b; p < e;) {
         if (fill == kStage) {
-          warp_flush<RECORD>(S, qn, nre, lane, ki, pi, Xi, Ri, g, pos, pp, acc, q, pair_buf, pair_count, pair_cap,
-                             rlist, rcount, err);
+          warp_flush<RECORD, HALF>(S, qn, nre, lane, ki, pi, Xi, Ri, ixu, rhome, g, pos, pp, acc, q, pair_buf,
+                                   pair_count, pair_cap, rlist, rcount, err);
+          flush_partners<HALF>(S, fill, lane, g, pos, F);
           fill = 0;
         }
         const int take = min(e - p, kStage - fill);
@@ -174,13 +240,18 @@ __device__ __forceinline__ void warp_chunk(const int4 cd, const Row *__restrict_
                                       __int_as_float(j));
           S.R[fill + t] = make_float4(fmaf(A, srx, pjr.x + s1.x), fmaf(A, sry, pjr.y + s1.y),
                                       fmaf(A, srz, pjr.z + s1.z), __int_as_float(meta_run + (cjx << 5)));
+          if (HALF) {
+            S.Fj[0][fill + t] = 0.f;
+            S.Fj[HALF ? 1 : 0][fill + t] = 0.f;
+            S.Fj[HALF ? 2 : 0][fill + t] = 0.f;
+          }
         }
         __syncwarp();
         for (int k0 = fill; k0 < fill + take; k0 += kTestBlock) {
           const int k1 = min(fill + take, k0 + kTestBlock);
           if (__any_sync(FULL, qn > kWarpQueue - kTestBlock))
-            warp_flush<RECORD>(S, qn, nre, lane, ki, pi, Xi, Ri, g, pos, pp, acc, q, pair_buf, pair_count, pair_cap,
-                               rlist, rcount, err);
+            warp_flush<RECORD, HALF>(S, qn, nre, lane, ki, pi, Xi, Ri, ixu, rhome, g, pos, pp, acc, q, pair_buf,
+                                     pair_count, pair_cap, rlist, rcount, err);
 #define NEMD_TEST(P, K)                                                       \
   {                                                                           \
     const float ddx = (P).x - Xi.x, ddy = (P).y - Xi.y, ddz = (P).z - Xi.z;   \
@@ -210,8 +281,9 @@ __device__ __forceinline__ void warp_chunk(const int4 cd, const Row *__restrict_
       if (jx == l1) jx = 0;
     }
   }
-  warp_flush<RECORD>(S, qn, nre, lane, ki, pi, Xi, Ri, g, pos, pp, acc, q, pair_buf, pair_count, pair_cap, rlist,
-                     rcount, err);
+  warp_flush<RECORD, HALF>(S, qn, nre, lane, ki, pi, Xi, Ri, ixu, rhome, g, pos, pp, acc, q, pair_buf, pair_count,
+                           pair_cap, rlist, rcount, err);
+  flush_partners<HALF>(S, fill, lane, g, pos, F);
 }
 
 // F (Cartesian) of a lane's particle from its frame force: F = Q F_frame.
@@ -223,7 +295,17 @@ __device__ __forceinline__ void store_force(float *F, const Geo *g, const float4
   F[3 * (size_t)oi + 2] = Qm[6] * acc.fx + Qm[7] * acc.fy + Qm[8] * acc.fz;
 }
 
-template <bool RECORD>
+// HALF: other warps add partner forces to the same particles, so the lane's own
+// force is added too.
+__device__ __forceinline__ void add_force(float *F, const Geo *g, const float4 &pi, const Acc &acc) {
+  const float *Qm = g->Qf;
+  const int oi = __float_as_int(pi.w);
+  atomicAdd(&F[3 * (size_t)oi], Qm[0] * acc.fx + Qm[1] * acc.fy + Qm[2] * acc.fz);
+  atomicAdd(&F[3 * (size_t)oi + 1], Qm[3] * acc.fx + Qm[4] * acc.fy + Qm[5] * acc.fz);
+  atomicAdd(&F[3 * (size_t)oi + 2], Qm[6] * acc.fx + Qm[7] * acc.fy + Qm[8] * acc.fz);
+}
+
+template <bool RECORD, bool HALF>
 __global__ void __launch_bounds__(kWarpThreads) k_force_warp(
     const Geo *__restrict__ g, const float4 *__restrict__ pos, const float4 *__restrict__ posr,
     const int *__restrict__ cell_sorted, const int *__restrict__ start, const Row *__restrict__ rows,
@@ -232,7 +314,7 @@ __global__ void __launch_bounds__(kWarpThreads) k_force_warp(
     int32_t *__restrict__ pair_buf, unsigned long long *__restrict__ pair_count, long long pair_cap,
     int4 *__restrict__ rlist, int *__restrict__ rcount, int *__restrict__ err) {
   constexpr int kWarps = kWarpThreads / 32;
-  __shared__ WarpStage stage[kWarps];
+  __shared__ WarpStageT<HALF> stage[kWarps];
   const int warp = threadIdx.x >> 5;
 
   Acc acc;  // U, W and the pair count accumulate over every particle this lane owns
@@ -247,22 +329,27 @@ __global__ void __launch_bounds__(kWarpThreads) k_force_warp(
     bool act;
     float4 pi;
     int ki;
-    warp_chunk<RECORD>(cd, rows + (size_t)cd.z * maxrows, rowcnt[cd.z], 0, g, pos, posr, cell_sorted, start,
-                       stage[warp], pp, q, acc, ncand, nre, act, pi, ki, pair_buf, pair_count, pair_cap, rlist,
-                       rcount, err);
-    if (act && F) store_force(F, g, pi, acc);
+    warp_chunk<RECORD, HALF>(cd, rows + (size_t)cd.z * maxrows, rowcnt[cd.z], 0, g, pos, posr, cell_sorted, start,
+                             stage[warp], pp, q, F, acc, ncand, nre, act, pi, ki, pair_buf, pair_count, pair_cap,
+                             rlist, rcount, err);
+    if (act && F) {
+      if (HALF)
+        add_force(F, g, pi, acc);
+      else
+        store_force(F, g, pi, acc);
+    }
   }
   double v[kPartials] = {acc.u, acc.wxx, acc.wyy, acc.wzz, acc.wxy, acc.wxz, acc.wyz,
                          (double)acc.npair, (double)ncand, (double)nre};
   block_reduce_store<kWarpThreads>(v, partials);
 }
 
-template <bool RECORD>
+template <bool RECORD, bool HALF>
 static int warp_resident_blocks(int sms) {
   static int per_sm = 0;
   if (!per_sm) {
-    cudaFuncSetAttribute(k_force_warp<RECORD>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_warp<RECORD>, kWarpThreads, 0) !=
+    cudaFuncSetAttribute(k_force_warp<RECORD, HALF>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_warp<RECORD, HALF>, kWarpThreads, 0) !=
             cudaSuccess ||
         per_sm < 1)
       per_sm = 1;
@@ -272,24 +359,29 @@ static int warp_resident_blocks(int sms) {
 
 bool warp_kernel_applies(const nemd_ctx *c) { return c->kfac <= 2; }
 
-cudaError_t launch_force_warp(nemd_ctx *c, float *F, int *nblocks) {
+// half: half neighbourhoods (F must have been zeroed; not with pair records).
+cudaError_t launch_force_warp(nemd_ctx *c, float *F, int *nblocks, bool half) {
   const Pot pp = make_pot(c);
   const bool rec = c->record_cap > 0;
-  int blocks = rec ? warp_resident_blocks<true>(c->sms) : warp_resident_blocks<false>(c->sms);
+  half = half && !rec;
+  int blocks = rec ? warp_resident_blocks<true, false>(c->sms)
+                   : (half ? warp_resident_blocks<false, true>(c->sms) : warp_resident_blocks<false, false>(c->sms));
   if (blocks > (int)(c->cap_partials - 1)) blocks = (int)(c->cap_partials - 1);
   *nblocks = blocks;
-#define NEMD_ARGS                                                                                                \
-  c->geo, c->pos4, c->posr, c->cell_sorted, c->start, c->rows, c->rowcnt, c->chunks, c->chunk_off + c->cap_cells, c->q_dev, pp, \
-      F, c->partials, c->pair_buf, c->pair_count, (long long)c->record_cap, c->recheck, c->nrecheck, &c->geo->error
+#define NEMD_ARGS                                                                                            \
+  c->geo, c->pos4, c->posr, c->cell_sorted, c->start, c->rows, c->rowcnt, c->chunks, c->chunk_off + c->cap_cells, \
+      c->q_dev, pp, F, c->partials, c->pair_buf, c->pair_count, (long long)c->record_cap, c->recheck, c->nrecheck, \
+      &c->geo->error
   if (rec)
-    k_force_warp<true><<<blocks, kWarpThreads, 0, c->stream>>>(NEMD_ARGS);
+    k_force_warp<true, false><<<blocks, kWarpThreads, 0, c->stream>>>(NEMD_ARGS);
+  else if (half)
+    k_force_warp<false, true><<<blocks, kWarpThreads, 0, c->stream>>>(NEMD_ARGS);
   else
-    k_force_warp<false><<<blocks, kWarpThreads, 0, c->stream>>>(NEMD_ARGS);
+    k_force_warp<false, false><<<blocks, kWarpThreads, 0, c->stream>>>(NEMD_ARGS);
 #undef NEMD_ARGS
   c->launches += 1;
   return cudaGetLastError();
 }
-
 
 // ---- batches: one persistent launch over every chunk of every system ----
 // Warps take chunks from a shared counter (chunks of different systems differ
@@ -319,9 +411,9 @@ __global__ void __launch_bounds__(kWarpThreads) k_b_force_warp(BatchView v) {
     bool act;
     float4 pi;
     int ki;
-    warp_chunk<false>(cd, v.rows + (size_t)cd.z * kBatchRowStride, v.rowcnt[cd.z], coff, g, v.pos4, v.posr,
-                      v.cell_sorted, v.start, stage[warp], pp, v.q, acc, ncand, nre, act, pi, ki, nullptr, nullptr, 0,
-                      v.recheck, v.nrecheck, &g->error);
+    warp_chunk<false, false>(cd, v.rows + (size_t)cd.z * kBatchRowStride, v.rowcnt[cd.z], coff, g, v.pos4, v.posr,
+                             v.cell_sorted, v.start, stage[warp], pp, v.q, v.F, acc, ncand, nre, act, pi, ki, nullptr,
+                             nullptr, 0, v.recheck, v.nrecheck, &g->error);
     if (act) {
       if (v.F) store_force(v.F, g, pi, acc);
       v.ppart[2 * (size_t)ki] = make_float4(acc.u, acc.wxx, acc.wyy, acc.wzz);

@@ -370,7 +370,7 @@ __device__ int stencil_class_warp(Geo *g, int cls, int cell_base, Row *out, int 
       r.cnt = 2 * K + 1;
       r.ky = (short)ky;
       r.kz = (short)kz;
-      r.pad1 = 0;
+      r.dir = dz > 0 || (dz == 0 && dy > 0) ? 1 : (dz == 0 && dy == 0 ? 0 : -1);
       out[e] = r;
     }
   } else {
@@ -416,7 +416,10 @@ __device__ int stencil_class_warp(Geo *g, int cls, int cell_base, Row *out, int 
       r.cnt = xhi - xlo + 1;
       r.ky = (short)ky;
       r.kz = (short)kz;
-      r.pad1 = 0;
+      {
+        const int dz = jzu - iz, dy = jyu - iy;
+        r.dir = dz > 0 || (dz == 0 && dy > 0) ? 1 : (dz == 0 && dy == 0 ? 0 : -1);
+      }
       out[e] = r;
     }
   }

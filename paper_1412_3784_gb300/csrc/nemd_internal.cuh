@@ -94,7 +94,12 @@ struct GridIn {
 // Geo::step); shift is split into an exact multiple of Geo::quantum (shx, shy,
 // shz) and a float32 residual (srx, sry, srz), and kept within half a cell
 // along x by the integer sxi.  The home cell's own row has shift 0 and sxi 0,
-// so the offset of the home cell itself is exactly 0.
+// so the offset of the home cell itself is exactly 0.  dir orders the rows for
+// half neighbourhoods: +1 when the row lies ahead of the home row (dz > 0, or
+// dz = 0 and dy > 0, in unwrapped cell offsets), 0 for the home row itself,
+// -1 behind; a pair met through a +1 row is met through a -1 row from its
+// partner's side, so a half neighbourhood visits +1 rows and the forward half
+// of the home row.
 struct __align__(16) Row {
   float shx, shy, shz;
   int cbase;   // l1 * (jy + l2 * jz)
@@ -103,7 +108,7 @@ struct __align__(16) Row {
   int cnt;
   short ky, kz;
   int sxi;
-  int pad1;
+  int dir;
 };
 static_assert(sizeof(Row) == 48, "Row is 48 bytes");
 
@@ -118,7 +123,7 @@ constexpr int kMlpParams = kMlpHidden * kMlpIn + kMlpHidden + kMlpHidden * kMlpH
 
 // Autotuner cache: per shape class, the summed mean time and the number of
 // measurements of every candidate configuration.
-constexpr int kTuneCandidates = 9;
+constexpr int kTuneCandidates = 11;
 constexpr int kMaxTuneClasses = 64;
 struct TuneEntry {
   int32_t key[2];
@@ -218,7 +223,7 @@ cudaError_t launch_forces(nemd_ctx *c, float *F_dev, double *UW_dev);
 bool chunk_kernel_applies(const nemd_ctx *c);
 bool warp_kernel_applies(const nemd_ctx *c);
 cudaError_t launch_chunk_build(nemd_ctx *c, int gs);
-cudaError_t launch_force_warp(nemd_ctx *c, float *F_dev, int *nblocks);
+cudaError_t launch_force_warp(nemd_ctx *c, float *F_dev, int *nblocks, bool half);
 // autotuner cache lookup (autotune.cu)
 void tune_apply(nemd_ctx *c, double rc);
 // learned selector inference for this step (mlp.cu)

@@ -32,7 +32,7 @@ def test_autotune_picks_fastest_and_keeps_results(tmp_path):
     ctx = make_ctx(w, nemd, torch)
     ctx.set_state(q, w.t)
     best, times = ctx.autotune(nemd.NEMD_AUTO_HEURISTIC, w.rc, reps=2)
-    assert len(times) == 9
+    assert len(times) == 11
     fastest = min(times, key=lambda x: x[1])[0]
     assert best == fastest          # first call: the class mean is this call's time
     F, st = evaluate(ctx, w, q, nemd.NEMD_AUTO_HEURISTIC)
@@ -65,7 +65,8 @@ def test_autotune_picks_fastest_and_keeps_results(tmp_path):
 def test_every_candidate_gives_the_same_pairs():
     w = W.config_planar(30, k=10)
     ref = oracle.evaluate(w, "do")
-    for kern, group, kfac in ((0, 16, 1), (2, 32, 1), (2, 32, 2), (1, 4, 2), (1, 8, 1), (1, 16, 2)):
+    for kern, group, kfac in ((0, 16, 1), (2, 32, 1), (2, 32, 2), (3, 32, 1), (3, 32, 2), (1, 4, 2), (1, 8, 1),
+                              (1, 16, 2)):
         g = run(w, nemd.NEMD_DO, kernel=(kern, group), kfac=kfac)
         assert g["stats"]["pairs"] == ref.npairs, (kern, group, kfac)
         assert force_err(g["F"], ref.F) <= 1e-5

@@ -33,7 +33,8 @@ def keys(p):
     return oracle.canonical_pair_keys(p)
 
 
-KERNELS = [(0, 16), (2, 32), (1, 16), (1, 4)]   # (kernel, group size): plain, warp, grouped
+KERNELS = [(0, 16), (2, 32), (3, 32), (1, 16), (1, 4)]   # (kernel, group): plain, warp, warp-half, grouped
+DETERMINISTIC = [(0, 16), (2, 32)]                   # kernels whose forces repeat bit for bit
 
 
 def check_against(w, variant, ref, *, pairs=True, precise=True, kfac=1, kernel=(0, 16)):
@@ -87,7 +88,7 @@ def test_config0_wca_equilibrium(variant, kernel):
 
 # ------------------------------------------------------ flows at strains ----
 
-@pytest.mark.parametrize("kernel", KERNELS[:2])
+@pytest.mark.parametrize("kernel", KERNELS[:3])
 @pytest.mark.parametrize("i", [0, 17, 40, 63])
 @pytest.mark.parametrize("variant", [DS, DO])
 def test_planar_flow_strains(i, variant, kernel):
@@ -105,7 +106,7 @@ def test_general_flow_incl_max_skew(t, variant, kernel):
     check_against(w, variant, ref, kernel=kernel)
 
 
-@pytest.mark.parametrize("kernel", KERNELS[:2])
+@pytest.mark.parametrize("kernel", KERNELS[:3])
 @pytest.mark.parametrize("variant", [DS, DO])
 def test_planar_config_full_size(variant, kernel):
     """The planar-flow configuration at its full size (N = 32000) at two strains."""
@@ -167,7 +168,7 @@ def test_ragged_counts_and_empty_cells(kernel):
 
 # ------------------------------------------------------------ properties ----
 
-@pytest.mark.parametrize("kernel", KERNELS[:2])
+@pytest.mark.parametrize("kernel", DETERMINISTIC)
 def test_deterministic_repeat(kernel):
     w = W.config_planar(23, k=10)
     a = run(w, DO, kernel=kernel)
@@ -179,7 +180,7 @@ def test_kernels_agree_bitwise_on_forces():
     """Same pair arithmetic and per-particle summation order in both kernels."""
     w = W.config_general(t=0.55, k=12)
     a = run(w, DO, kernel=(0, 16))
-    for kern in ((1, 16), (2, 32)):
+    for kern in ((1, 16), (2, 32), (3, 32)):
         b = run(w, DO, kernel=kern)
         assert a["stats"]["pairs"] == b["stats"]["pairs"]
         assert force_err(b["F"], a["F"]) <= 1e-6
