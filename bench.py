@@ -22,9 +22,12 @@ Printed as one JSON line (rank 0):
                CUDA graph, autotuned cell factor and tile; against a loop of
                per-system contexts with the plain kernel
   learned      the learned cell-list selector, trained on timings of the
-               N = 32000 planar, N = 256000 general and batched systems, driving
+               N = 32000 planar, N = 256000 general and 256 batched systems, driving
                the N = 2,097,152 general-flow system: regret against the
                exhaustive choice, pairs/s against the plain fixed variants
+  shear        Lees-Edwards shear remapped half way through the period, N = 2^20:
+               tuned against plain cell lists
+  equilibrium  the N = 2^20 system at rest (A = 0), 16 perturbed cubes per step
 
 --impl reference times the oracle (the reference arm of this project) on the
 same workload, one strain per step.
@@ -86,8 +89,8 @@ def parse():
     p.add_argument("--kernel", type=int, default=2, help="force kernel without autotuning (0 plain, 1 grouped, 2 warp)")
     p.add_argument("--group", type=int, default=16, help="lanes per group of the grouped kernel")
     p.add_argument("--kfac", type=int, default=1, help="cell-size factor without autotuning")
-    p.add_argument("--sections", default="main,batched,learned",
-                   help="comma list of main, batched, learned")
+    p.add_argument("--sections", default="main,batched,learned,shear,equilibrium",
+                   help="comma list of main, batched, learned, shear, equilibrium")
     p.add_argument("--batch-steps", type=int, default=10)
     p.add_argument("--learned-strains", type=int, default=64,
                    help="strains of the N = 2^21 system in the learned section (256 = one per period step)")
@@ -495,7 +498,7 @@ def section_learned(args, dev, torch, nemd, W):
     ctx.set_option(nemd.NEMD_OPT_KERNEL, 2)
     X, T = [], []
     t0 = time.perf_counter()
-    for ser, m in ((W.planar_series(k=20), 32), (W.general_series(k=40), 32)):
+    for ser, m in ((W.planar_series(k=20), 64), (W.general_series(k=40), 64)):
         ctx.set_flow(ser.A, ser.L0, ser.M, ser.period)
         ctx.set_potential(nemd.NEMD_LJ, 1.0, 1.0, 1)
         for i in range(m):
@@ -504,7 +507,7 @@ def section_learned(args, dev, torch, nemd, W):
             f, ms = ctx.time_options(ser.rc, reps=2)
             X.append(f)
             T.append(ms)
-    for w in W.batched_systems()[:64]:
+    for w in W.batched_systems():
         ctx.set_flow(w.A, w.L0, w.M, w.T)
         ctx.set_potential(nemd.NEMD_WCA if w.kind == W.POT_WCA else nemd.NEMD_LJ, 1.0, 1.0, 1)
         ctx.set_state(torch.from_numpy(w.q).to(dev), w.t)
@@ -585,6 +588,139 @@ def section_learned(args, dev, torch, nemd, W):
             "learned_over_best_plain": out["learned"] / max(out["plain_ds"], out["plain_do"])}
 
 
+def section_shear(args, world, dev, torch, nemd, W):
+    """Lees-Edwards shear (Sec. 2.2), remapped half way through the period, on
+    N = 1,048,576 LJ particles: 128 strains of one period, the tuned form
+    (autotuned kernel, per-strain cell list by neighbourhood volume) against the
+    plain fixed-variant cell lists."""
+    ser = W.shear_series(k=64)
+    S = 128
+    ts = [(i / S - 0.5) * ser.period for i in range(S)]
+    q_all = torch.empty((S, ser.n, 3), dtype=torch.float64, device=dev)
+    for i, t in enumerate(ts):
+        q_all[i].copy_(torch.from_numpy(ser.positions(t)))
+    F = torch.empty((ser.n, 3), dtype=torch.float32, device=dev)
+    ctx = nemd.Context(dev.index)
+    ctx.set_flow(ser.A, ser.L0, ser.M, ser.period)
+    ctx.set_potential(nemd.NEMD_LJ, 1.0, 1.0, 1)
+    ctx.set_option(nemd.NEMD_OPT_REMAP, 1)
+    for t in (-0.5 * ser.period, 0.0, 0.25 * ser.period):
+        ctx.set_state(torch.from_numpy(ser.positions(t)).to(dev), t)
+        best, _ = ctx.autotune(nemd.NEMD_AUTO_HEURISTIC, ser.rc, reps=2)
+
+    def form(kind):
+        ctx.set_option(nemd.NEMD_OPT_AUTOTUNED, 1 if kind == "tuned" else 0)
+        if kind != "tuned":
+            ctx.set_option(nemd.NEMD_OPT_KERNEL, 0)
+            ctx.set_option(nemd.NEMD_OPT_CELL_FACTOR, 1)
+        variant = {"tuned": nemd.NEMD_AUTO_HEURISTIC, "plain_ds": nemd.NEMD_DS, "plain_do": nemd.NEMD_DO}[kind]
+
+        def step():
+            for i in range(S):
+                ctx.set_state(q_all[i], ts[i])
+                ctx.build_cells(variant, ser.rc)
+                ctx.compute_forces(F)
+        return variant, step
+
+    out, cands = {}, {}
+    pairs = 0
+    for kind in ("plain_ds", "plain_do", "tuned"):
+        variant, step = form(kind)
+        c, vs, p = [], [], 0
+        for i in range(S):
+            ctx.set_state(q_all[i], ts[i])
+            ctx.build_cells(variant, ser.rc)
+            ctx.compute_forces(F)
+            ctx.sync()
+            st = ctx.stats()
+            c.append(st["candidates"])
+            vs.append(st["variant"])
+            p += st["pairs"]
+        cands[kind] = (c, vs)
+        pairs = p
+        if kind == "tuned":
+            ctx.set_option(nemd.NEMD_OPT_TIMING, 1)
+        ms = timed_loop(torch, dev, world, step, 2, 1) / 2
+        if kind == "tuned":
+            ctx.sync()
+            k_ms, k_n = ctx.kernel_time()
+            ctx.set_option(nemd.NEMD_OPT_TIMING, 0)
+        out[kind] = pairs / ms * 1e3
+    ops = 0.0
+    for i in range(S):
+        v = cands["tuned"][1][i]
+        ops += 0.5 * C_TEST * (cands["plain_do"] if v == 1 else cands["plain_ds"])[0][i]
+    ops += C_PAIR * pairs
+    props = torch.cuda.get_device_properties(dev)
+    peak = fp32_issue_peak(props.multi_processor_count, 2070.0)
+    frac = (ops / S) / ((k_ms / k_n) * 1e-3) / peak
+    ctx.close()
+    del q_all
+    return {"workload": f"Lees-Edwards shear u = y e_x, perturbed FCC N={ser.n}, rho=0.8442, LJ rc=2.5, "
+                        f"{S} strains of one period, remapped half way (tilt within half a spacing)",
+            "pairs_per_step": pairs, "pairs_per_s": out,
+            "tuned": f"autotuned: kernel {best['kernel']}, cell factor {best['cell_factor']}",
+            "tuned_over_best_plain": out["tuned"] / max(out["plain_ds"], out["plain_do"]),
+            "force_kernel_ms": k_ms / k_n, "roofline_frac": frac}
+
+
+def section_equilibrium(args, world, dev, torch, nemd, W):
+    """The N = 1,048,576 LJ system at rest (A = 0): 16 independently perturbed FCC
+    cubes per step (384 MB of positions, more than L2), tuned against plain."""
+    ws = W.equilibrium_set(k=64)
+    S = len(ws)
+    qs = [torch.from_numpy(w.q).to(dev) for w in ws]
+    F = torch.empty((ws[0].n, 3), dtype=torch.float32, device=dev)
+    ctx = nemd.Context(dev.index)
+    ctx.set_flow(ws[0].A, ws[0].L0, ws[0].M, ws[0].T)
+    ctx.set_potential(nemd.NEMD_LJ, 1.0, 1.0, 1)
+    ctx.set_state(qs[0], 0.0)
+    best, _ = ctx.autotune(nemd.NEMD_AUTO_HEURISTIC, ws[0].rc, reps=2)
+    out, cands, pairs = {}, {}, 0
+    for kind, variant in (("plain_ds", nemd.NEMD_DS), ("plain_do", nemd.NEMD_DO), ("tuned", nemd.NEMD_AUTO_HEURISTIC)):
+        ctx.set_option(nemd.NEMD_OPT_AUTOTUNED, 1 if kind == "tuned" else 0)
+        if kind != "tuned":
+            ctx.set_option(nemd.NEMD_OPT_KERNEL, 0)
+            ctx.set_option(nemd.NEMD_OPT_CELL_FACTOR, 1)
+        c, vs, p = [], [], 0
+        for i in range(S):
+            ctx.set_state(qs[i], 0.0)
+            ctx.build_cells(variant, ws[i].rc)
+            ctx.compute_forces(F)
+            ctx.sync()
+            st = ctx.stats()
+            c.append(st["candidates"])
+            vs.append(st["variant"])
+            p += st["pairs"]
+        cands[kind] = (c, vs)
+        pairs = p
+
+        def step():
+            for i in range(S):
+                ctx.set_state(qs[i], 0.0)
+                ctx.build_cells(variant, ws[i].rc)
+                ctx.compute_forces(F)
+        if kind == "tuned":
+            ctx.set_option(nemd.NEMD_OPT_TIMING, 1)
+        ms = timed_loop(torch, dev, world, step, 3, 1) / 3
+        if kind == "tuned":
+            ctx.sync()
+            k_ms, k_n = ctx.kernel_time()
+            ctx.set_option(nemd.NEMD_OPT_TIMING, 0)
+        out[kind] = pairs / ms * 1e3
+    ops = sum(0.5 * C_TEST * (cands["plain_do"] if cands["tuned"][1][i] == 1 else cands["plain_ds"])[0][i]
+              for i in range(S)) + C_PAIR * pairs
+    peak = fp32_issue_peak(torch.cuda.get_device_properties(dev).multi_processor_count, 2070.0)
+    eta = 2 * pairs / sum(cands["plain_ds"][0])
+    ctx.close()
+    return {"workload": f"A = 0, {S} independently perturbed FCC cubes of N={ws[0].n} per step, LJ rc=2.5",
+            "pairs_per_step": pairs, "pairs_per_s": out,
+            "tuned": f"autotuned: kernel {best['kernel']}, cell factor {best['cell_factor']}",
+            "tuned_over_best_plain": out["tuned"] / max(out["plain_ds"], out["plain_do"]),
+            "search_efficiency_ds": eta, "force_kernel_ms": k_ms / k_n,
+            "roofline_frac": (ops / S) / ((k_ms / k_n) * 1e-3) / peak}
+
+
 def main():
     args = parse()
     rank, world, local = dist_init(args)
@@ -606,6 +742,8 @@ def main():
     main_part = section_main(args, rank, world, dev, torch, nemd, W)
     batched = section_batched(args, world, dev, torch, nemd, W) if "batched" in sections else None
     learned = section_learned(args, dev, torch, nemd, W) if "learned" in sections else None
+    shear = section_shear(args, world, dev, torch, nemd, W) if "shear" in sections else None
+    equilibrium = section_equilibrium(args, world, dev, torch, nemd, W) if "equilibrium" in sections else None
     if rank == 0:
         line = {
             "metric": "interacting pairs/s per force eval", "value": main_part["value"], "unit": "pairs/s",
@@ -618,6 +756,8 @@ def main():
             line[key] = main_part[key]
         line["batched"] = batched
         line["learned"] = learned
+        line["shear"] = shear
+        line["equilibrium"] = equilibrium
         print(json.dumps(line), flush=True)
     barrier(world)
     if world > 1:

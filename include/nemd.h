@@ -92,8 +92,14 @@ typedef enum nemd_option {
     NEMD_OPT_TIMING = 6,        /* 1: record CUDA events around every force-kernel launch
                                    (read with nemd_get_kernel_time)                       */
     NEMD_OPT_GROUP = 7,         /* lanes per group of the grouped kernel: 4, 8, 16 or 32 */
-    NEMD_OPT_AUTOTUNED = 8      /* 1: nemd_build_cells applies the autotuner's choice for
+    NEMD_OPT_AUTOTUNED = 8,     /* 1: nemd_build_cells applies the autotuner's choice for
                                    the current shape class (when it has one)              */
+    NEMD_OPT_REMAP = 9          /* remap instant within a period: 0 (default) at its end,
+                                   tau = t - T floor(t/T) in [0, T); 1 half way,
+                                   tau = t - T floor(t/T + 1/2) in [-T/2, T/2) -- the
+                                   shear flow remapped at half a lattice spacing keeps
+                                   the box within 26.57 degrees of upright (Sec. 2.2).
+                                   Applies from the next nemd_set_state.                  */
 } nemd_option;
 
 /* Statistics of the last force evaluation (read with nemd_get_stats). */
@@ -312,7 +318,7 @@ typedef struct nemd_system {
     int32_t kind;        /* NEMD_LJ or NEMD_WCA                                    */
     int32_t shift;       /* energy shifted to 0 at rc (required for WCA)           */
     int32_t variant;     /* NEMD_DS, NEMD_DO or NEMD_AUTO_HEURISTIC (per step)     */
-    int32_t pad;
+    int32_t remap;       /* as NEMD_OPT_REMAP: 0 tau in [0, T), 1 in [-T/2, T/2)   */
 } nemd_system;
 
 typedef struct nemd_batch_stats {

@@ -27,7 +27,7 @@ def lib():
         L = ctypes.CDLL(path)
         L.orc_expm.argtypes = [_dp, ctypes.c_double, _dp]
         L.orc_expm.restype = None
-        L.orc_lattice.argtypes = [_dp, _dp, ctypes.c_double, ctypes.c_double, _dp]
+        L.orc_lattice.argtypes = [_dp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp]
         L.orc_lattice.restype = None
         L.orc_kr_residual.argtypes = [_dp, _dp, _i64p, ctypes.c_double]
         L.orc_kr_residual.restype = ctypes.c_double
@@ -79,12 +79,13 @@ def expm(A, tau):
     return E.reshape(3, 3)
 
 
-def lattice(A, L0, T, t):
-    """L(t) = exp(A (t mod T)) L0 with its inverse, volume, heights and QR."""
+def lattice(A, L0, T, t, centered=False):
+    """L(t) = exp(A tau) L0 with its inverse, volume, heights and QR; tau = t mod T
+    in [0, T), or in [-T/2, T/2) when centered (remap half way through a period)."""
     A, pA = _d(A)
     L0, pL = _d(L0)
     out = np.zeros(40)
-    lib().orc_lattice(pA, pL, float(T), float(t), out.ctypes.data_as(_dp))
+    lib().orc_lattice(pA, pL, float(T), float(t), 1 if centered else 0, out.ctypes.data_as(_dp))
     return {"L": out[0:9].reshape(3, 3).copy(), "Linv": out[9:18].reshape(3, 3).copy(),
             "V": float(out[18]), "h": out[19:22].copy(), "Q": out[22:31].reshape(3, 3).copy(),
             "R": out[31:40].reshape(3, 3).copy()}
@@ -246,7 +247,7 @@ def cells_do(L, s, qp, rc, kfac=1, eps=1.0, sigma=1.0, shift=1, want_pairs=True)
 
 def evaluate(w, method="ds", kfac=1, want_pairs=False):
     """Full oracle evaluation of a workload: lattice, wrap, then the chosen sum."""
-    lat = lattice(w.A, w.L0, w.T, w.t)
+    lat = lattice(w.A, w.L0, w.T, w.t, centered=bool(getattr(w, "remap", 0)))
     s, qp = wrap(lat["L"], lat["Linv"], w.q)
     if method == "brute":
         res = brute(lat["L"], s, qp, w.rc, w.eps, w.sigma, w.shift, want_pairs)

@@ -235,10 +235,14 @@ void orc_expm(const double *A, double tau, double *E)
 /* Lattice at time t: out = [L(9), Linv(9), V, h(3), Q(9), R(9)] = 40 doubles */
 /* ------------------------------------------------------------------------ */
 
-static double reduce_time(double T, double t)
+/* Time within the current remap period: tau in [0, T) (the remap happens at
+ * the end of each period), or, centred, tau in [-T/2, T/2) (the remap happens
+ * half way, as for the shear flow remapped at half a lattice spacing, Sec. 2.2). */
+static double reduce_time(double T, double t, int centered)
 {
-    if (T > 0.0) return t - T * floor(t / T);
-    return t;
+    if (!(T > 0.0)) return t;
+    if (centered) return t - T * floor(t / T + 0.5);
+    return t - T * floor(t / T);
 }
 
 static void cross3(const double *a, const double *b, double *c)
@@ -292,9 +296,9 @@ void orc_qr(const double *L, double *Q, double *R)
         for (int j = 0; j < 3; j++) Q[3 * a + j] = q[j][a];
 }
 
-void orc_lattice(const double *A, const double *L0, double T, double t, double *out)
+void orc_lattice(const double *A, const double *L0, double T, double t, int centered, double *out)
 {
-    double tau = reduce_time(T, t);
+    double tau = reduce_time(T, t, centered);
     double E[9];
     orc_expm(A, tau, E);
     double *L = out, *Linv = out + 9, *h = out + 19, *Q = out + 22, *R = out + 31;

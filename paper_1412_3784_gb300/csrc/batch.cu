@@ -198,6 +198,7 @@ int nemd_batch_add(nemd_batch *b, const nemd_system *sys, int64_t *index) {
     return set_err(b, NEMD_ERR_ARG, "batch_add: N = %lld outside 0 .. 2^21", (long long)sys->n);
   if (sys->variant != NEMD_DS && sys->variant != NEMD_DO && sys->variant != NEMD_AUTO_HEURISTIC)
     return set_err(b, NEMD_ERR_ARG, "batch_add: variant %d (DS, DO or AUTO_HEURISTIC)", sys->variant);
+  if (sys->remap != 0 && sys->remap != 1) return set_err(b, NEMD_ERR_ARG, "batch_add: remap %d", sys->remap);
   const double rc = sys->rc;
   if (!(rc > 0.0) || !isfinite(rc)) return set_err(b, NEMD_ERR_ARG, "batch_add: rc must be > 0");
   if (sys->kind == NEMD_WCA && fabs(rc - pow(2.0, 1.0 / 6.0) * sys->sigma) > 1e-12 * sys->sigma)
@@ -266,6 +267,7 @@ int nemd_batch_finalize(nemd_batch *b) {
       L.t = (k < K) ? y.T * (double)k / K : y.T * (1.0 - ldexp(1.0, -20));
       L.tau = 0.0;
       L.validate = 0;
+      L.centered = y.remap;
       GridIn &G = gin[(size_t)s * (K + 1) + k];
       G.rc = y.rc;
       G.kfac = nemd::kBatchMaxFactor;
@@ -334,6 +336,7 @@ int nemd_batch_finalize(nemd_batch *b) {
     lat[s].t = 0.0;
     lat[s].tau = 0.0;
     lat[s].validate = 0;
+    lat[s].centered = y.remap;
     gin[s].rc = y.rc;
     gin[s].variant = y.variant;
     gin[s].kfac = b->kfac;

@@ -423,6 +423,10 @@ int nemd_set_option(nemd_ctx *c, int key, int64_t value) {
       }
       return NEMD_OK;
     }
+    case NEMD_OPT_REMAP:
+      if (value != 0 && value != 1) return set_err(c, NEMD_ERR_ARG, "remap %lld (0 or 1)", (long long)value);
+      c->remap_centered = (int)value;
+      return NEMD_OK;
     case NEMD_OPT_KERNEL:
       if (value < 0 || value > 3) return set_err(c, NEMD_ERR_ARG, "kernel %lld", (long long)value);
       c->kernel = (int)value;

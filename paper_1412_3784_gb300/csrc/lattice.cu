@@ -1,7 +1,9 @@
 // lattice.cu -- lattice evolution and remap (Sec. 2.1, 2.2), cell grid (Sec. 4.1,
 // 4.2, 5.1, 5.2) and neighbour stencil (Sec. 4.1, 4.2) on the device, in FP64.
 //
-//   tau = t - T floor(t / T)                 remap L <- L M^-1 at every period (Eq. kr)
+//   tau = t - T floor(t / T)                 remap L <- L M^-1 at every period (Eq. kr);
+//   or centred, tau = t - T floor(t/T + 1/2), remapping half way through a period
+//   (Sec. 2.2: shear remapped at half a lattice spacing)
 //   L   = exp(tau A) L0                      (Sec. 2.1, dL/dt = A L)
 //   exp by Taylor series with scaling and squaring, products spread over lanes
 //   L^-1 by the adjugate, V = det L, heights h_i = 1 / |row_i(L^-1)|
@@ -64,7 +66,12 @@ __device__ __forceinline__ void lattice_body(Geo *g, const LatIn &in) {
     tau = tau_in;
   } else {
     const double T = in.T, t = in.t;
-    tau = (T > 0.0) ? t - T * floor(t / T) : t;
+    if (!(T > 0.0))
+      tau = t;
+    else if (in.centered)
+      tau = t - T * floor(t / T + 0.5);
+    else
+      tau = t - T * floor(t / T);
   }
   if (lane < 9) {
     g->A[lane] = in.A[lane];
@@ -452,6 +459,7 @@ cudaError_t launch_lattice(nemd_ctx *c, int validate, double tau) {
   in.t = c->t;
   in.tau = tau;
   in.validate = validate;
+  in.centered = c->remap_centered;
   k_lattice<<<1, 32, 0, c->stream>>>(c->geo, in);
   c->launches += 1;
   return cudaGetLastError();

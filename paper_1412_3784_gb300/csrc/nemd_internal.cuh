@@ -80,6 +80,7 @@ struct LatIn {
   double A[9], L0[9];
   double T, t, tau;
   int validate;
+  int centered;  // remap half way through the period: tau in [-T/2, T/2)
 };
 
 struct GridIn {
@@ -145,6 +146,7 @@ struct nemd_ctx {
   int pot_kind;
   double eps, sigma;
   int shift;
+  int remap_centered;  // NEMD_OPT_REMAP
   // state
   int64_t n;
   double t;

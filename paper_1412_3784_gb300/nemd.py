@@ -33,6 +33,7 @@ NEMD_OPT_PRECISE, NEMD_OPT_RECORD_PAIRS, NEMD_OPT_KERNEL, NEMD_OPT_CELL_FACTOR, 
 NEMD_OPT_TIMING = 6
 NEMD_OPT_GROUP = 7
 NEMD_OPT_AUTOTUNED = 8
+NEMD_OPT_REMAP = 9
 
 EXPORTED = ["nemd_create", "nemd_destroy", "nemd_set_flow", "nemd_set_potential", "nemd_set_state",
             "nemd_build_cells", "nemd_compute_forces", "nemd_sync", "nemd_last_error",
@@ -71,7 +72,7 @@ class nemd_system(ctypes.Structure):
     _fields_ = [("A", ctypes.c_double * 9), ("L0", ctypes.c_double * 9), ("M", ctypes.c_int64 * 9),
                 ("T", ctypes.c_double), ("eps", ctypes.c_double), ("sigma", ctypes.c_double),
                 ("rc", ctypes.c_double), ("n", ctypes.c_int64), ("kind", ctypes.c_int32),
-                ("shift", ctypes.c_int32), ("variant", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("shift", ctypes.c_int32), ("variant", ctypes.c_int32), ("remap", ctypes.c_int32)]
 
 
 class nemd_batch_stats(ctypes.Structure):
@@ -357,6 +358,7 @@ class Batch:
             y.kind = int(s.get("kind", NEMD_LJ))
             y.shift = int(s.get("shift", 1))
             y.variant = int(s.get("variant", NEMD_AUTO_HEURISTIC))
+            y.remap = int(s.get("remap", 0))
             self._check(nemd_batch_add(self.h, ctypes.byref(y), None))
         self._check(nemd_batch_finalize(self.h))
         ns = ctypes.c_int64()

@@ -31,6 +31,7 @@ import numpy as np
 M_PLANAR = np.array([[2, 1, 0], [1, 1, 0], [0, 0, 1]], dtype=np.int64)
 M_GENERAL = np.array([[3, 2, 1], [2, 2, 1], [1, 1, 1]], dtype=np.int64)
 M_IDENTITY = np.eye(3, dtype=np.int64)
+M_SHEAR = np.array([[1, 1, 0], [0, 1, 0], [0, 0, 1]], dtype=np.int64)
 
 RHO_DEFAULT = 0.8442
 DISPLACEMENT_STD = 0.05
@@ -57,6 +58,7 @@ class Workload:
     eps: float = 1.0
     sigma: float = 1.0
     shift: int = 1         # energy shifted to zero at rc
+    remap: int = 0         # 0: tau = t mod T in [0, T); 1: centred, tau in [-T/2, T/2)
 
     @property
     def n(self) -> int:
@@ -200,6 +202,63 @@ def config_general(i: int = 0, nstrain: int = 128, k: int = 40, seed: int = 2,
 
 
 NEAR_REMAP_T = 1.0 - 2.0 ** -20
+
+
+class ShearSeries:
+    """Lees-Edwards shear (Sec. 2.2) of a cubic perturbed-FCC box of side a: the
+    flow u = rate y e_x, A = rate e_x e_y^T, one period T = 1 / rate tilts the box
+    by one lattice spacing (exp(T A) L0 = L0 M with M = [[1,1,0],[0,1,0],[0,0,1]]),
+    and the remap is taken half way (tau in [-T/2, T/2)), so the tilt never
+    exceeds half a spacing.  Positions at time t are the affine image
+    (I + tau A) L0 s + delta of the seeded sites.
+    """
+
+    def __init__(self, k, seed, *, rate=1.0, rho=RHO_DEFAULT, kind=POT_LJ, rc=None, name=None):
+        rng = np.random.default_rng(seed)
+        self.s, side, self.delta = perturbed_fcc(k, rho, rng)
+        self.A = np.zeros((3, 3))
+        self.A[0, 1] = rate
+        self.period = 1.0 / rate
+        self.L0 = side * np.eye(3)
+        self.M = M_SHEAR.copy()
+        self.order = rng.permutation(self.s.shape[0])
+        self.kind = kind
+        self.rc = (WCA_RC if kind == POT_WCA else LJ_RC) if rc is None else rc
+        self.name = name or f"shear_N{self.s.shape[0]}"
+        self._sL = self.s @ self.L0.T
+
+    @property
+    def n(self):
+        return int(self.s.shape[0])
+
+    def positions(self, t):
+        tau = t - self.period * math.floor(t / self.period + 0.5)
+        F = np.eye(3)
+        F[0, 1] = tau * self.A[0, 1]
+        q = self._sL @ F.T + self.delta
+        return np.ascontiguousarray(q[self.order])
+
+    def workload(self, t, name=None):
+        return Workload(name=name or f"{self.name}_t{t:.6g}", A=self.A, L0=self.L0, M=self.M, T=self.period,
+                        t=t, q=self.positions(t), kind=self.kind, rc=self.rc, remap=1)
+
+
+def equilibrium_set(k: int = 64, nconf: int = 16, seed: int = 7) -> list:
+    """nconf independently perturbed FCC cubes of N = 4k^3 LJ particles at rest (A = 0)."""
+    out = []
+    for c in range(nconf):
+        rng = np.random.default_rng(seed + 1000 * c)
+        s, side, delta = perturbed_fcc(k, RHO_DEFAULT, rng)
+        L0 = side * np.eye(3)
+        q = (s @ L0.T + delta)[rng.permutation(s.shape[0])]
+        out.append(Workload(name=f"eq_N{s.shape[0]}_c{c}", A=np.zeros((3, 3)), L0=L0, M=M_IDENTITY.copy(), T=1.0,
+                            t=0.0, q=np.ascontiguousarray(q), kind=POT_LJ, rc=LJ_RC))
+    return out
+
+
+def shear_series(k: int = 20, seed: int = 6, rate: float = 1.0) -> ShearSeries:
+    """Lees-Edwards shear on N = 4k^3 LJ particles (32000 at k = 20, 1,048,576 at k = 64)."""
+    return ShearSeries(k, seed, rate=rate)
 
 
 def batched_systems(nsys: int = 256, seed: int = 3, nmin: int = 1000, nmax: int = 20000):

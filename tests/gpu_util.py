@@ -12,6 +12,7 @@ def make_ctx(w, nemd, torch):
     ctx = nemd.Context(0)
     ctx.set_flow(w.A, w.L0, w.M, w.T)
     ctx.set_potential(kind_of(w), w.eps, w.sigma, w.shift)
+    ctx.set_option(nemd.NEMD_OPT_REMAP, getattr(w, "remap", 0))
     return ctx
 
 

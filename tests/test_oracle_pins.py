@@ -82,6 +82,43 @@ def test_lees_edwards_closed_form_and_angle():
     assert oracle.kr_residual(A, L0, Msh, 1.0 / eps) < 1e-14
 
 
+def test_centred_remap_keeps_shear_within_half_a_spacing():
+    """Remapping half way through the period (Sec. 2.2): the tilt of the shear
+    box stays in [-1/2, 1/2) of a spacing, its angle within 26.57 deg of
+    upright, and the lattice is the uncentred one in another basis (L M^-1)."""
+    ser = W.shear_series(k=4, rate=0.8)
+    T = ser.period
+    g = GOLDEN["lees_edwards_max_angle_deg"]
+    worst = 0.0
+    for t in np.linspace(-1.3 * T, 2.7 * T, 97):
+        Lc = oracle.lattice(ser.A, ser.L0, T, t, centered=True)["L"]
+        tilt = Lc[0, 1] / Lc[1, 1]
+        assert -0.5 - 1e-12 <= tilt < 0.5 + 1e-12
+        v1, v2 = Lc[:, 0], Lc[:, 1]
+        worst = max(worst, 90.0 - math.degrees(math.acos(abs(v1 @ v2) / np.linalg.norm(v1) / np.linalg.norm(v2))))
+        Lu = oracle.lattice(ser.A, ser.L0, T, t)["L"]
+        # same lattice: Lu = Lc M^k for an integer power k of the remap matrix
+        Mk = np.linalg.solve(Lc, Lu)
+        assert np.abs(Mk - np.rint(Mk)).max() < 1e-9 and abs(np.linalg.det(np.rint(Mk)) - 1) < 1e-9
+    assert round(worst, g["digits"]) <= g["value"] + 10 ** -g["digits"]
+    # just before and at half a period: the tilt jumps from +1/2 to -1/2
+    a = oracle.lattice(ser.A, ser.L0, T, 0.5 * T * (1 - 1e-12), centered=True)["L"]
+    b = oracle.lattice(ser.A, ser.L0, T, 0.5 * T, centered=True)["L"]
+    assert abs(a[0, 1] / a[1, 1] - 0.5) < 1e-9 and abs(b[0, 1] / b[1, 1] + 0.5) < 1e-12
+
+
+def test_shear_cell_lists_equal_brute_force():
+    """Pair sets of both cell lists equal brute force under centred shear, at
+    strains across the period including the remap instant."""
+    ser = W.shear_series(k=4, seed=7)
+    for t in (0.0, 0.17, 0.4999, 0.5, 0.83):
+        w = ser.workload(t * ser.period)
+        ref = oracle.evaluate(w, "brute", want_pairs=True)
+        for method in ("ds", "do"):
+            r = oracle.evaluate(w, method, want_pairs=True)
+            assert np.array_equal(oracle.canonical_pair_keys(r.pairs), oracle.canonical_pair_keys(ref.pairs))
+
+
 # --------------------------------------------------------------------------
 # Box geometry (Sec. 4.1 heights, Sec. 4.2 QR)
 # --------------------------------------------------------------------------
