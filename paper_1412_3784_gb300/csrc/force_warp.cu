@@ -25,26 +25,49 @@
 // results are deterministic.
 #include <math.h>
 
+#include <type_traits>
+
 #include "batch_internal.cuh"
 
 namespace nemd {
 
-constexpr int kWarpThreads = 128;  // 4 warps per block
+// Shape of the kernel (compile-time): threads per block, staged particles per
+// warp, queue entries per lane, resident blocks the register allocation aims
+// at.  Measured on GB300 (N = 2^20 general flow): 224 staged particles and five
+// blocks of four warps per SM (96 registers, 43 KB of shared memory per block)
+// beat 256 particles at four blocks by 16 %; more staging at fewer resident
+// warps and less staging at more are both slower.
+#ifndef NEMD_WARP_THREADS
+#define NEMD_WARP_THREADS 128
+#endif
+#ifndef NEMD_WARP_STAGE
+#define NEMD_WARP_STAGE 224
+#endif
+#ifndef NEMD_WARP_QUEUE
+#define NEMD_WARP_QUEUE 64
+#endif
+#ifndef NEMD_WARP_MINBLOCKS
+#define NEMD_WARP_MINBLOCKS 5
+#endif
+constexpr int kWarpThreads = NEMD_WARP_THREADS;
 constexpr int kRowsStaged = 32;    // rows per class the kernel stages (cell factor <= 2)
-constexpr int kWarpQueue = 64;     // queue entries per lane
+constexpr int kWarpQueue = NEMD_WARP_QUEUE;  // queue entries per lane
 constexpr int kTestBlock = 32;     // candidates tested between two queue checks
 constexpr int kMetaBias = 1 << 12;  // R_j.w = row | (unwrapped x-cell + kMetaBias) << 5
+static_assert(kWarpQueue >= 2 * kTestBlock, "a queue check must leave room for a test block");
 
 // Shared memory of one warp.  HALF (half neighbourhoods) also accumulates the
 // force on every staged partner (Fj), and stages fewer particles so that four
-// blocks still fit an SM.
+// blocks still fit an SM.  A queue entry is a slot index: one byte for up to
+// 256 slots, two beyond.
 template <bool HALF>
 struct WarpStageT {
-  static constexpr int kSlots = HALF ? 192 : 256;  // a queue entry (slot) is one byte
+  static constexpr int kSlots = HALF ? 192 : NEMD_WARP_STAGE;
+  using Entry = typename std::conditional<(kSlots > 256), unsigned short, unsigned char>::type;
   float4 X[kSlots];  // .w: sorted index of j (bits)
   float4 R[kSlots];  // .w: row and unwrapped x-cell of j (bits)
   float Fj[HALF ? 3 : 1][HALF ? kSlots : 1];
-  unsigned char q[kWarpQueue][32];
+  Entry q[kWarpQueue][32];
   float4 rows[kRowsStaged][3];
 };
 using WarpStage = WarpStageT<false>;
@@ -256,7 +279,7 @@ __device__ __forceinline__ void warp_chunk(const int4 cd, const Row *__restrict_
   {                                                                           \
     const float ddx = (P).x - Xi.x, ddy = (P).y - Xi.y, ddz = (P).z - Xi.z;   \
     const float r2 = fmaf(ddz, ddz, fmaf(ddy, ddy, ddx * ddx));               \
-    S.q[qn][lane] = (unsigned char)(K);                                       \
+    S.q[qn][lane] = (typename WarpStageT<HALF>::Entry)(K);                    \
     qn += (r2 < hil) ? 1 : 0;                                                 \
   }
           int k = k0;
@@ -306,7 +329,7 @@ __device__ __forceinline__ void add_force(float *F, const Geo *g, const float4 &
 }
 
 template <bool RECORD, bool HALF>
-__global__ void __launch_bounds__(kWarpThreads) k_force_warp(
+__global__ void __launch_bounds__(kWarpThreads, NEMD_WARP_MINBLOCKS) k_force_warp(
     const Geo *__restrict__ g, const float4 *__restrict__ pos, const float4 *__restrict__ posr,
     const int *__restrict__ cell_sorted, const int *__restrict__ start, const Row *__restrict__ rows,
     const int *__restrict__ rowcnt, const int4 *__restrict__ chunks, const int *__restrict__ nchunks_p,
@@ -389,7 +412,7 @@ cudaError_t launch_force_warp(nemd_ctx *c, float *F, int *nblocks, bool half) {
 // own pair sums (float32, per sorted particle); the per-system reduction adds
 // those in float64 in a fixed order, so no result depends on which warp took
 // which chunk.
-__global__ void __launch_bounds__(kWarpThreads) k_b_force_warp(BatchView v) {
+__global__ void __launch_bounds__(kWarpThreads, NEMD_WARP_MINBLOCKS) k_b_force_warp(BatchView v) {
   constexpr int kWarps = kWarpThreads / 32;
   constexpr unsigned FULL = 0xffffffffu;
   __shared__ WarpStage stage[kWarps];
