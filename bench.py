@@ -60,9 +60,9 @@ C_PAIR = 24    # FP32 instructions per interacting pair (force, energy, virial, 
 # DRAM bytes (read + write) of one k_force_warp launch on the N = 2^20 system,
 # from the ncu capture summarised in profiles/k_force_warp_general_n1m.md; valid
 # only while the kernel's sources are the ones captured (sha1 prefixes).
-WARP_TRAFFIC = {"bytes": 39.403008e6 + 0.265984e6,
-                "sha1": {"paper_1412_3784_gb300/csrc/force_warp.cu": "65169c16eaef",
-                         "paper_1412_3784_gb300/csrc/force_common.cuh": "137892eaafbd"}}
+WARP_TRAFFIC = {"bytes": 39.440128e6 + 0.731648e6,
+                "sha1": {"paper_1412_3784_gb300/csrc/force_warp.cu": "1ab03e6666f2",
+                         "paper_1412_3784_gb300/csrc/force_common.cuh": "236e2e7e2cf5"}}
 
 
 def warp_traffic():
