@@ -94,6 +94,14 @@ typedef enum nemd_option {
     NEMD_OPT_GROUP = 7,         /* lanes per group of the grouped kernel: 4, 8, 16 or 32 */
     NEMD_OPT_AUTOTUNED = 8,     /* 1: nemd_build_cells applies the autotuner's choice for
                                    the current shape class (when it has one)              */
+    NEMD_OPT_ASYNC_HOST = 10,   /* 1: host inputs and outputs do not synchronise.  A host
+                                   q is copied on the context's copy stream into one of
+                                   two device buffers (so the copy of the next state
+                                   overlaps the current evaluation) and must stay valid
+                                   and unchanged until the next nemd_sync; host F, U, W
+                                   are written by that copy stream and are valid after
+                                   the next nemd_sync.  0 (default): a call that writes
+                                   host outputs synchronises before it returns.          */
     NEMD_OPT_REMAP = 9          /* remap instant within a period: 0 (default) at its end,
                                    tau = t - T floor(t/T) in [0, T); 1 half way,
                                    tau = t - T floor(t/T + 1/2) in [-T/2, T/2) -- the

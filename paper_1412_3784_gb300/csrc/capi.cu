@@ -109,6 +109,33 @@ int ensure_cells(nemd_ctx *c, int64_t cells, int kfac) {
   return NEMD_OK;
 }
 
+// Stream, events and double buffers of the asynchronous host path.
+int ensure_async(nemd_ctx *c) {
+  if (!c->copy_stream) {
+    CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&c->copy_back, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; k++) {
+      CK(cudaEventCreateWithFlags(&c->ev_q[k], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&c->ev_done[k], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&c->ev_out[k], cudaEventDisableTiming));
+      c->done_valid[k] = c->out_valid[k] = false;
+    }
+  }
+  if (c->acap < c->cap_n || !c->aq[0]) {
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaStreamSynchronize(c->copy_stream));
+    CK(cudaStreamSynchronize(c->copy_back));
+    for (int k = 0; k < 2; k++) {
+      int r;
+      if ((r = grow(c, &c->aq[k], 3 * c->cap_n, "async q"))) return r;
+      if ((r = grow(c, &c->af[k], 3 * c->cap_n, "async F"))) return r;
+      if ((r = grow(c, &c->auw[k], 10, "async UW"))) return r;
+    }
+    c->acap = c->cap_n;
+  }
+  return NEMD_OK;
+}
+
 int take_device_error(nemd_ctx *c) {
   int bits = *c->h_error;
   *c->h_error = 0;
@@ -210,6 +237,20 @@ int nemd_destroy(nemd_ctx *c) {
                   c->chunk_cnt, c->chunk_off, c->chunk_tiles};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  if (c->copy_stream) {
+    cudaStreamSynchronize(c->copy_stream);
+    cudaStreamSynchronize(c->copy_back);
+    for (int k = 0; k < 2; k++) {
+      cudaEventDestroy(c->ev_q[k]);
+      cudaEventDestroy(c->ev_done[k]);
+      cudaEventDestroy(c->ev_out[k]);
+      if (c->aq[k]) cudaFree(c->aq[k]);
+      if (c->af[k]) cudaFree(c->af[k]);
+      if (c->auw[k]) cudaFree(c->auw[k]);
+    }
+    cudaStreamDestroy(c->copy_stream);
+    cudaStreamDestroy(c->copy_back);
+  }
   if (c->h_error) cudaFreeHost(c->h_error);
   if (c->ev) {
     for (int k = 0; k < 2 * c->ev_cap; k++)
@@ -298,9 +339,21 @@ int nemd_set_state(nemd_ctx *c, const double *q, int64_t n, double t) {
   if (r) return r;
   c->n = n;
   c->t = t;
+  if (c->async_host) {
+    if ((r = ensure_async(c))) return r;
+    c->aslot ^= 1;
+  }
   if (n > 0) {
     if (is_device_ptr(q)) {
       c->q_dev = q;
+    } else if (c->async_host) {
+      // copy on the copy stream once the evaluation that last read this buffer is done
+      const int k = c->aslot;
+      if (c->done_valid[k]) CK(cudaStreamWaitEvent(c->copy_stream, c->ev_done[k], 0));
+      CK(cudaMemcpyAsync(c->aq[k], q, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, c->copy_stream));
+      CK(cudaEventRecord(c->ev_q[k], c->copy_stream));
+      CK(cudaStreamWaitEvent(c->stream, c->ev_q[k], 0));
+      c->q_dev = c->aq[k];
     } else {
       if (!c->q_copy) {
         if ((r = grow(c, &c->q_copy, 3 * c->cap_n, "q_copy"))) return r;
@@ -355,10 +408,35 @@ int nemd_build_cells(nemd_ctx *c, int variant, double rc) {
   return NEMD_OK;
 }
 
+// Asynchronous host outputs: the evaluation writes the current buffer pair,
+// which the copy stream then moves to the host; nothing waits on the host.
+static int compute_forces_async(nemd_ctx *c, float *F, double *U, double *W) {
+  const int k = c->aslot;
+  const bool fd = F && is_device_ptr(F), ud = U && is_device_ptr(U), wd = W && is_device_ptr(W);
+  // the buffers of this pair are free once their previous copies to the host are done
+  if (c->out_valid[k]) CK(cudaStreamWaitEvent(c->stream, c->ev_out[k], 0));
+  float *Fd = (F && c->n > 0) ? (fd ? F : c->af[k]) : nullptr;
+  cudaError_t e = nemd::launch_forces(c, Fd, c->auw[k]);
+  if (e != cudaSuccess) return cuda_err(c, e, "compute_forces");
+  if (ud) CK(cudaMemcpyAsync(U, c->auw[k], sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  if (wd) CK(cudaMemcpyAsync(W, c->auw[k] + 1, 9 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaEventRecord(c->ev_done[k], c->stream));
+  c->done_valid[k] = true;
+  CK(cudaStreamWaitEvent(c->copy_back, c->ev_done[k], 0));
+  if (F && c->n > 0 && !fd)
+    CK(cudaMemcpyAsync(F, c->af[k], sizeof(float) * 3 * (size_t)c->n, cudaMemcpyDeviceToHost, c->copy_back));
+  if (U && !ud) CK(cudaMemcpyAsync(U, c->auw[k], sizeof(double), cudaMemcpyDeviceToHost, c->copy_back));
+  if (W && !wd) CK(cudaMemcpyAsync(W, c->auw[k] + 1, 9 * sizeof(double), cudaMemcpyDeviceToHost, c->copy_back));
+  CK(cudaEventRecord(c->ev_out[k], c->copy_back));
+  c->out_valid[k] = true;
+  return NEMD_OK;
+}
+
 int nemd_compute_forces(nemd_ctx *c, float *F, double *U, double *W) {
   if (!c) return NEMD_ERR_ARG;
   if (!c->have_cells) return set_err(c, NEMD_ERR_ORDER, "compute_forces before build_cells");
   CK(cudaSetDevice(c->device));
+  if (c->async_host) return compute_forces_async(c, F, U, W);
   float *Fd = nullptr;
   bool host_out = false;
   if (F && c->n > 0) {
@@ -400,6 +478,10 @@ int nemd_sync(nemd_ctx *c) {
   c->launches += 1;
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->stream));
+  if (c->copy_stream) {
+    CK(cudaStreamSynchronize(c->copy_stream));
+    CK(cudaStreamSynchronize(c->copy_back));
+  }
   return take_device_error(c);
 }
 
@@ -423,6 +505,15 @@ int nemd_set_option(nemd_ctx *c, int key, int64_t value) {
       }
       return NEMD_OK;
     }
+    case NEMD_OPT_ASYNC_HOST:
+      CK(cudaSetDevice(c->device));
+      CK(cudaStreamSynchronize(c->stream));
+      if (c->copy_stream) {
+        CK(cudaStreamSynchronize(c->copy_stream));
+        CK(cudaStreamSynchronize(c->copy_back));
+      }
+      c->async_host = value ? 1 : 0;
+      return NEMD_OK;
     case NEMD_OPT_REMAP:
       if (value != 0 && value != 1) return set_err(c, NEMD_ERR_ARG, "remap %lld (0 or 1)", (long long)value);
       c->remap_centered = (int)value;

@@ -210,6 +210,19 @@ struct nemd_ctx {
   nemd::TuneEntry tune[nemd::kMaxTuneClasses];
   char msg[512];
   double last_stats_band;
+  // asynchronous host input/output (NEMD_OPT_ASYNC_HOST): double-buffered device
+  // copies on a copy stream, ordered against the context's stream by events
+  int async_host;
+  int aslot;                  // buffer pair of the current evaluation
+  int64_t acap;               // particles the async buffers hold
+  cudaStream_t copy_stream;   // host -> device
+  cudaStream_t copy_back;     // device -> host (a separate queue: an output copy waits for
+                              // its evaluation, the next input copy must not wait behind it)
+  cudaEvent_t ev_q[2], ev_done[2], ev_out[2];
+  bool done_valid[2], out_valid[2];
+  double *aq[2];              // positions copied from the host
+  float *af[2];               // forces copied to the host
+  double *auw[2];             // U, W copied to the host
 };
 
 namespace nemd {

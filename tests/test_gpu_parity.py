@@ -237,3 +237,29 @@ def test_do_stencil_size_matches_oracle():
         d = run(w, DS)
         c = oracle.ds_counts(lat["L"], w.rc)
         assert d["stats"]["stencil_cells"] == 27 * int(np.prod(c))
+
+
+def test_async_host_io_matches_sync():
+    """NEMD_OPT_ASYNC_HOST: host positions in, host F, U, W out over several
+    states without synchronising, then one nemd_sync -- bitwise the results of
+    the synchronising path."""
+    from paper_1412_3784_gb300 import nemd
+    from gpu_util import make_ctx
+    states = [W.config_planar(i) for i in (3, 20, 41, 58)]
+    ref = [run(w, DO, kernel=(2, 32)) for w in states]
+    ctx = make_ctx(states[0], nemd, torch)
+    ctx.set_option(nemd.NEMD_OPT_KERNEL, 2)
+    ctx.set_option(nemd.NEMD_OPT_ASYNC_HOST, 1)
+    qs = [torch.from_numpy(w.q).pin_memory() for w in states]
+    Fs = [torch.empty((w.n, 3), dtype=torch.float32).pin_memory() for w in states]
+    Us = [np.zeros(1) for _ in states]
+    Ws = [np.zeros(9) for _ in states]
+    for w, q, F, U, Wv in zip(states, qs, Fs, Us, Ws):
+        ctx.set_state(q, w.t)
+        ctx.build_cells(DO, w.rc)
+        ctx.compute_forces(F, U, Wv)
+    ctx.sync()
+    for r, F, U, Wv in zip(ref, Fs, Us, Ws):
+        assert np.array_equal(F.numpy().astype(np.float64), r["F"])
+        assert U[0] == r["U"] and np.array_equal(Wv.reshape(3, 3), r["W"])
+    ctx.close()
