@@ -408,7 +408,20 @@ def section_main(args, rank, world, dev, torch, nemd, W):
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
     ctx.set_option(nemd.NEMD_OPT_ASYNC_HOST, 0)
     e2e_pairs = sum_over_ranks(float(sum(per["tuned"]["pairs"][:Se])), world, dev)
-    e2e = {"value": e2e_pairs / e2e_s, "unit": "pairs/s",
+    # the box's pinned host <-> device copy rate, measured beside the e2e loop
+    probe_h = torch.empty(6 << 20, dtype=torch.float32).pin_memory()
+    probe_d = torch.empty(6 << 20, dtype=torch.float32, device=dev)
+    rates = {}
+    for name, dst, src in (("h2d_gbs", probe_d, probe_h), ("d2h_gbs", probe_h, probe_d)):
+        for _ in range(3):
+            dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        for _ in range(10):
+            dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        rates[name] = 10 * (24 << 20) / (time.perf_counter() - t1) / 1e9
+    e2e = {"value": e2e_pairs / e2e_s, "unit": "pairs/s", "copy_rates": rates,
            "h2d_bytes_per_step": int(S * n * 3 * 8), "d2h_bytes_per_step": int(S * (n * 3 * 4 + 80)),
            "strains_timed": Se,
            "mode": "host positions in and host F, U, W out every strain through the C ABI with "
@@ -512,7 +525,7 @@ def section_learned(args, dev, torch, nemd, W):
         for i in range(m):
             t = (i + 0.5) / m * ser.period
             ctx.set_state(torch.from_numpy(ser.positions(t)).to(dev), t)
-            f, ms = ctx.time_options(ser.rc, reps=2)
+            f, ms = ctx.time_options(ser.rc, reps=3)
             X.append(f)
             T.append(ms)
     for w in W.batched_systems():
@@ -520,7 +533,7 @@ def section_learned(args, dev, torch, nemd, W):
         ctx.set_potential(nemd.NEMD_WCA if w.kind == W.POT_WCA else nemd.NEMD_LJ, 1.0, 1.0, 1)
         ctx.set_state(torch.from_numpy(w.q).to(dev), w.t)
         try:
-            f, ms = ctx.time_options(w.rc, reps=2)
+            f, ms = ctx.time_options(w.rc, reps=3)
         except nemd.NemdError:
             continue                  # an option whose box is too small for the cut-off
         X.append(f)
@@ -543,7 +556,7 @@ def section_learned(args, dev, torch, nemd, W):
     table, feats, rule = [], [], []
     for i in range(S4):
         ctx.set_state(q_all[i], ts[i])
-        f, ms = ctx.time_options(ser.rc, reps=2)
+        f, ms = ctx.time_options(ser.rc, reps=3)
         table.append(ms)
         feats.append(f)
         ctx.set_option(nemd.NEMD_OPT_CELL_FACTOR, 1)
