@@ -26,7 +26,10 @@ __device__ __forceinline__ void wrap_body(Geo *g, const double *__restrict__ q, 
                                           float4 *__restrict__ relc, float4 *__restrict__ relr,
                                           int *__restrict__ rank, int *__restrict__ count) {
   double x = q[3 * (size_t)i], y = q[3 * (size_t)i + 1], z = q[3 * (size_t)i + 2];
-  if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
+  // NaN or infinity: every exponent bit set (integer test, no float64 work)
+  const unsigned long long ex = 0x7ff0000000000000ull;
+  if ((__double_as_longlong(x) & ex) == ex || (__double_as_longlong(y) & ex) == ex ||
+      (__double_as_longlong(z) & ex) == ex) {
     atomicOr(&g->error, ERRB_NONFINITE);
     x = y = z = 0.0;
   }
@@ -60,7 +63,7 @@ __device__ __forceinline__ void wrap_body(Geo *g, const double *__restrict__ q, 
     }
   }
   // split into an exact multiple of the quantum and a float32 residual
-  const double qu = g->quantum, qinv = 1.0 / qu;
+  const double qu = g->quantum, qinv = g->quantum_inv;
   float rq[3], rr[3];
   for (int a = 0; a < 3; a++) {
     double h = rint(rel[a] * qinv) * qu;

@@ -39,8 +39,7 @@ __device__ __forceinline__ void mm3(const double *a, const double *b, double *c,
 
 // Row shift split into an exact multiple of the quantum q (a power of two, so
 // scaling by 1/q is exact) and a float32 residual.
-__device__ __forceinline__ void set_shift(Row &r, double ox, double oy, double oz, double q) {
-  const double qi = 1.0 / q;
+__device__ __forceinline__ void set_shift(Row &r, double ox, double oy, double oz, double q, double qi) {
   double qx = rint(ox * qi) * q, qy = rint(oy * qi) * q, qz = rint(oz * qi) * q;
   r.shx = (float)qx;
   r.shy = (float)qy;
@@ -303,6 +302,7 @@ __device__ void grid_body(Geo *g, const GridIn &in) {
   frexp(M, &e2);             // M < 2^e2
   const double q = ldexp(1.0, e2 - 23);
   g->quantum = q;
+  g->quantum_inv = ldexp(1.0, 23 - e2);
   // frame vector between consecutive x-cells: G e_x (dynamic size), (w1, 0, 0) (dynamic offset)
   for (int a = 0; a < 3; a++) {
     double sv = Gd[3 * a];
@@ -370,7 +370,7 @@ __device__ int stencil_class_warp(Geo *g, int cls, int cell_base, Row *out, int 
       const int jy = jyu - ky * l2, jz = jzu - kz * l3;
       const double c1 = dy, c2 = dz;
       Row r;
-      set_shift(r, g->G[1] * c1 + g->G[2] * c2, g->G[4] * c1 + g->G[5] * c2, g->G[7] * c1 + g->G[8] * c2, q);
+      set_shift(r, g->G[1] * c1 + g->G[2] * c2, g->G[4] * c1 + g->G[5] * c2, g->G[7] * c1 + g->G[8] * c2, q, g->quantum_inv);
       r.cbase = cell_base + l1 * (jy + l2 * jz);
       r.sxi = 0;
       r.dxlo = -K;
@@ -416,7 +416,7 @@ __device__ int stencil_class_warp(Geo *g, int cls, int cell_base, Row *out, int 
       const int xhi = (int)ceil((w1 + rce - sx) * iw1) - 1;
       Row r;
       const double sxi = rint(sx * iw1);
-      set_shift(r, sx - sxi * w1, (double)(jyu - iy) * w2 + yshift, (double)(jzu - iz) * w3, q);
+      set_shift(r, sx - sxi * w1, (double)(jyu - iy) * w2 + yshift, (double)(jzu - iz) * w3, q, g->quantum_inv);
       r.cbase = cell_base + l1 * (jy + l2 * jz);
       r.sxi = (int)sxi;
       r.dxlo = xlo;

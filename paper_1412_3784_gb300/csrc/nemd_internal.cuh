@@ -66,6 +66,7 @@ struct Geo {
   float kap[3];
   float rho1;
   double quantum;     // float32 coordinates and offsets are multiples of this power of 2
+  double quantum_inv;  // 1 / quantum (exact)
   double vol_ds, vol_do;  // neighbourhood volumes (Sec. 5.1, 5.2) of both variants
   int counts_ds[3], counts_do[3];
   int error;   // this step's error bits
