@@ -382,8 +382,11 @@ def section_main(args, rank, world, dev, torch, nemd, W):
                               f"lane-ops/s; derived from unit counts and the clock, not measured)"}
 
     # end to end through the C ABI with pinned host buffers
+    # Se strains spread evenly over the period, so that the e2e workload has
+    # the same mix of lattice shapes as the device-resident step
     Se = min(args.e2e_strains, S)
-    qh = [torch.from_numpy(ser.positions(ts[i])).pin_memory() for i in range(Se)]
+    e2e_idx = [j * S // Se for j in range(Se)]
+    qh = [torch.from_numpy(ser.positions(ts[i])).pin_memory() for i in e2e_idx]
     Fh = torch.empty((n, 3), dtype=torch.float32).pin_memory()
     Uh = torch.zeros(1, dtype=torch.float64).pin_memory()
     Wh = torch.zeros(9, dtype=torch.float64).pin_memory()
@@ -391,23 +394,33 @@ def section_main(args, rank, world, dev, torch, nemd, W):
     # asynchronous host I/O: the copy of the next state's positions (and of the
     # previous result) overlaps the current evaluation; results valid after sync
     ctx.set_option(nemd.NEMD_OPT_ASYNC_HOST, 1)
-    for i in range(min(3, Se)):
-        ctx.set_state(qh[i], ts[i])
+    for j in range(min(3, Se)):
+        ctx.set_state(qh[j], ts[e2e_idx[j]])
         ctx.build_cells(variant, ser.rc)
         ctx.compute_forces(Fh, Uh, Wh)
     ctx.sync()
     barrier(world)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    for i in range(Se):
-        ctx.set_state(qh[i], ts[i])
+    for j in range(Se):
+        ctx.set_state(qh[j], ts[e2e_idx[j]])
         ctx.build_cells(variant, ser.rc)
         ctx.compute_forces(Fh, Uh, Wh)
     ctx.sync()                           # every copy back has landed
     torch.cuda.synchronize(dev)
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
     ctx.set_option(nemd.NEMD_OPT_ASYNC_HOST, 0)
-    e2e_pairs = sum_over_ranks(float(sum(per["tuned"]["pairs"][:Se])), world, dev)
+    e2e_pairs = sum_over_ranks(float(sum(per["tuned"]["pairs"][i] for i in e2e_idx)), world, dev)
+    # the same strains from device-resident positions, timed the same way
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for j in range(Se):
+        ctx.set_state(q_all[e2e_idx[j]], ts[e2e_idx[j]])
+        ctx.build_cells(variant, ser.rc)
+        ctx.compute_forces(F, U, Wv)
+    ctx.sync()
+    torch.cuda.synchronize(dev)
+    dev_same_s = max_over_ranks(time.perf_counter() - t0, world, dev)
     # the box's pinned host <-> device copy rate, measured beside the e2e loop
     probe_h = torch.empty(6 << 20, dtype=torch.float32).pin_memory()
     probe_d = torch.empty(6 << 20, dtype=torch.float32, device=dev)
@@ -422,8 +435,9 @@ def section_main(args, rank, world, dev, torch, nemd, W):
         torch.cuda.synchronize(dev)
         rates[name] = 10 * (24 << 20) / (time.perf_counter() - t1) / 1e9
     e2e = {"value": e2e_pairs / e2e_s, "unit": "pairs/s", "copy_rates": rates,
+           "device_resident_same_strains": e2e_pairs / dev_same_s,
            "h2d_bytes_per_step": int(S * n * 3 * 8), "d2h_bytes_per_step": int(S * (n * 3 * 4 + 80)),
-           "strains_timed": Se,
+           "strains_timed": Se, "strains_timed_are": "evenly spaced over the period",
            "mode": "host positions in and host F, U, W out every strain through the C ABI with "
                    "NEMD_OPT_ASYNC_HOST (copies on a second stream overlap the evaluations), one sync at the end"}
     ctx.close()

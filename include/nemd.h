@@ -242,7 +242,7 @@ int nemd_tune_load(nemd_ctx *ctx, const char *path);
  * cell lists is the neighbourhood-volume comparison of Sec. 5.1-5.2
  * (NEMD_AUTO_HEURISTIC), which remains the fallback.  A small multilayer
  * perceptron (12 -> 64 -> 64 -> 4, ReLU, float32) predicts, per step, the
- * normalised ln(time) of the four options o = (variant o & 1, cell factor
+ * normalised ln(time / N) of the four options o = (variant o & 1, cell factor
  * 1 + (o >> 1)) from the features of the step:
  *   x[0..8]  the entries of L(t) / V^(1/3) (row-major)
  *   x[9]     N / V        x[10]  rc        x[11]  ln N
@@ -264,7 +264,8 @@ int nemd_features(nemd_ctx *ctx, double rc, float out[12]);
 int nemd_time_options(nemd_ctx *ctx, double rc, int reps, float features[12], float ms[4]);
 
 /* Train from scratch on `rows` rows (X: rows x 12 features, T_ms: rows x 4
- * times in ms, all > 0): inputs and ln(time) targets normalised by their mean
+ * times in ms, all > 0): inputs and ln(time / N) targets (time per particle,
+ * N = exp(x[11])) normalised by their mean
  * and standard deviation, Glorot-uniform weights from `seed`, then `steps`
  * Adam steps (lr) on mini-batches of `batch` rows drawn with replacement.
  * loss_hist (optional) receives each step's mini-batch mean squared error.
@@ -272,7 +273,7 @@ int nemd_time_options(nemd_ctx *ctx, double rc, int reps, float features[12], fl
 int nemd_model_train(nemd_ctx *ctx, const float *X, const float *T_ms, int64_t rows, int steps, int batch, double lr,
                      uint64_t seed, float *loss_hist);
 
-/* Predicted normalised ln(time) (rows x 4) of raw feature rows X (rows x 12). */
+/* Predicted normalised ln(time / N) (rows x 4) of raw feature rows X (rows x 12). */
 int nemd_model_predict(nemd_ctx *ctx, const float *X, int64_t rows, float *Y);
 
 /* Gradient (NEMD_MLP_PARAMS floats) and value of L = sum (y - t)^2 / (rows 4)

@@ -6,10 +6,10 @@
 // against.  The choice changes only the time, never the pair set or forces.
 //
 // Inputs (12): the 9 entries of L(t) / V^(1/3), the number density N / V, the
-// cut-off rc and ln N.  Outputs (4): predicted normalised ln(time) of
+// cut-off rc and ln N.  Outputs (4): predicted normalised ln(time / N) of
 // option o = (variant o & 1, cell factor 1 + (o >> 1)).  Layers 12 -> 64 (ReLU)
 // -> 64 (ReLU) -> 4, float32.  Training minimises the mean squared error of
-// the normalised ln(time) with Adam; gradients are summed per weight over the
+// the normalised ln(time / N) with Adam; gradients are summed per weight over the
 // batch in a fixed order (one thread per weight), so training is deterministic.
 #include <math.h>
 #include <stdio.h>
@@ -329,7 +329,7 @@ int nemd_model_grad(nemd_ctx *c, const float *Xn, const float *Tn, int64_t rows,
 }
 
 // Train on (features X, times T in ms, rows x 4) from scratch: inputs and
-// ln(time) targets are normalised by their mean and standard deviation,
+// ln(time / N) targets are normalised by their mean and standard deviation,
 // weights start Glorot-uniform from `seed`, then `steps` Adam steps on
 // mini-batches of `batch` rows drawn with replacement.  loss_hist (optional,
 // `steps` entries) receives each step's mini-batch loss.
@@ -342,7 +342,11 @@ int nemd_model_train(nemd_ctx *c, const float *X, const float *Tms, int64_t rows
   if (r) return r;
   const int DI = nemd::kMlpIn, H = nemd::kMlpHidden, DO_ = nemd::kMlpOut, P = nemd::kMlpParams;
   const size_t nr = (size_t)rows;
-  // normalisation (host): input means / std, one mean / std over all ln(time) targets
+  // normalisation (host): input means / std, one mean / std over all targets.
+  // Targets are ln(time / N) (x[11] = ln N): the time per particle depends far
+  // less on N than the time itself, so a system larger than every training
+  // system is not an extrapolation of the target; the option with the smallest
+  // prediction is the same either way.
   float norm[2 * nemd::kMlpIn + 2];
   for (int i = 0; i < DI; i++) {
     double m = 0.0, v = 0.0;
@@ -353,13 +357,14 @@ int nemd_model_train(nemd_ctx *c, const float *X, const float *Tms, int64_t rows
     norm[i] = (float)m;
     norm[DI + i] = (float)(v > 1e-6 ? v : 1.0);
   }
+  auto target = [&](size_t k) { return log((double)Tms[k]) - (double)X[(k / DO_) * DI + (DI - 1)]; };
   double tm = 0.0, tv = 0.0;
   for (size_t k = 0; k < nr * DO_; k++) {
     if (!(Tms[k] > 0.f)) return NEMD_ERR_ARG;
-    tm += log((double)Tms[k]);
+    tm += target(k);
   }
   tm /= (double)(nr * DO_);
-  for (size_t k = 0; k < nr * DO_; k++) tv += (log((double)Tms[k]) - tm) * (log((double)Tms[k]) - tm);
+  for (size_t k = 0; k < nr * DO_; k++) tv += (target(k) - tm) * (target(k) - tm);
   tv = sqrt(tv / (double)(nr * DO_));
   norm[2 * DI] = (float)tm;
   norm[2 * DI + 1] = (float)(tv > 1e-6 ? tv : 1.0);
@@ -375,7 +380,7 @@ int nemd_model_train(nemd_ctx *c, const float *X, const float *Tms, int64_t rows
   float *tn = xn + nr * DI;
   for (size_t b = 0; b < nr; b++) {
     for (int i = 0; i < DI; i++) xn[b * DI + i] = (X[b * DI + i] - norm[i]) / norm[DI + i];
-    for (int o = 0; o < DO_; o++) tn[b * DO_ + o] = (float)((log((double)Tms[b * DO_ + o]) - tm) / norm[2 * DI + 1]);
+    for (int o = 0; o < DO_; o++) tn[b * DO_ + o] = (float)((target(b * DO_ + o) - tm) / norm[2 * DI + 1]);
   }
   init_params(p0, seed);
   r = nemd_model_set_params(c, p0, norm);

@@ -49,7 +49,7 @@ def test_training_fits_a_smooth_target():
     assert hist[-50:].mean() < 0.1 * hist[:50].mean()
     Y = ctx.model_predict(X)
     _, norm = ctx.model_get_params()
-    pred = np.exp(Y * norm[25] + norm[24])
+    pred = np.exp(Y * norm[25] + norm[24] + X[:, 11:12])     # targets are ln(time / N), N = exp(x[11])
     assert np.mean(np.abs(np.log(pred) - np.log(T))) < 0.1
     ctx.close()
 
