@@ -399,16 +399,20 @@ def section_main(args, rank, world, dev, torch, nemd, W):
         ctx.build_cells(variant, ser.rc)
         ctx.compute_forces(Fh, Uh, Wh)
     ctx.sync()
-    barrier(world)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for j in range(Se):
-        ctx.set_state(qh[j], ts[e2e_idx[j]])
-        ctx.build_cells(variant, ser.rc)
-        ctx.compute_forces(Fh, Uh, Wh)
-    ctx.sync()                           # every copy back has landed
-    torch.cuda.synchronize(dev)
-    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    # three timed passes over the Se strains; the median pass is reported
+    e2e_reps = []
+    for _ in range(3):
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for j in range(Se):
+            ctx.set_state(qh[j], ts[e2e_idx[j]])
+            ctx.build_cells(variant, ser.rc)
+            ctx.compute_forces(Fh, Uh, Wh)
+        ctx.sync()                           # every copy back has landed
+        torch.cuda.synchronize(dev)
+        e2e_reps.append(max_over_ranks(time.perf_counter() - t0, world, dev))
+    e2e_s = sorted(e2e_reps)[1]
     ctx.set_option(nemd.NEMD_OPT_ASYNC_HOST, 0)
     e2e_pairs = sum_over_ranks(float(sum(per["tuned"]["pairs"][i] for i in e2e_idx)), world, dev)
     # the same strains from device-resident positions, timed the same way
@@ -436,10 +440,11 @@ def section_main(args, rank, world, dev, torch, nemd, W):
         rates[name] = 10 * (24 << 20) / (time.perf_counter() - t1) / 1e9
     e2e = {"value": e2e_pairs / e2e_s, "unit": "pairs/s", "copy_rates": rates,
            "device_resident_same_strains": e2e_pairs / dev_same_s,
+           "pass_ms": [round(x * 1e3, 3) for x in e2e_reps],
            "h2d_bytes_per_step": int(S * n * 3 * 8), "d2h_bytes_per_step": int(S * (n * 3 * 4 + 80)),
            "strains_timed": Se, "strains_timed_are": "evenly spaced over the period",
            "mode": "host positions in and host F, U, W out every strain through the C ABI with "
-                   "NEMD_OPT_ASYNC_HOST (copies on a second stream overlap the evaluations), one sync at the end"}
+                   "NEMD_OPT_ASYNC_HOST (copies on a second stream overlap the evaluations), one sync at the end; median of three passes"}
     ctx.close()
     del q_all
 

@@ -434,7 +434,7 @@ int nemd_batch_autotune(nemd_batch *b, int reps, nemd_tune_entry *times, int cap
  * legacy default stream).  All work is asynchronous on `stream`. */
 #define NEMD_NOALLOC_MAX_N 16384
 #define NEMD_NOALLOC_MAX_CELLS 16384
-#define NEMD_NOALLOC_SCRATCH_BYTES 11154176
+#define NEMD_NOALLOC_SCRATCH_BYTES 11154432
 int nemd_forces_noalloc(const double A[9], const double L0[9], double T, double t, const double *q, int64_t n,
                         int variant, double rc, int kind, double eps, double sigma, int shift, float *F, double *UW,
                         int *status, void *stream);

@@ -36,39 +36,52 @@ __device__ __forceinline__ void wrap_body(Geo *g, const double *__restrict__ q, 
   double s[3];
   frac_wrap(g->Linv, x, y, z, s);
   const int l1 = g->nc[0], l2 = g->nc[1], l3 = g->nc[2];
+  // Everything after the float64 fractional coordinates runs in float-float
+  // (float64 throughput is a small fraction of float32 throughput here); the
+  // position error stays below g->wrap_tol, which the guard bands and the
+  // dynamic offset windows include.
+  const ff sf[3] = {split_unit(s[0]), split_unit(s[1]), split_unit(s[2])};
   // position relative to the centre of its cell, in the variant's frame:
-  // dynamic size: Cartesian, G (u - 1/2) with u = c s - idx the cell-fractional part;
+  // dynamic size: Cartesian, G (u - 1/2) with u = c s - idx the cell-fractional part
+  // (the cell index itself from the float64 product c s);
   // dynamic offset: the rotated frame, b - (idx + 1/2) w for the brick point b
   int idx[3];
-  double rel[3];
+  ff rel[3];
   if (g->variant == NEMD_DS) {
-    double u[3];
+    ff u[3];
     for (int a = 0; a < 3; a++) {
-      double v = s[a] * g->Ginv_scale[a];
-      int k = (int)floor(v);
+      int k = __double2int_rd(__dmul_rn(s[a], g->Ginv_scale[a]));
       k = min(max(k, 0), g->nc[a] - 1);
       idx[a] = k;
-      u[a] = (v - (double)k) - 0.5;
+      u[a] = ff_add(ff_mul_f(sf[a], (float)g->nc[a]), ff{-((float)k + 0.5f), 0.f});
     }
-    for (int a = 0; a < 3; a++) rel[a] = fma(g->G[3 * a], u[0], fma(g->G[3 * a + 1], u[1], g->G[3 * a + 2] * u[2]));
+    for (int a = 0; a < 3; a++)
+      rel[a] = ff_add(ff_add(ff_mul(ff_of(g->Gff[3 * a]), u[0]), ff_mul(ff_of(g->Gff[3 * a + 1]), u[1])),
+                      ff_mul(ff_of(g->Gff[3 * a + 2]), u[2]));
   } else {
-    double b[3];
+    ff b[3];
     int m[3];
-    brick_wrap(g->R, g->rinv, s, b, m);
+    brick_wrap_ff(g, sf, b, m);
     for (int a = 0; a < 3; a++) {
-      int k = (int)floor(b[a] * g->Ginv_scale[a]);
+      int k = (int)ff_floor(ff_mul(b[a], ff_of(g->Ginvff[a])));
       k = min(max(k, 0), g->nc[a] - 1);
       idx[a] = k;
-      rel[a] = b[a] - ((double)k + 0.5) * g->w[a];
+      rel[a] = ff_add(b[a], ff_neg(ff_mul_f(ff_of(g->wff[a]), (float)k + 0.5f)));
     }
   }
-  // split into an exact multiple of the quantum and a float32 residual
-  const double qu = g->quantum, qinv = g->quantum_inv;
+  // split into an exact multiple of the quantum q and a float32 residual:
+  // t = rel / q (exact power-of-two scaling), r = nearest integer to t,
+  // stored r q (exact) and (t - r) q (t.hi - r exact, one rounding)
+  const float qf = g->quantum_f, qif = g->quantum_inv_f;
   float rq[3], rr[3];
   for (int a = 0; a < 3; a++) {
-    double h = rint(rel[a] * qinv) * qu;
-    rq[a] = (float)h;
-    rr[a] = (float)(rel[a] - h);
+    const float th = __fmul_rn(rel[a].hi, qif), tl = __fmul_rn(rel[a].lo, qif);
+    float r = rintf(th);
+    const float d = __fadd_rn(__fsub_rn(th, r), tl);
+    if (d > 0.5f) r = __fadd_rn(r, 1.f);
+    else if (d < -0.5f) r = __fsub_rn(r, 1.f);
+    rq[a] = __fmul_rn(r, qf);
+    rr[a] = __fmaf_rn(tl, qf, __fmul_rn(__fsub_rn(th, r), qf));
   }
   const int cell = cell_base + idx[0] + l1 * (idx[1] + l2 * idx[2]);
   (void)l3;

@@ -14,6 +14,14 @@
 
 #include "batch_internal.cuh"
 
+namespace {
+// float-float (hi, lo) form of a float64 value: hi rounded, lo the rounded rest
+__device__ __forceinline__ float2 to_ff2(double x) {
+  const float hi = __double2float_rn(x);
+  return make_float2(hi, __double2float_rn(x - (double)hi));
+}
+}  // namespace
+
 namespace nemd {
 
 namespace {
@@ -182,8 +190,14 @@ __device__ __forceinline__ void lattice_body(Geo *g, const LatIn &in) {
     Ri[8] = i33;
   }
   __syncwarp();
-  if (lane < 9) g->R[lane] = Rm[lane];
-  if (lane < 3) g->rinv[lane] = 1.0 / Rm[4 * lane];
+  if (lane < 9) {
+    g->R[lane] = Rm[lane];
+    g->Rff[lane] = to_ff2(Rm[lane]);
+  }
+  if (lane < 3) {
+    g->rinv[lane] = 1.0 / Rm[4 * lane];
+    g->rinvff[lane] = to_ff2(1.0 / Rm[4 * lane]);
+  }
   mm3(Ls, Ri, Ri, lane);  // Q = L R^-1
   if (lane < 9) g->Q[lane] = Ri[lane];
   __syncwarp();
@@ -246,7 +260,15 @@ __device__ void grid_body(Geo *g, const GridIn &in) {
   float step[3];
   int reach[3];
   int maxrows;
-  const double rce = rc * (1.0 + kMargin);
+  // bound on the float-float wrap's position error (it does a few dozen
+  // operations of relative error ~2^-45 on values up to the box's extent):
+  // the dynamic offset windows reach this much further, so a particle binned a
+  // rounding outside its cell still finds every partner
+  double lsum = 0.0;
+  for (int k = 0; k < 9; k++) lsum += fabs(Ls[k]) + fabs(Rm[k]);
+  const double wtol = ldexp(lsum + 1.0, -38);
+  g->wrap_tol = wtol;
+  const double rce = rc * (1.0 + kMargin) + (variant == NEMD_DS ? 0.0 : 2.0 * wtol);
   if (variant == NEMD_DS) {
     for (int a = 0; a < 3; a++) nc[a] = (int)floor(fac * (double)kf * g->h[a] / rc);
     for (int a = 0; a < 3; a++)
@@ -265,6 +287,8 @@ __device__ void grid_body(Geo *g, const GridIn &in) {
       double w = (nc[a] > 0) ? Rm[4 * a] / (double)nc[a] : 1.0;
       g->w[a] = w;
       g->Ginv_scale[a] = 1.0 / w;
+      g->wff[a] = to_ff2(w);
+      g->Ginvff[a] = to_ff2(1.0 / w);
       Gd[4 * a] = w;
       reach[a] = (int)ceil(rce / w);
     }
@@ -285,6 +309,7 @@ __device__ void grid_body(Geo *g, const GridIn &in) {
   for (int k = 0; k < 9; k++) {
     g->G[k] = Gd[k];
     g->Gf[k] = (float)Gd[k];
+    g->Gff[k] = to_ff2(Gd[k]);
   }
   // Quantum: float32 positions and offsets are stored as exact multiples of a
   // power of two q, chosen so that every intermediate (|rel| + |offset| bounded
@@ -303,6 +328,8 @@ __device__ void grid_body(Geo *g, const GridIn &in) {
   const double q = ldexp(1.0, e2 - 23);
   g->quantum = q;
   g->quantum_inv = ldexp(1.0, 23 - e2);
+  g->quantum_f = (float)q;
+  g->quantum_inv_f = (float)g->quantum_inv;
   // frame vector between consecutive x-cells: G e_x (dynamic size), (w1, 0, 0) (dynamic offset)
   for (int a = 0; a < 3; a++) {
     double sv = Gd[3 * a];
@@ -317,9 +344,14 @@ __device__ void grid_body(Geo *g, const GridIn &in) {
   const double u = 5.9604644775390625e-08;  // 2^-24
   const double E = (double)(rmax + 6 + kMaxSpan) * 0.5 * q;
   const double s3 = 1.7320508075688772;
-  double band = 2.0 * (2.0 * s3 * rc * E + 3.0 * E * E + 3.0 * u * rc * rc) + 1e-12 * rc * rc;
+  // Both bands also cover the wrap's float-float error: each position within
+  // dw of its float64 value (wrap_tol, plus a rounding of the residual), so
+  // |d| within 2 dw and r^2 within 4 rc dw + 4 dw^2.
+  const double dw = wtol + ldexp(q, -20);
+  const double wterm = 4.0 * rc * dw + 4.0 * dw * dw;
+  double band = 2.0 * (2.0 * s3 * rc * E + 3.0 * E * E + 3.0 * u * rc * rc) + 1e-12 * rc * rc + wterm;
   const double E2 = 2.0 * u * (rc + q);
-  double band2 = 2.0 * (2.0 * s3 * rc * E2 + 3.0 * E2 * E2 + 3.0 * u * rc * rc) + 1e-12 * rc * rc;
+  double band2 = 2.0 * (2.0 * s3 * rc * E2 + 3.0 * E2 * E2 + 3.0 * u * rc * rc) + 1e-12 * rc * rc + wterm;
   for (int a = 0; a < 3; a++) g->step[a] = step[a];
   g->band = (float)band;
   {
@@ -356,7 +388,7 @@ __device__ int stencil_class_warp(Geo *g, int cls, int cell_base, Row *out, int 
   constexpr int kMaxZ = 2 * kMaxFactor + 4;  // bound on the z-rows of a dynamic offset class
   const int l1 = g->nc[0], l2 = g->nc[1], l3 = g->nc[2];
   const int maxrows = g->maxrows;
-  const double rce = g->rc * (1.0 + kMargin);
+  const double rce = g->rc * (1.0 + kMargin) + (g->variant == NEMD_DS ? 0.0 : 2.0 * g->wrap_tol);
   const double q = g->quantum;
   const int iy = cls % l2, iz = cls / l2;
   int nr;

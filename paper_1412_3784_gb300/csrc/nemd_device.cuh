@@ -33,27 +33,94 @@ __device__ __forceinline__ void frac_to_cart(const double *L, const double s[3],
     qp[a] = __dadd_rn(__dadd_rn(__dmul_rn(L[3 * a], s[0]), __dmul_rn(L[3 * a + 1], s[1])), __dmul_rn(L[3 * a + 2], s[2]));
 }
 
-// Rectangular rearrangement of the rotated box (Sec. 4.2): the point R s is
-// moved by lattice vectors into the brick [0,r11) x [0,r22) x [0,r33) --
-// first along z (shifting x and y by the third column of R), then y (shifting
-// x by r12), then x modulo r11.  b = R (s - m).  The quotients use the
-// reciprocals rinv = 1 / r_ii; every caller uses this one function, so the
-// binning and the image of a pair agree even for points on a brick face (b
-// may then lie a rounding outside the brick; the cell index is clamped).
-__device__ __forceinline__ void brick_wrap(const double *R, const double *rinv, const double s[3], double b[3],
-                                           int m[3]) {
-  double x = R[0] * s[0] + R[1] * s[1] + R[2] * s[2];
-  double y = R[4] * s[1] + R[5] * s[2];
-  double z = R[8] * s[2];
-  double m3 = floor(z * rinv[2]);
-  z -= m3 * R[8];
-  y -= m3 * R[5];
-  x -= m3 * R[2];
-  double m2 = floor(y * rinv[1]);
-  y -= m2 * R[4];
-  x -= m2 * R[1];
-  double m1 = floor(x * rinv[0]);
-  x -= m1 * R[0];
+// ---- float-float arithmetic: a value is hi + lo with |lo| <= ulp(hi) / 2 ----
+// Built from error-free transformations: TwoSum (Knuth), Fast2Sum (Dekker) and
+// TwoProduct through a fused multiply-add.  Every step is an explicit
+// round-to-nearest intrinsic, so no compiler contraction changes a result and
+// the same inputs give the same bits in every kernel.  Relative error of one
+// operation is about 2^-45 of its operands' magnitudes.
+struct ff {
+  float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_of(float2 v) { return {v.x, v.y}; }
+
+__device__ __forceinline__ ff fast2sum(float a, float b) {  // |a| >= |b| or a = 0
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ ff ff_add(ff x, ff y) {
+  const float s = __fadd_rn(x.hi, y.hi);
+  const float bb = __fsub_rn(s, x.hi);
+  float e = __fadd_rn(__fsub_rn(x.hi, __fsub_rn(s, bb)), __fsub_rn(y.hi, bb));
+  e = __fadd_rn(e, __fadd_rn(x.lo, y.lo));
+  return fast2sum(s, e);
+}
+
+__device__ __forceinline__ ff ff_neg(ff x) { return {-x.hi, -x.lo}; }
+
+__device__ __forceinline__ ff ff_mul(ff x, ff y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return fast2sum(p, e);
+}
+
+__device__ __forceinline__ ff ff_mul_f(ff x, float b) {
+  const float p = __fmul_rn(x.hi, b);
+  float e = __fmaf_rn(x.hi, b, -p);
+  e = __fmaf_rn(x.lo, b, e);
+  return fast2sum(p, e);
+}
+
+// floor(hi + lo) as a float: floor(hi), one lower when hi is an integer and lo < 0
+// (a non-integer hi is at least ulp(hi) from every integer, more than |lo|)
+__device__ __forceinline__ float ff_floor(ff x) {
+  const float f = floorf(x.hi);
+  return (f == x.hi && x.lo < 0.f) ? __fsub_rn(f, 1.f) : f;
+}
+
+// Float-float split of s in [0, 1) from its bits, integer operations only: hi
+// keeps the leading 24 significant bits, lo the next 29 (rounded to 24), then
+// the pair is renormalised; values below 2^-74 lose lo (below 2^-126 also hi),
+// an error under 2^-98.
+__device__ __forceinline__ ff split_unit(double s) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(s);
+  const int e = (int)(b >> 52);  // biased exponent; s >= 0
+  if (e < 1023 - 126) return {0.f, 0.f};
+  const unsigned int m_hi = (unsigned int)(b >> 29) & 0x7fffffu;
+  const float hi = __int_as_float(((e - 1023 + 127) << 23) | (int)m_hi);
+  if (e < 949) return {hi, 0.f};
+  const unsigned int m_lo = (unsigned int)b & 0x1fffffffu;
+  const float scale = __int_as_float((e - 1075 + 127) << 23);  // 2^(e - 1075), normal for e >= 949
+  return fast2sum(hi, __fmul_rn(__uint2float_rn(m_lo), scale));
+}
+
+// Rectangular rearrangement of the rotated box (Sec. 4.2) in float-float: the
+// point R s is moved by lattice vectors into the brick [0,r11) x [0,r22) x
+// [0,r33) -- first along z (shifting x and y by the third column of R), then y
+// (shifting x by r12), then x modulo r11.  b = R (s - m).  Every caller (the
+// wrap, and the image of a pair in the float64 guard band and the pair record)
+// uses this one function on the same split of the same s, so the binning and
+// the image of a pair agree even for points on a brick face (b may then lie a
+// rounding outside the brick; the cell index is clamped).
+__device__ __forceinline__ void brick_wrap_ff(const Geo *g, const ff s[3], ff b[3], int m[3]) {
+  const ff r11 = ff_of(g->Rff[0]), r12 = ff_of(g->Rff[1]), r13 = ff_of(g->Rff[2]);
+  const ff r22 = ff_of(g->Rff[4]), r23 = ff_of(g->Rff[5]), r33 = ff_of(g->Rff[8]);
+  ff x = ff_add(ff_add(ff_mul(r11, s[0]), ff_mul(r12, s[1])), ff_mul(r13, s[2]));
+  ff y = ff_add(ff_mul(r22, s[1]), ff_mul(r23, s[2]));
+  ff z = ff_mul(r33, s[2]);
+  const float m3 = ff_floor(ff_mul(z, ff_of(g->rinvff[2])));
+  z = ff_add(z, ff_neg(ff_mul_f(r33, m3)));
+  y = ff_add(y, ff_neg(ff_mul_f(r23, m3)));
+  x = ff_add(x, ff_neg(ff_mul_f(r13, m3)));
+  const float m2 = ff_floor(ff_mul(y, ff_of(g->rinvff[1])));
+  y = ff_add(y, ff_neg(ff_mul_f(r22, m2)));
+  x = ff_add(x, ff_neg(ff_mul_f(r12, m2)));
+  const float m1 = ff_floor(ff_mul(x, ff_of(g->rinvff[0])));
+  x = ff_add(x, ff_neg(ff_mul_f(r11, m1)));
   b[0] = x;
   b[1] = y;
   b[2] = z;
@@ -85,9 +152,11 @@ __device__ __forceinline__ double canon_r2(const Geo *g, const double *q, int oi
 // Lattice image of particle oi's brick position relative to its wrapped
 // fractional position (dynamic offset frame), recomputed from q.
 __device__ __forceinline__ void brick_image(const Geo *g, const double *q, int oi, int m[3]) {
-  double s[3], b[3];
+  double s[3];
   frac_wrap(g->Linv, q[3 * (size_t)oi], q[3 * (size_t)oi + 1], q[3 * (size_t)oi + 2], s);
-  brick_wrap(g->R, g->rinv, s, b, m);
+  const ff sf[3] = {split_unit(s[0]), split_unit(s[1]), split_unit(s[2])};
+  ff b[3];
+  brick_wrap_ff(g, sf, b, m);
 }
 
 }  // namespace nemd

@@ -65,6 +65,12 @@ struct Geo {
   // are farther apart than rc
   float kap[3];
   float rho1;
+  // float-float (hi, lo) copies of the wrap's frame data: R, 1 / r_ii, G, the
+  // dynamic offset 1 / w_i and w_i.  The wrap works in float-float after the
+  // float64 fractional coordinates; wrap_tol bounds its position error.
+  float2 Rff[9], rinvff[3], Gff[9], Ginvff[3], wff[3];
+  double wrap_tol;
+  float quantum_f, quantum_inv_f;  // the quantum and its inverse (powers of two) as float
   double quantum;     // float32 coordinates and offsets are multiples of this power of 2
   double quantum_inv;  // 1 / quantum (exact)
   double vol_ds, vol_do;  // neighbourhood volumes (Sec. 5.1, 5.2) of both variants

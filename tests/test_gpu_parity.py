@@ -157,6 +157,56 @@ def test_edge_cases_small_n():
         assert abs(g["F"][0, 0] - (-du)) < 1e-5 * abs(du)
 
 
+def face_positions(L, rc, faces, rng):
+    """Particles on the half-cell grid of one variant's cells (every interior
+    face and centre; cell factor 1) with 30 % vacancies, each coordinate moved by 0, +-1 or +-2 units in the
+    last place or +-2^-44 of the box: binning decisions at and a rounding either
+    side of every face."""
+    if faces == "ds":
+        c = oracle.ds_counts(L, rc)
+        axes = [np.arange(2 * c[a]) / (2.0 * c[a]) for a in range(3)]
+        s = np.stack(np.meshgrid(*axes, indexing="ij"), -1).reshape(-1, 3)
+        q = s @ L.T
+    else:
+        Q, R = oracle.qr(L)
+        l = oracle.do_counts(R, rc)
+        axes = [np.arange(2 * l[a]) * (R[a, a] / (2.0 * l[a])) for a in range(3)]
+        b = np.stack(np.meshgrid(*axes, indexing="ij"), -1).reshape(-1, 3)
+        q = b @ Q.T       # L s = Q R s = Q b
+    # Interior faces only: a particle within a rounding of the unit cell's own
+    # boundary (s = 0 or 1) is wrapped by L(t), which each side computes to
+    # ~1e-15 relative on its own, so its canonical image (the n of its pairs)
+    # may legitimately differ by a lattice vector between the two.
+    sr = q @ np.linalg.inv(L).T
+    keep = (np.abs(sr - np.rint(sr)).min(axis=1) > 1e-9) & (rng.random(len(q)) < 0.7)
+    q = q[keep]                          # (and vacancies: no symmetric cancellation of forces)
+    ulp = np.spacing(np.abs(q) + 1e-300)
+    kick = rng.choice(np.array([0.0, 1.0, -1.0, 2.0, -2.0]), size=q.shape) * ulp
+    tiny = rng.choice(np.array([0.0, 1.0, -1.0]), size=q.shape) * (2.0 ** -44) * np.abs(L).max()
+    use_tiny = rng.random(q.shape) < 0.3
+    return np.ascontiguousarray(q + np.where(use_tiny, tiny, kick))
+
+
+@pytest.mark.parametrize("kernel", DETERMINISTIC)
+@pytest.mark.parametrize("faces", ["ds", "do"])
+@pytest.mark.parametrize("frac", [0.0, 0.37, 0.999])
+def test_particles_on_cell_and_brick_faces(frac, faces, kernel):
+    """Particles on the faces of the dynamic size cells or the dynamic offset
+    bricks of a general-flow box at three strains; both variants, both cell
+    factors: exact pair set, forces, energy and virial against brute force."""
+    rng = np.random.default_rng(int(frac * 1000) + (17 if faces == "ds" else 71))
+    ser = W.general_series(k=10, seed=9)
+    t = frac * ser.period
+    L = oracle.lattice(ser.A, ser.L0, ser.period, t)["L"]
+    q = face_positions(L, ser.rc, faces, rng)
+    w = W.Workload(name="faces", A=ser.A, L0=ser.L0, M=ser.M, T=ser.period, t=t, q=q, kind=W.POT_LJ, rc=ser.rc)
+    ref = oracle.evaluate(w, "brute", want_pairs=True)
+    assert ref.npairs > 0
+    for kfac in (1, 2):
+        for v in (DS, DO):
+            check_against(w, v, ref, kfac=kfac, kernel=kernel, precise=(kfac == 1))
+
+
 @pytest.mark.parametrize("kernel", KERNELS)
 def test_ragged_counts_and_empty_cells(kernel):
     """A dilute random system: many empty cells, uneven occupancy."""
