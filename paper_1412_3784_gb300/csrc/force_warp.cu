@@ -168,6 +168,31 @@ __device__ __forceinline__ void flush_partners(WarpStageT<HALF> &S, int fill, in
   __syncwarp();
 }
 
+// Window of one staged row for the chunk: the window cells u in [ufirst, ulast]
+// (ulast < ufirst: none) whose A = dxlo + sxi + u can hold a partner of a lane
+// with kappa position in [pmin, pmax], and the wrapped x-cell jx of the first.
+struct RowWindow {
+  int ufirst, ulast, jx, ulo;
+};
+
+__device__ __forceinline__ RowWindow row_window(const float4 &s0, const float4 &s1, const float4 &s2, int ixlo,
+                                                int ixhi, int l1, float kx0, float ky0, float kz0, float pmin,
+                                                float pmax, float reach1) {
+  const int dxlo = __float_as_int(s1.w);
+  const int rcnt = __float_as_int(s2.x), sxi = __float_as_int(s2.z);
+  RowWindow w;
+  w.ulo = ixlo + dxlo;
+  const int nu = ixhi - ixlo + rcnt;
+  // the row shift along the row
+  const float sh1 = fmaf(kz0, s0.z + s1.z, fmaf(ky0, s0.y + s1.y, kx0 * (s0.x + s1.x)));
+  const float a0 = (float)(dxlo + sxi) + sh1;
+  w.ufirst = max(0, (int)ceilf(pmin - reach1 - a0));
+  w.ulast = min(nu - 1, (int)floorf(pmax + reach1 - a0));
+  const int ustart = w.ulo + w.ufirst;
+  w.jx = ustart - floordiv_dev(ustart, l1) * l1;
+  return w;
+}
+
 // Everything one warp does for one chunk cd: stage the rows of the chunk's
 // class (crow, nr of them), then per row stage, test and queue, flushing as
 // needed.  On return acc.fx, fy, fz hold the force on the lane's particle pi
@@ -224,24 +249,40 @@ __device__ __forceinline__ void warp_chunk(const int4 cd, const Row *__restrict_
     pmax = fmaxf(pmax, __shfl_xor_sync(FULL, pmax, o));
   }
   const float reach1 = g->rho1 + 0.5f + 1e-4f;
+  // lane r looks up the particle ranges of the first two runs of row r, so that
+  // the row loop finds them without a dependent global load
+  int rb0 = 0, re0 = 0, rb1 = 0, re1 = 0;
+  if (lane < nr) {
+    const float4 s0 = S.rows[lane][0], s1 = S.rows[lane][1], s2 = S.rows[lane][2];
+    const RowWindow w = row_window(s0, s1, s2, ixlo, ixhi, l1, kx0, ky0, kz0, pmin, pmax, reach1);
+    const int cbase = __float_as_int(s0.w);
+    if (w.ufirst <= w.ulast) {
+      const int len0 = min(w.ulast + 1 - w.ufirst, l1 - w.jx);
+      rb0 = start[cbase + w.jx];
+      re0 = start[cbase + w.jx + len0];
+      const int rest = w.ulast + 1 - w.ufirst - len0;
+      if (rest > 0) {
+        rb1 = start[cbase];
+        re1 = start[cbase + min(rest, l1)];
+      }
+    }
+  }
 
   for (int r = 0; r < nr; r++) {
     const float4 s0 = S.rows[r][0], s1 = S.rows[r][1], s2 = S.rows[r][2];
+    const int pb0 = __shfl_sync(FULL, rb0, r), pe0 = __shfl_sync(FULL, re0, r);
+    const int pb1 = __shfl_sync(FULL, rb1, r), pe1 = __shfl_sync(FULL, re1, r);
     if (HALF && __float_as_int(s2.w) < 0) continue;  // met from the partner's side
     const int cbase = __float_as_int(s0.w), dxlo = __float_as_int(s1.w);
-    const int rcnt = __float_as_int(s2.x), sxi = __float_as_int(s2.z);
-    const int ulo = ixlo + dxlo, nu = ixhi - ixlo + rcnt;
-    // the row shift along the row, and the window cells u whose A = dxlo + sxi + u can hold a partner
-    const float sh1 = fmaf(kz0, s0.z + s1.z, fmaf(ky0, s0.y + s1.y, kx0 * (s0.x + s1.x)));
-    const float a0 = (float)(dxlo + sxi) + sh1;
-    const int ufirst = max(0, (int)ceilf(pmin - reach1 - a0));
-    const int ulast = min(nu - 1, (int)floorf(pmax + reach1 - a0));
-    const int ustart = ulo + ufirst;
-    int jx = ustart - floordiv_dev(ustart, l1) * l1;
+    const int sxi = __float_as_int(s2.z);
+    const RowWindow w = row_window(s0, s1, s2, ixlo, ixhi, l1, kx0, ky0, kz0, pmin, pmax, reach1);
+    const int ufirst = w.ufirst, ulast = w.ulast, ulo = w.ulo;
+    int jx = w.jx;
     // runs of consecutive cells without an x-wrap: contiguous particles
-    for (int u = ufirst; u <= ulast;) {
+    for (int u = ufirst, run = 0; u <= ulast; run++) {
       const int len = min(ulast + 1 - u, l1 - jx);
-      const int b = start[cbase + jx], e = start[cbase + jx + len];
+      const int b = run == 0 ? pb0 : (run == 1 ? pb1 : start[cbase + jx]);
+      const int e = run == 0 ? pe0 : (run == 1 ? pe1 : start[cbase + jx + len]);
       const int arun = dxlo + sxi + u - jx;  // A of a particle of cell jx' of this run: arun + jx'
       const int meta_run = r + ((ulo + u - jx + kMetaBias) << 5);
       if (act) ncand += e - b;
@@ -254,19 +295,31 @@ __device__ __forceinline__ void warp_chunk(const int4 cd, const Row *__restrict_
         }
         const int take = min(e - p, kStage - fill);
         __syncwarp();  // slots about to be overwritten are no longer read
-        for (int t = lane; t < take; t += 32) {
-          const int j = p + t;
-          const float4 pj = pos[j], pjr = posr[j];
-          const int cjx = cell_sorted[j] - cbase;
-          const float A = (float)(arun + cjx);
-          S.X[fill + t] = make_float4(fmaf(A, sx, pj.x + s0.x), fmaf(A, sy, pj.y + s0.y), fmaf(A, sz, pj.z + s0.z),
-                                      __int_as_float(j));
-          S.R[fill + t] = make_float4(fmaf(A, srx, pjr.x + s1.x), fmaf(A, sry, pjr.y + s1.y),
-                                      fmaf(A, srz, pjr.z + s1.z), __int_as_float(meta_run + (cjx << 5)));
-          if (HALF) {
-            S.Fj[0][fill + t] = 0.f;
-            S.Fj[HALF ? 1 : 0][fill + t] = 0.f;
-            S.Fj[HALF ? 2 : 0][fill + t] = 0.f;
+        // two particles per lane per pass, both loaded before either is stored
+        for (int t0 = lane; t0 < take; t0 += 64) {
+          const int t1 = t0 + 32;
+          const bool two = t1 < take;
+          const int j0 = p + t0, j1 = two ? p + t1 : j0;
+          const float4 pj0 = pos[j0], pjr0 = posr[j0];
+          const int c0 = cell_sorted[j0];
+          const float4 pj1 = pos[j1], pjr1 = posr[j1];
+          const int c1 = cell_sorted[j1];
+#pragma unroll
+          for (int h = 0; h < 2; h++) {
+            if (h == 1 && !two) break;
+            const int t = h ? t1 : t0, j = h ? j1 : j0;
+            const float4 pj = h ? pj1 : pj0, pjr = h ? pjr1 : pjr0;
+            const int cjx = (h ? c1 : c0) - cbase;
+            const float A = (float)(arun + cjx);
+            S.X[fill + t] = make_float4(fmaf(A, sx, pj.x + s0.x), fmaf(A, sy, pj.y + s0.y),
+                                        fmaf(A, sz, pj.z + s0.z), __int_as_float(j));
+            S.R[fill + t] = make_float4(fmaf(A, srx, pjr.x + s1.x), fmaf(A, sry, pjr.y + s1.y),
+                                        fmaf(A, srz, pjr.z + s1.z), __int_as_float(meta_run + (cjx << 5)));
+            if (HALF) {
+              S.Fj[0][fill + t] = 0.f;
+              S.Fj[HALF ? 1 : 0][fill + t] = 0.f;
+              S.Fj[HALF ? 2 : 0][fill + t] = 0.f;
+            }
           }
         }
         __syncwarp();

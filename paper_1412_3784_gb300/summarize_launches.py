@@ -1,6 +1,6 @@
 """Summarise an ncu --csv launch list (gpu__time_duration.sum) per kernel.
 
-Usage: python profiles/summarize_launches.py launches.csv
+Usage: python -m paper_1412_3784_gb300.summarize_launches launches.csv
 Prints launches, total time and share per kernel (markdown table).
 """
 import collections
