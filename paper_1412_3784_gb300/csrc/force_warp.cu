@@ -53,7 +53,7 @@ constexpr int kWarpThreads = NEMD_WARP_THREADS;
 constexpr int kRowsStaged = 32;    // rows per class the kernel stages (cell factor <= 2)
 constexpr int kWarpQueue = NEMD_WARP_QUEUE;  // queue entries per lane
 constexpr int kTestBlock = 32;     // candidates tested between two queue checks
-constexpr int kMetaBias = 1 << 12;  // R_j.w = row | (unwrapped x-cell + kMetaBias) << 5
+constexpr int kABias = 64;          // SA[slot] = row | (A + kABias) << 5, 0 <= A + kABias < 2^10
 static_assert(kWarpQueue >= 2 * kTestBlock, "a queue check must leave room for a test block");
 
 // Shared memory of one warp.  HALF (half neighbourhoods) also accumulates the
@@ -64,11 +64,12 @@ template <bool HALF>
 struct WarpStageT {
   static constexpr int kSlots = HALF ? 192 : NEMD_WARP_STAGE;
   using Entry = typename std::conditional<(kSlots > 256), unsigned short, unsigned char>::type;
-  float4 X[kSlots];  // .w: sorted index of j (bits)
-  float4 R[kSlots];  // .w: row and unwrapped x-cell of j (bits)
+  float4 X[kSlots];  // .w: |X_j|^2
+  float4 R[kSlots];  // .w: sorted index of j (bits)
   float Fj[HALF ? 3 : 1][HALF ? kSlots : 1];
   Entry q[kWarpQueue][32];
   float4 rows[kRowsStaged][3];
+  unsigned short SA[kSlots];  // row of the slot and its cell offset A from the chunk's first cell
 };
 using WarpStage = WarpStageT<false>;
 
@@ -78,13 +79,27 @@ __device__ __forceinline__ void red_shared_add(float *p, float v) {
   asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
 }
 
+// Stencil image (kx, ky, kz) of a staged slot: its row gives (ky, kz) and the
+// row's x-shift sxi; its unwrapped x-cell is ixlo + A - sxi.
+template <bool HALF>
+__device__ __forceinline__ void slot_image(const WarpStageT<HALF> &S, int slot, int ixlo, int l1, int &kx, int &ky,
+                                           int &kz) {
+  const int sa = S.SA[slot];
+  const float4 s2 = S.rows[sa & 31][2];
+  const int kyz = __float_as_int(s2.y);
+  kx = floordiv_dev(ixlo + (sa >> 5) - kABias - __float_as_int(s2.z), l1);
+  ky = (short)(kyz & 0xffff);
+  kz = kyz >> 16;
+}
+
 // Forces of the queued pairs of every lane.  HALF: entries of the home row
 // (row rhome) count only towards partners ahead of the lane's particle --
 // a larger unwrapped x-cell, or the same cell and a larger sorted index --
 // and each accepted pair also adds its force to the partner's slot.
 template <bool RECORD, bool HALF>
 __device__ __forceinline__ void warp_flush(WarpStageT<HALF> &S, int &qn, int &nre, int lane, int ki,
-                                           const float4 &pi, const float3 &Xi, const float3 &Ri, int ixu, int rhome,
+                                           const float4 &pi, const float3 &Xi, const float3 &Ri, int ixu, int ixlo,
+                                           int rhome,
                                            const Geo *g, const float4 *__restrict__ pos, const Pot &pp, Acc &acc,
                                            const double *q, int32_t *pair_buf, unsigned long long *pair_count,
                                            long long pair_cap, int4 *rlist, int *rcount, int *err) {
@@ -98,11 +113,12 @@ __device__ __forceinline__ void warp_flush(WarpStageT<HALF> &S, int &qn, int &nr
       const int slot = S.q[HALF ? e : s][lane];
       if (HALF && ++e == qn) e = 0;
       const float4 X = S.X[slot], R = S.R[slot];
-      const int j = __float_as_int(X.w);
+      const int j = __float_as_int(R.w);
       if (HALF) {
-        const int meta = __float_as_int(R.w);
-        if ((meta & 31) == rhome) {
-          const int jxu = (meta >> 5) - kMetaBias;
+        const int sa = S.SA[slot];
+        if ((sa & 31) == rhome) {
+          // the home row has no x-shift: unwrapped x-cell = ixlo + A
+          const int jxu = ixlo + (sa >> 5) - kABias;
           if (!(jxu > ixu || (jxu == ixu && j > ki))) continue;
         }
       }
@@ -113,10 +129,8 @@ __device__ __forceinline__ void warp_flush(WarpStageT<HALF> &S, int &qn, int &nr
       bool accept = r2c < lo2;
       if (!(r2c < lo)) nre++;
       if (!accept && r2c < hi2) {
-        const int meta = __float_as_int(R.w);
-        const int kyz = __float_as_int(S.rows[meta & 31][2].y);
-        const int kx = floordiv_dev((meta >> 5) - kMetaBias, g->nc[0]);
-        const int ky = (short)(kyz & 0xffff), kz = kyz >> 16;
+        int kx, ky, kz;
+        slot_image(S, slot, ixlo, g->nc[0], kx, ky, kz);
         if (RECORD)
           accept = guard_band_accept(g, q, __float_as_int(pi.w), __float_as_int(pos[j].w), kx, ky, kz);
         else
@@ -134,11 +148,10 @@ __device__ __forceinline__ void warp_flush(WarpStageT<HALF> &S, int &qn, int &nr
           acc.add_r2(pp, cx, cy, cz, r2c);
         }
         if (RECORD) {
-          const int meta = __float_as_int(R.w);
-          const int kyz = __float_as_int(S.rows[meta & 31][2].y);
-          record_pair(g, q, __float_as_int(pi.w), __float_as_int(pos[j].w),
-                      floordiv_dev((meta >> 5) - kMetaBias, g->nc[0]), (short)(kyz & 0xffff), kyz >> 16, pair_buf,
-                      pair_count, pair_cap);
+          int kx, ky, kz;
+          slot_image(S, slot, ixlo, g->nc[0], kx, ky, kz);
+          record_pair(g, q, __float_as_int(pi.w), __float_as_int(pos[j].w), kx, ky, kz, pair_buf, pair_count,
+                      pair_cap);
         }
       }
     }
@@ -158,7 +171,7 @@ __device__ __forceinline__ void flush_partners(WarpStageT<HALF> &S, int fill, in
     for (int t = lane; t < fill; t += 32) {
       const float fx = S.Fj[0][t], fy = S.Fj[HALF ? 1 : 0][t], fz = S.Fj[HALF ? 2 : 0][t];
       if (fx != 0.f || fy != 0.f || fz != 0.f) {
-        const int oj = __float_as_int(pos[__float_as_int(S.X[t].w)].w);
+        const int oj = __float_as_int(pos[__float_as_int(S.R[t].w)].w);
         atomicAdd(&F[3 * (size_t)oj], Qm[0] * fx + Qm[1] * fy + Qm[2] * fz);
         atomicAdd(&F[3 * (size_t)oj + 1], Qm[3] * fx + Qm[4] * fy + Qm[5] * fz);
         atomicAdd(&F[3 * (size_t)oj + 2], Qm[6] * fx + Qm[7] * fy + Qm[8] * fz);
@@ -234,7 +247,18 @@ __device__ __forceinline__ void warp_chunk(const int4 cd, const Row *__restrict_
   if (HALF)
     for (int r = 0; r < nr; r++)
       if (__float_as_int(S.rows[r][2].w) == 0) rhome = r;
-  const float hil = act ? g->rc2_hi : -1.0f;  // an inactive lane accepts nothing
+  // Coarse test in dot-product form: r^2 = |X_i|^2 + |X_j|^2 - 2 X_i . X_j, so a
+  // test is three fused multiply-adds on the staged (X_j, |X_j|^2) against
+  // thr = rc2_hi - |X_i|^2 + margin.  Every candidate with exact quantised r^2
+  // below rc2_hi has |X_j| <= |X_i| + rc + 1, and for such candidates the
+  // roundings (of |X_j|^2, the three products, |X_i|^2 and thr) stay below
+  // 10 u (2 |X_i| + rc + 1)^2, u = 2^-24: the margin, so no partner is lost.
+  // Candidates accepted only through the margin are rejected by the flush's
+  // corrected distance, so the pair set is unchanged.
+  const float n2i = fmaf(Xi.z, Xi.z, fmaf(Xi.y, Xi.y, Xi.x * Xi.x));
+  const float mxi = -2.0f * Xi.x, myi = -2.0f * Xi.y, mzi = -2.0f * Xi.z;
+  const float ebound = 2.0f * (fabsf(Xi.x) + fabsf(Xi.y) + fabsf(Xi.z)) + sqrtf(g->rc2_hi) + 1.0f;
+  const float thr = act ? (g->rc2_hi - n2i) + 5.9604645e-7f * ebound * ebound : -1e30f;  // inactive: accepts nothing
   acc.fx = acc.fy = acc.fz = 0.f;
   int qn = 0, fill = 0;
   // extent of the lanes along the row (cell units from the chunk's first cell):
@@ -276,7 +300,7 @@ __device__ __forceinline__ void warp_chunk(const int4 cd, const Row *__restrict_
     const int cbase = __float_as_int(s0.w), dxlo = __float_as_int(s1.w);
     const int sxi = __float_as_int(s2.z);
     const RowWindow w = row_window(s0, s1, s2, ixlo, ixhi, l1, kx0, ky0, kz0, pmin, pmax, reach1);
-    const int ufirst = w.ufirst, ulast = w.ulast, ulo = w.ulo;
+    const int ufirst = w.ufirst, ulast = w.ulast;
     int jx = w.jx;
     // runs of consecutive cells without an x-wrap: contiguous particles
     for (int u = ufirst, run = 0; u <= ulast; run++) {
@@ -284,11 +308,10 @@ __device__ __forceinline__ void warp_chunk(const int4 cd, const Row *__restrict_
       const int b = run == 0 ? pb0 : (run == 1 ? pb1 : start[cbase + jx]);
       const int e = run == 0 ? pe0 : (run == 1 ? pe1 : start[cbase + jx + len]);
       const int arun = dxlo + sxi + u - jx;  // A of a particle of cell jx' of this run: arun + jx'
-      const int meta_run = r + ((ulo + u - jx + kMetaBias) << 5);
       if (act) ncand += e - b;
       for (int p = b; p < e;) {
         if (fill == kStage) {
-          warp_flush<RECORD, HALF>(S, qn, nre, lane, ki, pi, Xi, Ri, ixu, rhome, g, pos, pp, acc, q, pair_buf,
+          warp_flush<RECORD, HALF>(S, qn, nre, lane, ki, pi, Xi, Ri, ixu, ixlo, rhome, g, pos, pp, acc, q, pair_buf,
                                    pair_count, pair_cap, rlist, rcount, err);
           flush_partners<HALF>(S, fill, lane, g, pos, F);
           fill = 0;
@@ -311,10 +334,11 @@ __device__ __forceinline__ void warp_chunk(const int4 cd, const Row *__restrict_
             const float4 pj = h ? pj1 : pj0, pjr = h ? pjr1 : pjr0;
             const int cjx = (h ? c1 : c0) - cbase;
             const float A = (float)(arun + cjx);
-            S.X[fill + t] = make_float4(fmaf(A, sx, pj.x + s0.x), fmaf(A, sy, pj.y + s0.y),
-                                        fmaf(A, sz, pj.z + s0.z), __int_as_float(j));
+            const float xx = fmaf(A, sx, pj.x + s0.x), xy = fmaf(A, sy, pj.y + s0.y), xz = fmaf(A, sz, pj.z + s0.z);
+            S.X[fill + t] = make_float4(xx, xy, xz, fmaf(xz, xz, fmaf(xy, xy, xx * xx)));
             S.R[fill + t] = make_float4(fmaf(A, srx, pjr.x + s1.x), fmaf(A, sry, pjr.y + s1.y),
-                                        fmaf(A, srz, pjr.z + s1.z), __int_as_float(meta_run + (cjx << 5)));
+                                        fmaf(A, srz, pjr.z + s1.z), __int_as_float(j));
+            S.SA[fill + t] = (unsigned short)(r | ((arun + cjx + kABias) << 5));
             if (HALF) {
               S.Fj[0][fill + t] = 0.f;
               S.Fj[HALF ? 1 : 0][fill + t] = 0.f;
@@ -326,14 +350,13 @@ __device__ __forceinline__ void warp_chunk(const int4 cd, const Row *__restrict_
         for (int k0 = fill; k0 < fill + take; k0 += kTestBlock) {
           const int k1 = min(fill + take, k0 + kTestBlock);
           if (__any_sync(FULL, qn > kWarpQueue - kTestBlock))
-            warp_flush<RECORD, HALF>(S, qn, nre, lane, ki, pi, Xi, Ri, ixu, rhome, g, pos, pp, acc, q, pair_buf,
+            warp_flush<RECORD, HALF>(S, qn, nre, lane, ki, pi, Xi, Ri, ixu, ixlo, rhome, g, pos, pp, acc, q, pair_buf,
                                      pair_count, pair_cap, rlist, rcount, err);
 #define NEMD_TEST(P, K)                                                       \
   {                                                                           \
-    const float ddx = (P).x - Xi.x, ddy = (P).y - Xi.y, ddz = (P).z - Xi.z;   \
-    const float r2 = fmaf(ddz, ddz, fmaf(ddy, ddy, ddx * ddx));               \
+    const float t = fmaf(mxi, (P).x, fmaf(myi, (P).y, fmaf(mzi, (P).z, (P).w))); \
     S.q[qn][lane] = (typename WarpStageT<HALF>::Entry)(K);                    \
-    qn += (r2 < hil) ? 1 : 0;                                                 \
+    qn += (t < thr) ? 1 : 0;                                                  \
   }
           int k = k0;
           for (; k + 4 <= k1; k += 4) {
@@ -357,7 +380,7 @@ __device__ __forceinline__ void warp_chunk(const int4 cd, const Row *__restrict_
       if (jx == l1) jx = 0;
     }
   }
-  warp_flush<RECORD, HALF>(S, qn, nre, lane, ki, pi, Xi, Ri, ixu, rhome, g, pos, pp, acc, q, pair_buf, pair_count,
+  warp_flush<RECORD, HALF>(S, qn, nre, lane, ki, pi, Xi, Ri, ixu, ixlo, rhome, g, pos, pp, acc, q, pair_buf, pair_count,
                            pair_cap, rlist, rcount, err);
   flush_partners<HALF>(S, fill, lane, g, pos, F);
 }
