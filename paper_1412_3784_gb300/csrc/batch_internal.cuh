@@ -74,6 +74,9 @@ cudaError_t launch_batch_stencil(cudaStream_t st, const BatchView &v, int max_cl
 cudaError_t launch_batch_bin(cudaStream_t st, const BatchView &v, int sms);
 // bin.cu: exclusive scan of in[0..len) into out[0..len], out[len] = total
 cudaError_t launch_fixed_scan(cudaStream_t st, const int *in, int *out, int *tiles, int len);
+// One block: exclusive scan of the per-class chunk counts (c2 c3 classes from
+// the grid), total at out[cap].
+cudaError_t launch_class_scan(nemd_ctx *c, const int *in, int *out, int cap);
 // force_chunk.cu: per-class chunk counts, their scan, the chunk list
 cudaError_t launch_batch_chunks(cudaStream_t st, const BatchView &v, int sms);
 // force_warp.cu: the persistent force kernel over every chunk of every system

@@ -262,6 +262,42 @@ cudaError_t launch_bin(nemd_ctx *c) {
 }
 
 
+// ---- one-block scan of the per-class chunk counts ----
+// out[0..ncls) exclusive prefix sums of in[0..ncls), ncls = c2 c3 classes read
+// from the grid (0 after a box or capacity error), and the total at out[cap],
+// where the force kernels read the number of chunks.
+__global__ void __launch_bounds__(kScanThreads) k_fscan_classes(const Geo *g, const int *__restrict__ in,
+                                                                int *__restrict__ out, int cap) {
+  __shared__ int sh[32];
+  const bool ok = !(g->error & (ERRB_BOX | ERRB_CAPACITY));
+  const int len = ok ? g->nc[1] * g->nc[2] : 0;
+  int carry = 0;
+  for (int base = 0; base < len; base += kScanTile) {
+    int v[kScanItems];
+    int sum = 0;
+    for (int k = 0; k < kScanItems; k++) {
+      const int idx = base + threadIdx.x * kScanItems + k;
+      v[k] = (idx < len) ? in[idx] : 0;
+      sum += v[k];
+    }
+    int total;
+    int ex = block_exclusive_scan(sum, sh, total) + carry;
+    for (int k = 0; k < kScanItems; k++) {
+      const int idx = base + threadIdx.x * kScanItems + k;
+      if (idx < len) out[idx] = ex;
+      ex += v[k];
+    }
+    carry += total;
+  }
+  if (threadIdx.x == 0) out[cap] = carry;
+}
+
+cudaError_t launch_class_scan(nemd_ctx *c, const int *in, int *out, int cap) {
+  k_fscan_classes<<<1, kScanThreads, 0, c->stream>>>(c->geo, in, out, cap);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
 // ---- fixed-length scan: out[0..len) exclusive, out[len] = total ----
 static_assert(kFixedScanTile == kScanTile, "scan tile");
 

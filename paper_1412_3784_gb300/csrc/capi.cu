@@ -103,7 +103,6 @@ int ensure_cells(nemd_ctx *c, int64_t cells, int kfac) {
   if ((r = grow(c, &c->rows, cap * stride, "rows"))) return r;
   if ((r = grow(c, &c->chunk_cnt, cap + 1, "chunk counts"))) return r;
   if ((r = grow(c, &c->chunk_off, cap + 1, "chunk offsets"))) return r;
-  if ((r = grow(c, &c->chunk_tiles, cap / 4096 + 2, "chunk scan tiles"))) return r;
   c->cap_cells = cap;
   c->cap_rows = cap * stride;
   return NEMD_OK;
@@ -229,12 +228,12 @@ int nemd_create(nemd_ctx **out, int device, void *stream) {
 int nemd_destroy(nemd_ctx *c) {
   if (!c) return NEMD_OK;
   cudaSetDevice(c->device);
-  if (c->stream || true) cudaStreamSynchronize(c->stream);
+  cudaStreamSynchronize(c->stream);
   if (c->model) cudaFree(c->model);
   void *ptrs[] = {c->geo,  c->q_copy, c->relc,     c->relr, c->posr, c->rank,     c->count,    c->start, c->chunks, c->nchunks, c->recheck, c->nrecheck,
                   c->block_sums, c->perm, c->pos4, c->cell_sorted, c->rows, c->rowcnt,
                   c->partials, c->uw_out, c->f_dev, c->pair_buf, c->pair_count, c->counters,
-                  c->chunk_cnt, c->chunk_off, c->chunk_tiles};
+                  c->chunk_cnt, c->chunk_off};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->copy_stream) {

@@ -160,16 +160,74 @@ __global__ void __launch_bounds__(NT) k_force_plain(const Geo *__restrict__ g, c
   block_reduce_store<NT>(v, partials);
 }
 
+// One block: sums the per-block partials in a fixed order (deterministic),
+// halves the full-neighbourhood double count, rotates the virial of the
+// dynamic offset frame back to Cartesian (W = Q W_R Q^T) and publishes
+// U, W and the counters.
+__device__ __forceinline__ void reduce_final_body(Geo *__restrict__ g, const double *__restrict__ partials,
+                                                  int nblocks, int frame_is_cartesian, double *__restrict__ uw,
+                                                  unsigned long long *__restrict__ counters, double hf,
+                                                  double (*sh)[kPartials]) {
+  double acc[kPartials];
+#pragma unroll
+  for (int k = 0; k < kPartials; k++) acc[k] = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < kPartials; k++) acc[k] += __ldcg(&partials[(size_t)b * kPartials + k]);
+#pragma unroll
+  for (int k = 0; k < kPartials; k++) sh[threadIdx.x][k] = acc[k];
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s)
+#pragma unroll
+      for (int k = 0; k < kPartials; k++) sh[threadIdx.x][k] += sh[threadIdx.x + s][k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const bool ok = !(g->error & (ERRB_BOX | ERRB_CAPACITY));
+    // hf: 1/2 for full neighbourhoods (every pair met from both sides), 1 for half
+    double U = hf * sh[0][0];
+    double Wr[9];
+    Wr[0] = hf * sh[0][1];
+    Wr[4] = hf * sh[0][2];
+    Wr[8] = hf * sh[0][3];
+    Wr[1] = Wr[3] = hf * sh[0][4];
+    Wr[2] = Wr[6] = hf * sh[0][5];
+    Wr[5] = Wr[7] = hf * sh[0][6];
+    double W[9];
+    if (!frame_is_cartesian && g->variant == NEMD_DO) {
+      double T9[9];
+      const double *Q = g->Q;
+      for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) T9[3 * a + b] = Q[3 * a] * Wr[b] + Q[3 * a + 1] * Wr[3 + b] + Q[3 * a + 2] * Wr[6 + b];
+      for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++)
+          W[3 * a + b] = T9[3 * a] * Q[3 * b] + T9[3 * a + 1] * Q[3 * b + 1] + T9[3 * a + 2] * Q[3 * b + 2];
+    } else {
+      for (int k = 0; k < 9; k++) W[k] = Wr[k];
+    }
+    uw[0] = ok ? U : 0.0;
+    for (int k = 0; k < 9; k++) uw[1 + k] = ok ? W[k] : 0.0;
+    counters[0] = (unsigned long long)(hf * sh[0][7] + 0.25);
+    counters[1] = (unsigned long long)(sh[0][8] + 0.5);
+    counters[2] = (unsigned long long)(sh[0][9] + 0.5);
+    g->sticky |= g->error;
+  }
+}
+
 // Float64 fix-up of the candidates the force kernels left within float32
 // rounding of rc: the canonical decision (Sec. 2 images, strict r < rc), and for
 // each accepted pair the force on i (added to F, Cartesian), half of u and of
 // r (x) f (the other half comes from the pair's other orientation, which the
 // full neighbourhood also defers), written as one more block of partials per
 // block in the variant's frame.  Runs after the force kernel.
-__global__ void k_recheck_fixup(const Geo *__restrict__ g, const int4 *__restrict__ list,
-                                const int *__restrict__ count, const float4 *__restrict__ pos,
-                                const double *__restrict__ q, Pot pp, float *__restrict__ F,
-                                double *__restrict__ partial_slot, int half) {
+__global__ void __launch_bounds__(256) k_recheck_fixup(Geo *__restrict__ g, const int4 *__restrict__ list,
+                                                       const int *__restrict__ count, const float4 *__restrict__ pos,
+                                                       const double *__restrict__ q, Pot pp, float *__restrict__ F,
+                                                       double *__restrict__ partials, int nforce, int half,
+                                                       int frame_is_cartesian, double *__restrict__ uw,
+                                                       unsigned long long *__restrict__ counters) {
+  double *partial_slot = partials + (size_t)nforce * kPartials;
   double v[kPartials];
   for (int k = 0; k < kPartials; k++) v[k] = 0.0;
   const int n = min(*count, kRecheckCap);
@@ -215,61 +273,18 @@ __global__ void k_recheck_fixup(const Geo *__restrict__ g, const int4 *__restric
   }
   if (threadIdx.x < kPartials)
     partial_slot[(size_t)blockIdx.x * kPartials + threadIdx.x] = (threadIdx.x < 8) ? sh[0][threadIdx.x] : 0.0;
-}
-
-// Single block: sums the per-block partials in a fixed order (deterministic),
-// halves the full-neighbourhood double count, rotates the virial of the
-// dynamic offset frame back to Cartesian (W = Q W_R Q^T) and publishes
-// U, W and the counters.
-__global__ void k_reduce_final(Geo *__restrict__ g, const double *__restrict__ partials, int nblocks,
-                               int frame_is_cartesian, double *__restrict__ uw,
-                               unsigned long long *__restrict__ counters, double hf) {
-  __shared__ double sh[256][kPartials];
-  double acc[kPartials];
-#pragma unroll
-  for (int k = 0; k < kPartials; k++) acc[k] = 0.0;
-  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
-#pragma unroll
-    for (int k = 0; k < kPartials; k++) acc[k] += partials[(size_t)b * kPartials + k];
-#pragma unroll
-  for (int k = 0; k < kPartials; k++) sh[threadIdx.x][k] = acc[k];
+  // The last block to finish (ticket in counters[3], returned to zero) sums
+  // every block's partials in a fixed order (deterministic) and publishes U, W
+  // and the counters.
+  __shared__ bool last;
+  __threadfence();
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s)
-#pragma unroll
-      for (int k = 0; k < kPartials; k++) sh[threadIdx.x][k] += sh[threadIdx.x + s][k];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    const bool ok = !(g->error & (ERRB_BOX | ERRB_CAPACITY));
-    // hf: 1/2 for full neighbourhoods (every pair met from both sides), 1 for half
-    double U = hf * sh[0][0];
-    double Wr[9];
-    Wr[0] = hf * sh[0][1];
-    Wr[4] = hf * sh[0][2];
-    Wr[8] = hf * sh[0][3];
-    Wr[1] = Wr[3] = hf * sh[0][4];
-    Wr[2] = Wr[6] = hf * sh[0][5];
-    Wr[5] = Wr[7] = hf * sh[0][6];
-    double W[9];
-    if (!frame_is_cartesian && g->variant == NEMD_DO) {
-      double T9[9];
-      const double *Q = g->Q;
-      for (int a = 0; a < 3; a++)
-        for (int b = 0; b < 3; b++) T9[3 * a + b] = Q[3 * a] * Wr[b] + Q[3 * a + 1] * Wr[3 + b] + Q[3 * a + 2] * Wr[6 + b];
-      for (int a = 0; a < 3; a++)
-        for (int b = 0; b < 3; b++)
-          W[3 * a + b] = T9[3 * a] * Q[3 * b] + T9[3 * a + 1] * Q[3 * b + 1] + T9[3 * a + 2] * Q[3 * b + 2];
-    } else {
-      for (int k = 0; k < 9; k++) W[k] = Wr[k];
-    }
-    uw[0] = ok ? U : 0.0;
-    for (int k = 0; k < 9; k++) uw[1 + k] = ok ? W[k] : 0.0;
-    counters[0] = (unsigned long long)(hf * sh[0][7] + 0.25);
-    counters[1] = (unsigned long long)(sh[0][8] + 0.5);
-    counters[2] = (unsigned long long)(sh[0][9] + 0.5);
-    g->sticky |= g->error;
-  }
+  if (threadIdx.x == 0) last = atomicAdd(&counters[3], 1ull) == (unsigned long long)(gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  reduce_final_body(g, partials, nforce + (int)gridDim.x, frame_is_cartesian, uw, counters, half ? 1.0 : 0.5, sh);
+  if (threadIdx.x == 0) counters[3] = 0ull;
 }
 
 Pot make_pot(const nemd_ctx *c) {
@@ -292,12 +307,6 @@ Pot make_pot(const nemd_ctx *c) {
   return p;
 }
 
-cudaError_t launch_reduce(nemd_ctx *c, int nblocks, int frame_is_cartesian, double *UW_dev, bool half) {
-  k_reduce_final<<<1, 256, 0, c->stream>>>(c->geo, c->partials, nblocks, frame_is_cartesian, UW_dev, c->counters,
-                                           half ? 1.0 : 0.5);
-  c->launches += 1;
-  return cudaGetLastError();
-}
 
 template <int NT>
 static void launch_plain(nemd_ctx *c, int nblocks, Pot pp, float *F) {
@@ -366,9 +375,10 @@ cudaError_t launch_forces(nemd_ctx *c, float *F_dev, double *UW_dev) {
   int nfix = kFixupBlocks;
   if (nblocks + nfix > c->cap_partials) nfix = (int)(c->cap_partials - nblocks);
   k_recheck_fixup<<<nfix, 256, 0, c->stream>>>(c->geo, c->recheck, c->nrecheck, c->pos4, c->q_dev, make_pot(c),
-                                               F_dev, c->partials + (size_t)nblocks * kPartials, half ? 1 : 0);
+                                               F_dev, c->partials, nblocks, half ? 1 : 0, c->precise ? 1 : 0, UW_dev,
+                                               c->counters);
   c->launches += 1;
-  return launch_reduce(c, nblocks + nfix, c->precise ? 1 : 0, UW_dev, half);
+  return cudaGetLastError();
 }
 
 

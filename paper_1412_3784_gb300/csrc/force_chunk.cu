@@ -86,13 +86,11 @@ __device__ __forceinline__ void chunk_walk_warp(const int *__restrict__ start, i
 
 __global__ void __launch_bounds__(32 * kWalkWarps) k_chunk_count(const Geo *__restrict__ g,
                                                                  const int *__restrict__ start,
-                                                                 int *__restrict__ cnt, int gs, int cap) {
+                                                                 int *__restrict__ cnt, int gs) {
   __shared__ int sm[kWalkWarps][kWalkCells + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool ok = !(g->error & (ERRB_BOX | ERRB_CAPACITY));
   const int l1 = g->nc[0], ncls = ok ? g->nc[1] * g->nc[2] : 0;
-  // unused class slots count no chunks
-  for (int k = ncls + blockIdx.x * blockDim.x + threadIdx.x; k < cap; k += gridDim.x * blockDim.x) cnt[k] = 0;
   const int nw = gridDim.x * kWalkWarps;
   for (int cls = blockIdx.x * kWalkWarps + warp; cls < ncls; cls += nw) {
     int n = 0;
@@ -280,11 +278,11 @@ cudaError_t launch_chunk_build(nemd_ctx *c, int gs) {
   int64_t blocks = (c->cap_cells + kWalkWarps - 1) / kWalkWarps;
   if (blocks > 16 * (int64_t)c->sms) blocks = 16 * (int64_t)c->sms;
   if (blocks < 1) blocks = 1;
-  k_chunk_count<<<(int)blocks, 32 * kWalkWarps, 0, c->stream>>>(c->geo, c->start, c->chunk_cnt, gs, cap);
-  cudaError_t e = launch_fixed_scan(c->stream, c->chunk_cnt, c->chunk_off, c->chunk_tiles, cap);
+  k_chunk_count<<<(int)blocks, 32 * kWalkWarps, 0, c->stream>>>(c->geo, c->start, c->chunk_cnt, gs);
+  cudaError_t e = launch_class_scan(c, c->chunk_cnt, c->chunk_off, cap);
   if (e != cudaSuccess) return e;
   k_chunk_write<<<(int)blocks, 32 * kWalkWarps, 0, c->stream>>>(c->geo, c->start, c->chunk_off, c->chunks, gs);
-  c->launches += 5;
+  c->launches += 2;
   return cudaGetLastError();
 }
 

@@ -17,7 +17,6 @@ Pot make_pot(const nemd_ctx *c);
 
 // FP64 reductions of the per-block partials (force.cu); half: the partials hold
 // every unordered pair once (half neighbourhoods) instead of twice.
-cudaError_t launch_reduce(nemd_ctx *c, int nblocks, int frame_is_cartesian, double *UW_dev, bool half = false);
 
 // Per-block sums of the per-thread values (float64, fixed order within the
 // block) -> partials[blockIdx.x * kPartials + k].

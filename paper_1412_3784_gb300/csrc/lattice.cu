@@ -99,8 +99,9 @@ __device__ __forceinline__ void lattice_body(Geo *g, const LatIn &in) {
       double cs = fabs(B[j]) + fabs(B[3 + j]) + fabs(B[6 + j]);
       nrm = fmax(nrm, cs);
     }
+    // smallest s with 8 nrm <= 2^s (from the exponent: 8 nrm = f 2^e, f in [1/2, 1))
     int s = 0;
-    if (nrm > 0.125) s = (int)ceil(log2(nrm * 8.0));
+    if (nrm > 0.125) frexp(nrm * 8.0, &s);
     sh_s = s;
   }
   __syncwarp();
@@ -109,12 +110,16 @@ __device__ __forceinline__ void lattice_body(Geo *g, const LatIn &in) {
   __syncwarp();
 
   // Taylor polynomial of degree 12 by Horner: P = I + B/12, P = I + B P / k ...
+  // (1/k as constants: a float64 division costs many float64 operations here)
   const int deg = 12;
-  if (lane < 9) P[lane] = ((lane % 4) == 0 ? 1.0 : 0.0) + B[lane] / (double)deg;
+  const double inv_k[deg + 1] = {0.0,       1.0,       1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5, 1.0 / 6,
+                                 1.0 / 7,   1.0 / 8,   1.0 / 9,  1.0 / 10, 1.0 / 11, 1.0 / 12};
+  if (lane < 9) P[lane] = ((lane % 4) == 0 ? 1.0 : 0.0) + B[lane] * inv_k[deg];
   __syncwarp();
+#pragma unroll
   for (int k = deg - 1; k >= 1; k--) {
     mm3(B, P, P, lane);
-    if (lane < 9) P[lane] = ((lane % 4) == 0 ? 1.0 : 0.0) + P[lane] / (double)k;
+    if (lane < 9) P[lane] = ((lane % 4) == 0 ? 1.0 : 0.0) + P[lane] * inv_k[k];
     __syncwarp();
   }
   for (int k = 0; k < s; k++) mm3(P, P, P, lane);

@@ -202,7 +202,7 @@ struct nemd_ctx {
   // grouped force kernel
   int4 *chunks;
   int *nchunks;
-  int *chunk_cnt, *chunk_off, *chunk_tiles;  // per class slot: chunks, their scan (cap_cells + 1)
+  int *chunk_cnt, *chunk_off;  // per class slot: chunks, their scan (total at [cap_cells])
   int group;
   // candidates left within float32 rounding of rc, decided by the float64 fix-up
   int4 *recheck;
