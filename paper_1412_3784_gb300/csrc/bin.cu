@@ -33,27 +33,45 @@ __device__ __forceinline__ void wrap_body(Geo *g, const double *__restrict__ q, 
     atomicOr(&g->error, ERRB_NONFINITE);
     x = y = z = 0.0;
   }
-  double s[3];
-  frac_wrap(g->Linv, x, y, z, s);
+  // fractional coordinates in float-float (float64 only for the rare particle
+  // within rounding of an integer), the wrapped image exactly the definition's
+  double s64[3];
+  ff sf[3];
+  bool exact;
+  float tol[3];
+  frac_wrap_ff(g, x, y, z, sf, s64, exact, tol);
   const int l1 = g->nc[0], l2 = g->nc[1], l3 = g->nc[2];
-  // Everything after the float64 fractional coordinates runs in float-float
-  // (float64 throughput is a small fraction of float32 throughput here); the
-  // position error stays below g->wrap_tol, which the guard bands and the
-  // dynamic offset windows include.
-  const ff sf[3] = {split_unit(s[0]), split_unit(s[1]), split_unit(s[2])};
+  // Everything after the fractional coordinates runs in float-float (float64
+  // throughput is a small fraction of float32 throughput here); the position
+  // error stays below g->wrap_tol, which the guard bands and the dynamic offset
+  // windows include.
   // position relative to the centre of its cell, in the variant's frame:
   // dynamic size: Cartesian, G (u - 1/2) with u = c s - idx the cell-fractional part
-  // (the cell index itself from the float64 product c s);
+  // (the cell index that of the float64 product c s: taken from float-float
+  // unless c s lies within its error bound of a cell face);
   // dynamic offset: the rotated frame, b - (idx + 1/2) w for the brick point b
   int idx[3];
   ff rel[3];
   if (g->variant == NEMD_DS) {
     ff u[3];
     for (int a = 0; a < 3; a++) {
-      int k = __double2int_rd(__dmul_rn(s[a], g->Ginv_scale[a]));
+      const float c = (float)g->nc[a];
+      const ff t = ff_mul_f(sf[a], c);
+      int k;
+      const float r = rintf(t.hi);
+      const float d = __fadd_rn(__fsub_rn(t.hi, r), t.lo);
+      if (!exact && fabsf(d) > 4.0f * c * tol[a]) {
+        k = (int)(d < 0.f ? __fsub_rn(r, 1.f) : r);
+      } else {
+        if (!exact) {
+          frac_wrap(g->Linv, x, y, z, s64);
+          exact = true;
+        }
+        k = __double2int_rd(__dmul_rn(s64[a], g->Ginv_scale[a]));
+      }
       k = min(max(k, 0), g->nc[a] - 1);
       idx[a] = k;
-      u[a] = ff_add(ff_mul_f(sf[a], (float)g->nc[a]), ff{-((float)k + 0.5f), 0.f});
+      u[a] = ff_add(t, ff{-((float)k + 0.5f), 0.f});
     }
     for (int a = 0; a < 3; a++)
       rel[a] = ff_add(ff_add(ff_mul(ff_of(g->Gff[3 * a]), u[0]), ff_mul(ff_of(g->Gff[3 * a + 1]), u[1])),

@@ -166,34 +166,45 @@ __global__ void __launch_bounds__(NT) k_force_plain(const Geo *__restrict__ g, c
 // U, W and the counters.
 __device__ __forceinline__ void reduce_final_body(Geo *__restrict__ g, const double *__restrict__ partials,
                                                   int nblocks, int frame_is_cartesian, double *__restrict__ uw,
-                                                  unsigned long long *__restrict__ counters, double hf,
-                                                  double (*sh)[kPartials]) {
+                                                  unsigned long long *__restrict__ counters, double hf) {
+  constexpr int kW = 256 / 32;
+  __shared__ double shw[kW][kPartials];
   double acc[kPartials];
 #pragma unroll
   for (int k = 0; k < kPartials; k++) acc[k] = 0.0;
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
 #pragma unroll
     for (int k = 0; k < kPartials; k++) acc[k] += __ldcg(&partials[(size_t)b * kPartials + k]);
+  // fixed shuffle tree within each warp, then the warps in order
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int k = 0; k < kPartials; k++) sh[threadIdx.x][k] = acc[k];
+  for (int k = 0; k < kPartials; k++) {
+    double x = acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) shw[warp][k] = x;
+  }
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s)
+  double sh0[kPartials];
+  if (threadIdx.x == 0) {
 #pragma unroll
-      for (int k = 0; k < kPartials; k++) sh[threadIdx.x][k] += sh[threadIdx.x + s][k];
-    __syncthreads();
+    for (int k = 0; k < kPartials; k++) {
+      double x = 0.0;
+      for (int w = 0; w < kW; w++) x += shw[w][k];
+      sh0[k] = x;
+    }
   }
   if (threadIdx.x == 0) {
     const bool ok = !(g->error & (ERRB_BOX | ERRB_CAPACITY));
     // hf: 1/2 for full neighbourhoods (every pair met from both sides), 1 for half
-    double U = hf * sh[0][0];
+    double U = hf * sh0[0];
     double Wr[9];
-    Wr[0] = hf * sh[0][1];
-    Wr[4] = hf * sh[0][2];
-    Wr[8] = hf * sh[0][3];
-    Wr[1] = Wr[3] = hf * sh[0][4];
-    Wr[2] = Wr[6] = hf * sh[0][5];
-    Wr[5] = Wr[7] = hf * sh[0][6];
+    Wr[0] = hf * sh0[1];
+    Wr[4] = hf * sh0[2];
+    Wr[8] = hf * sh0[3];
+    Wr[1] = Wr[3] = hf * sh0[4];
+    Wr[2] = Wr[6] = hf * sh0[5];
+    Wr[5] = Wr[7] = hf * sh0[6];
     double W[9];
     if (!frame_is_cartesian && g->variant == NEMD_DO) {
       double T9[9];
@@ -208,9 +219,9 @@ __device__ __forceinline__ void reduce_final_body(Geo *__restrict__ g, const dou
     }
     uw[0] = ok ? U : 0.0;
     for (int k = 0; k < 9; k++) uw[1 + k] = ok ? W[k] : 0.0;
-    counters[0] = (unsigned long long)(hf * sh[0][7] + 0.25);
-    counters[1] = (unsigned long long)(sh[0][8] + 0.5);
-    counters[2] = (unsigned long long)(sh[0][9] + 0.5);
+    counters[0] = (unsigned long long)(hf * sh0[7] + 0.25);
+    counters[1] = (unsigned long long)(sh0[8] + 0.5);
+    counters[2] = (unsigned long long)(sh0[9] + 0.5);
     g->sticky |= g->error;
   }
 }
@@ -263,16 +274,7 @@ __global__ void __launch_bounds__(256) k_recheck_fixup(Geo *__restrict__ g, cons
     v[6] += fr * df[1] * df[2];
     v[7] += 1.0;
   }
-  __shared__ double sh[256][kPartials];
-  for (int k = 0; k < kPartials; k++) sh[threadIdx.x][k] = v[k];
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s)
-      for (int k = 0; k < kPartials; k++) sh[threadIdx.x][k] += sh[threadIdx.x + s][k];
-    __syncthreads();
-  }
-  if (threadIdx.x < kPartials)
-    partial_slot[(size_t)blockIdx.x * kPartials + threadIdx.x] = (threadIdx.x < 8) ? sh[0][threadIdx.x] : 0.0;
+  block_reduce_store<256>(v, partial_slot);
   // The last block to finish (ticket in counters[3], returned to zero) sums
   // every block's partials in a fixed order (deterministic) and publishes U, W
   // and the counters.
@@ -283,7 +285,7 @@ __global__ void __launch_bounds__(256) k_recheck_fixup(Geo *__restrict__ g, cons
   __syncthreads();
   if (!last) return;
   __threadfence();
-  reduce_final_body(g, partials, nforce + (int)gridDim.x, frame_is_cartesian, uw, counters, half ? 1.0 : 0.5, sh);
+  reduce_final_body(g, partials, nforce + (int)gridDim.x, frame_is_cartesian, uw, counters, half ? 1.0 : 0.5);
   if (threadIdx.x == 0) counters[3] = 0ull;
 }
 

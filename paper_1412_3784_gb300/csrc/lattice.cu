@@ -163,6 +163,7 @@ __device__ __forceinline__ void lattice_body(Geo *g, const LatIn &in) {
   if (lane < 9) {
     g->L[lane] = Ls[lane];
     g->Linv[lane] = cof[lane] / det;
+    g->Linvff[lane] = to_ff2(cof[lane] / det);
   }
   // Gram matrix L^T L for the Cholesky QR
   if (lane < 9) Lt[lane] = Ls[(lane % 3) * 3 + lane / 3];
@@ -265,13 +266,14 @@ __device__ void grid_body(Geo *g, const GridIn &in) {
   float step[3];
   int reach[3];
   int maxrows;
-  // bound on the float-float wrap's position error (it does a few dozen
-  // operations of relative error ~2^-45 on values up to the box's extent):
-  // the dynamic offset windows reach this much further, so a particle binned a
-  // rounding outside its cell still finds every partner
+  // bound on the float-float wrap's position error: fractional coordinates
+  // within 2^-42 (16 + 1) of the definition's, then a few dozen operations of
+  // relative error ~2^-45 on values up to the box's extent; the dynamic offset
+  // windows reach this much further, so a particle binned a rounding outside
+  // its cell still finds every partner
   double lsum = 0.0;
   for (int k = 0; k < 9; k++) lsum += fabs(Ls[k]) + fabs(Rm[k]);
-  const double wtol = ldexp(lsum + 1.0, -38);
+  const double wtol = ldexp(lsum + 1.0, -36);
   g->wrap_tol = wtol;
   const double rce = rc * (1.0 + kMargin) + (variant == NEMD_DS ? 0.0 : 2.0 * wtol);
   if (variant == NEMD_DS) {

@@ -98,6 +98,61 @@ __device__ __forceinline__ ff split_unit(double s) {
   return fast2sum(hi, __fmul_rn(__uint2float_rn(m_lo), scale));
 }
 
+// Float-float split of any double x from its bits (integer operations only):
+// exact to 2^-48 relative for 2^-100 <= |x| < 2^100; below, zero (an error
+// under 2^-100); at or above, ok is cleared (the caller takes float64).
+__device__ __forceinline__ ff split_double(double x, bool &ok) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e < 1023 - 100) return {0.f, 0.f};
+  if (e >= 1023 + 100) {
+    ok = false;
+    return {0.f, 0.f};
+  }
+  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+  const unsigned int m_hi = (unsigned int)(b >> 29) & 0x7fffffu;
+  const float hi = __uint_as_float(sign | ((unsigned int)(e - 1023 + 127) << 23) | m_hi);
+  if (e < 949) return {hi, 0.f};
+  const unsigned int m_lo = (unsigned int)b & 0x1fffffffu;
+  const float lo = __fmul_rn(__uint2float_rn(m_lo), __int_as_float((e - 1075 + 127) << 23));
+  return fast2sum(hi, sign ? -lo : lo);
+}
+
+// Fractional coordinates for binning, s = L^-1 q - floor(L^-1 q), in
+// float-float.  The float64 definition (frac_wrap) is followed exactly: each
+// v_a = (L^-1 q)_a is formed in float-float (within 2^-43 sum_b |L^-1_ab q_b|
+// of the float64 value, itself within 2^-51 of that sum of the exact one), and
+// whenever v_a lies within 2^-42 (sum + 1) of an integer, the sum reaches 16
+// (a position far outside the unit cell), or the inputs are out of range, the
+// particle takes the float64 path instead.  So floor(v_a)
+// is always the float64 definition's, the wrapped image agrees with the
+// canonical one, and s is within tol_a = 2^-42 (sum + 1) of the canonical s.
+// exact reports that the float64 path was taken (s64 then holds the canonical s).
+__device__ __forceinline__ void frac_wrap_ff(const Geo *g, double x, double y, double z, ff sf[3], double s64[3],
+                                             bool &exact, float tol[3]) {
+  bool ok = true;
+  const ff X = split_double(x, ok), Y = split_double(y, ok), Z = split_double(z, ok);
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    const ff l0 = ff_of(g->Linvff[3 * a]), l1 = ff_of(g->Linvff[3 * a + 1]), l2 = ff_of(g->Linvff[3 * a + 2]);
+    const ff v = ff_add(ff_add(ff_mul(l0, X), ff_mul(l1, Y)), ff_mul(l2, Z));
+    const float mag = fmaf(fabsf(l2.hi), fabsf(Z.hi), fmaf(fabsf(l1.hi), fabsf(Y.hi), fabsf(l0.hi) * fabsf(X.hi)));
+    const float r = rintf(v.hi);
+    const float d = __fadd_rn(__fsub_rn(v.hi, r), v.lo);  // v - r: v.hi - r is exact for |v.hi| < 2^22
+    tol[a] = 2.2737368e-13f * (mag * 1.0001f + 1.0f);  // 2^-42 (sum + 1)
+    ok = ok && mag < 16.f && fabsf(d) > tol[a];  // (mag < 16 also bounds |v.hi| for the exact v.hi - r)
+    const float fl = d < 0.f ? __fsub_rn(r, 1.f) : r;
+    sf[a] = ff_add(v, ff{-fl, 0.f});
+  }
+  exact = !ok;
+  if (!ok) {
+    frac_wrap(g->Linv, x, y, z, s64);
+    sf[0] = split_unit(s64[0]);
+    sf[1] = split_unit(s64[1]);
+    sf[2] = split_unit(s64[2]);
+  }
+}
+
 // Rectangular rearrangement of the rotated box (Sec. 4.2) in float-float: the
 // point R s is moved by lattice vectors into the brick [0,r11) x [0,r22) x
 // [0,r33) -- first along z (shifting x and y by the third column of R), then y
@@ -152,9 +207,11 @@ __device__ __forceinline__ double canon_r2(const Geo *g, const double *q, int oi
 // Lattice image of particle oi's brick position relative to its wrapped
 // fractional position (dynamic offset frame), recomputed from q.
 __device__ __forceinline__ void brick_image(const Geo *g, const double *q, int oi, int m[3]) {
-  double s[3];
-  frac_wrap(g->Linv, q[3 * (size_t)oi], q[3 * (size_t)oi + 1], q[3 * (size_t)oi + 2], s);
-  const ff sf[3] = {split_unit(s[0]), split_unit(s[1]), split_unit(s[2])};
+  double s64[3];
+  ff sf[3];
+  bool exact;
+  float tol[3];
+  frac_wrap_ff(g, q[3 * (size_t)oi], q[3 * (size_t)oi + 1], q[3 * (size_t)oi + 2], sf, s64, exact, tol);
   ff b[3];
   brick_wrap_ff(g, sf, b, m);
 }

@@ -157,7 +157,7 @@ def test_edge_cases_small_n():
         assert abs(g["F"][0, 0] - (-du)) < 1e-5 * abs(du)
 
 
-def face_positions(L, rc, faces, rng):
+def face_positions(L, rc, faces, rng, interior=True):
     """Particles on the half-cell grid of one variant's cells (every interior
     face and centre; cell factor 1) with 30 % vacancies, each coordinate moved by 0, +-1 or +-2 units in the
     last place or +-2^-44 of the box: binning decisions at and a rounding either
@@ -178,7 +178,9 @@ def face_positions(L, rc, faces, rng):
     # ~1e-15 relative on its own, so its canonical image (the n of its pairs)
     # may legitimately differ by a lattice vector between the two.
     sr = q @ np.linalg.inv(L).T
-    keep = (np.abs(sr - np.rint(sr)).min(axis=1) > 1e-9) & (rng.random(len(q)) < 0.7)
+    keep = rng.random(len(q)) < 0.7
+    if interior:
+        keep &= np.abs(sr - np.rint(sr)).min(axis=1) > 1e-9
     q = q[keep]                          # (and vacancies: no symmetric cancellation of forces)
     ulp = np.spacing(np.abs(q) + 1e-300)
     kick = rng.choice(np.array([0.0, 1.0, -1.0, 2.0, -2.0]), size=q.shape) * ulp
@@ -205,6 +207,35 @@ def test_particles_on_cell_and_brick_faces(frac, faces, kernel):
     for kfac in (1, 2):
         for v in (DS, DO):
             check_against(w, v, ref, kfac=kfac, kernel=kernel, precise=(kfac == 1))
+
+
+@pytest.mark.parametrize("faces", ["ds", "do"])
+@pytest.mark.parametrize("frac", [0.0, 0.37])
+def test_particles_on_unit_cell_faces(frac, faces):
+    """The same grids including the unit cell's own faces (s = 0 = 1, a few
+    units in the last place either side): the binning takes its float64 path
+    there.  Which image of such a particle is canonical depends on the last
+    bits of L(t), which the two sides compute independently, so the pair
+    images n may differ by lattice vectors; everything else is unique: the
+    (i, j) multiset, forces, energy and virial."""
+    rng = np.random.default_rng(int(frac * 1000) + (19 if faces == "ds" else 73))
+    ser = W.general_series(k=10, seed=9)
+    t = frac * ser.period
+    L = oracle.lattice(ser.A, ser.L0, ser.period, t)["L"]
+    q = face_positions(L, ser.rc, faces, rng, interior=False)
+    w = W.Workload(name="faces", A=ser.A, L0=ser.L0, M=ser.M, T=ser.period, t=t, q=q, kind=W.POT_LJ, rc=ser.rc)
+    ref = oracle.evaluate(w, "brute", want_pairs=True)
+    ij_ref = np.sort(ref.pairs[:, 0].astype(np.int64) * w.n + ref.pairs[:, 1])
+    for kfac in (1, 2):
+        for v in (DS, DO):
+            for kernel in DETERMINISTIC:
+                g = run(w, v, record=True, kfac=kfac, kernel=kernel)
+                assert g["stats"]["pairs"] == ref.npairs
+                ij = np.sort(g["pairs"][:, 0].astype(np.int64) * w.n + g["pairs"][:, 1])
+                assert np.array_equal(ij, ij_ref)
+                g = run(w, v, kfac=kfac, kernel=kernel)
+                assert force_err(g["F"], ref.F) <= F_TOL
+                assert rel(g["U"], ref.U) <= UW_TOL_FAST and mat_rel(g["W"], ref.W) <= UW_TOL_FAST
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
