@@ -60,9 +60,9 @@ C_PAIR = 24    # FP32 instructions per interacting pair (force, energy, virial, 
 # DRAM bytes (read + write) of one k_force_warp launch on the N = 2^20 system,
 # from the ncu capture summarised in profiles/k_force_warp_general_n1m.md; valid
 # only while the kernel's sources are the ones captured (sha1 prefixes).
-WARP_TRAFFIC = {"bytes": 39.440128e6 + 0.731648e6,
-                "sha1": {"paper_1412_3784_gb300/csrc/force_warp.cu": "1ab03e6666f2",
-                         "paper_1412_3784_gb300/csrc/force_common.cuh": "236e2e7e2cf5"}}
+WARP_TRAFFIC = {"bytes": 39.407104e6 + 0.407552e6,
+                "sha1": {"paper_1412_3784_gb300/csrc/force_warp.cu": "e3ccfad894aa",
+                         "paper_1412_3784_gb300/csrc/force_common.cuh": "2c912e007080"}}
 
 
 def warp_traffic():
@@ -797,7 +797,7 @@ def main():
             "metric": "interacting pairs/s per force eval", "value": main_part["value"], "unit": "pairs/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": main_part["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 pair math, f64 lattice/wrap/reductions",
+            "vs_baseline": None, "dtype": "f32 pair math, f64 lattice/guard band/reductions, float-float wrap",
             "data": "synthetic",
         }
         for key in ("config", "plain", "autotune", "roofline", "cpu_baseline", "e2e", "gpu_launches", "clocks"):

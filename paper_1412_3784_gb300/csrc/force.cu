@@ -160,70 +160,41 @@ __global__ void __launch_bounds__(NT) k_force_plain(const Geo *__restrict__ g, c
   block_reduce_store<NT>(v, partials);
 }
 
-// One block: sums the per-block partials in a fixed order (deterministic),
+// Publishes the totals sh0 (the fixed-order sums of every block's partials):
 // halves the full-neighbourhood double count, rotates the virial of the
-// dynamic offset frame back to Cartesian (W = Q W_R Q^T) and publishes
-// U, W and the counters.
-__device__ __forceinline__ void reduce_final_body(Geo *__restrict__ g, const double *__restrict__ partials,
-                                                  int nblocks, int frame_is_cartesian, double *__restrict__ uw,
-                                                  unsigned long long *__restrict__ counters, double hf) {
-  constexpr int kW = 256 / 32;
-  __shared__ double shw[kW][kPartials];
-  double acc[kPartials];
-#pragma unroll
-  for (int k = 0; k < kPartials; k++) acc[k] = 0.0;
-  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
-#pragma unroll
-    for (int k = 0; k < kPartials; k++) acc[k] += __ldcg(&partials[(size_t)b * kPartials + k]);
-  // fixed shuffle tree within each warp, then the warps in order
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < kPartials; k++) {
-    double x = acc[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if (lane == 0) shw[warp][k] = x;
+// dynamic offset frame back to Cartesian (W = Q W_R Q^T), writes U, W and the
+// counters.  One thread.
+__device__ __forceinline__ void publish_uw(Geo *__restrict__ g, const double (&sh0)[kPartials],
+                                          int frame_is_cartesian, double *__restrict__ uw,
+                                          unsigned long long *__restrict__ counters, double hf) {
+  const bool ok = !(g->error & (ERRB_BOX | ERRB_CAPACITY));
+  // hf: 1/2 for full neighbourhoods (every pair met from both sides), 1 for half
+  double U = hf * sh0[0];
+  double Wr[9];
+  Wr[0] = hf * sh0[1];
+  Wr[4] = hf * sh0[2];
+  Wr[8] = hf * sh0[3];
+  Wr[1] = Wr[3] = hf * sh0[4];
+  Wr[2] = Wr[6] = hf * sh0[5];
+  Wr[5] = Wr[7] = hf * sh0[6];
+  double W[9];
+  if (!frame_is_cartesian && g->variant == NEMD_DO) {
+    double T9[9];
+    const double *Q = g->Q;
+    for (int a = 0; a < 3; a++)
+      for (int b = 0; b < 3; b++) T9[3 * a + b] = Q[3 * a] * Wr[b] + Q[3 * a + 1] * Wr[3 + b] + Q[3 * a + 2] * Wr[6 + b];
+    for (int a = 0; a < 3; a++)
+      for (int b = 0; b < 3; b++)
+        W[3 * a + b] = T9[3 * a] * Q[3 * b] + T9[3 * a + 1] * Q[3 * b + 1] + T9[3 * a + 2] * Q[3 * b + 2];
+  } else {
+    for (int k = 0; k < 9; k++) W[k] = Wr[k];
   }
-  __syncthreads();
-  double sh0[kPartials];
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < kPartials; k++) {
-      double x = 0.0;
-      for (int w = 0; w < kW; w++) x += shw[w][k];
-      sh0[k] = x;
-    }
-  }
-  if (threadIdx.x == 0) {
-    const bool ok = !(g->error & (ERRB_BOX | ERRB_CAPACITY));
-    // hf: 1/2 for full neighbourhoods (every pair met from both sides), 1 for half
-    double U = hf * sh0[0];
-    double Wr[9];
-    Wr[0] = hf * sh0[1];
-    Wr[4] = hf * sh0[2];
-    Wr[8] = hf * sh0[3];
-    Wr[1] = Wr[3] = hf * sh0[4];
-    Wr[2] = Wr[6] = hf * sh0[5];
-    Wr[5] = Wr[7] = hf * sh0[6];
-    double W[9];
-    if (!frame_is_cartesian && g->variant == NEMD_DO) {
-      double T9[9];
-      const double *Q = g->Q;
-      for (int a = 0; a < 3; a++)
-        for (int b = 0; b < 3; b++) T9[3 * a + b] = Q[3 * a] * Wr[b] + Q[3 * a + 1] * Wr[3 + b] + Q[3 * a + 2] * Wr[6 + b];
-      for (int a = 0; a < 3; a++)
-        for (int b = 0; b < 3; b++)
-          W[3 * a + b] = T9[3 * a] * Q[3 * b] + T9[3 * a + 1] * Q[3 * b + 1] + T9[3 * a + 2] * Q[3 * b + 2];
-    } else {
-      for (int k = 0; k < 9; k++) W[k] = Wr[k];
-    }
-    uw[0] = ok ? U : 0.0;
-    for (int k = 0; k < 9; k++) uw[1 + k] = ok ? W[k] : 0.0;
-    counters[0] = (unsigned long long)(hf * sh0[7] + 0.25);
-    counters[1] = (unsigned long long)(sh0[8] + 0.5);
-    counters[2] = (unsigned long long)(sh0[9] + 0.5);
-    g->sticky |= g->error;
-  }
+  uw[0] = ok ? U : 0.0;
+  for (int k = 0; k < 9; k++) uw[1 + k] = ok ? W[k] : 0.0;
+  counters[0] = (unsigned long long)(hf * sh0[7] + 0.25);
+  counters[1] = (unsigned long long)(sh0[8] + 0.5);
+  counters[2] = (unsigned long long)(sh0[9] + 0.5);
+  g->sticky |= g->error;
 }
 
 // Float64 fix-up of the candidates the force kernels left within float32
@@ -243,7 +214,11 @@ __global__ void __launch_bounds__(256) k_recheck_fixup(Geo *__restrict__ g, cons
   for (int k = 0; k < kPartials; k++) v[k] = 0.0;
   const int n = min(*count, kRecheckCap);
   const bool ok = !(g->error & (ERRB_BOX | ERRB_CAPACITY));
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; ok && e < n; e += gridDim.x * blockDim.x) {
+  // entries dealt round robin over the blocks, so that their float64 work
+  // (a small fraction of the float32 rate here) spreads over as many SMs
+  bool has = false;
+  for (int e = blockIdx.x + gridDim.x * threadIdx.x; ok && e < n; e += gridDim.x * blockDim.x) {
+    has = true;
     const int4 it = list[e];
     const int oi = __float_as_int(pos[it.x].w), oj = __float_as_int(pos[it.y].w);
     const int ky = (short)(it.w & 0xffff), kz = it.w >> 16;
@@ -274,19 +249,59 @@ __global__ void __launch_bounds__(256) k_recheck_fixup(Geo *__restrict__ g, cons
     v[6] += fr * df[1] * df[2];
     v[7] += 1.0;
   }
-  block_reduce_store<256>(v, partial_slot);
-  // The last block to finish (ticket in counters[3], returned to zero) sums
-  // every block's partials in a fixed order (deterministic) and publishes U, W
-  // and the counters.
+  // Block sum, in a fixed order: the warps' entry sums, then this block's slice
+  // of the force kernel's partials (rows b, b + G, b + 2G, ..., G = gridDim.x;
+  // thread t < 10 P sums value t % 10 of slice rows p, p + P, ... with p = t / 10).
+  constexpr int P = 24;
+  __shared__ double shw[256 / 32][kPartials];
+  __shared__ double shp[P][kPartials];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool any = __any_sync(0xffffffffu, has);
+#pragma unroll
+  for (int k = 0; k < kPartials; k++) {
+    double x = v[k];
+    if (any) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    }
+    if (lane == 0) shw[warp][k] = any ? x : 0.0;
+  }
+  if (threadIdx.x < P * kPartials) {
+    const int k = threadIdx.x % kPartials, pp0 = threadIdx.x / kPartials;
+    const int G = gridDim.x;
+    double x = 0.0;
+    for (int r = blockIdx.x + G * pp0; r < nforce; r += G * P) x += __ldcg(&partials[(size_t)r * kPartials + k]);
+    shp[pp0][k] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < kPartials) {
+    double x = 0.0;
+    for (int w = 0; w < 256 / 32; w++) x += shw[w][threadIdx.x];
+    for (int p = 0; p < P; p++) x += shp[p][threadIdx.x];
+    partial_slot[(size_t)blockIdx.x * kPartials + threadIdx.x] = x;
+  }
+  // The last block to finish (ticket in counters[3], returned to zero) adds the
+  // blocks' sums in block order and publishes U, W and the counters.
   __shared__ bool last;
+  __shared__ double tot[kPartials];
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) last = atomicAdd(&counters[3], 1ull) == (unsigned long long)(gridDim.x - 1);
   __syncthreads();
   if (!last) return;
   __threadfence();
-  reduce_final_body(g, partials, nforce + (int)gridDim.x, frame_is_cartesian, uw, counters, half ? 1.0 : 0.5);
-  if (threadIdx.x == 0) counters[3] = 0ull;
+  if (threadIdx.x < kPartials) {
+    double x = 0.0;
+    for (int b = 0; b < (int)gridDim.x; b++) x += __ldcg(&partial_slot[(size_t)b * kPartials + threadIdx.x]);
+    tot[threadIdx.x] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sh0[kPartials];
+    for (int k = 0; k < kPartials; k++) sh0[k] = tot[k];
+    publish_uw(g, sh0, frame_is_cartesian, uw, counters, half ? 1.0 : 0.5);
+    counters[3] = 0ull;
+  }
 }
 
 Pot make_pot(const nemd_ctx *c) {
