@@ -22,12 +22,15 @@ Printed as one JSON line (rank 0):
                CUDA graph, autotuned cell factor and tile; against a loop of
                per-system contexts with the plain kernel
   learned      the learned cell-list selector, trained on timings of the
-               N = 32000 planar, N = 256000 general and 256 batched systems, driving
-               the N = 2,097,152 general-flow system: regret against the
-               exhaustive choice, pairs/s against the plain fixed variants
+               N = 32000 planar, N = 256000 and 2^20 general and 256 batched
+               systems, driving the N = 2,097,152 general-flow system: regret
+               against the exhaustive choice, pairs/s against the plain variants
   shear        Lees-Edwards shear remapped half way through the period, N = 2^20:
                tuned against plain cell lists
   equilibrium  the N = 2^20 system at rest (A = 0), 16 perturbed cubes per step
+  integrate    time integration under the flow (nemd_integrate): 1728 WCA
+               particles for 10,000 steps (the paper's runtime comparison of the
+               two cell lists) and the N = 2^20 LJ system for 50 steps
 
 --impl reference times the oracle (the reference arm of this project) on the
 same workload, one strain per step.
@@ -89,7 +92,7 @@ def parse():
     p.add_argument("--kernel", type=int, default=2, help="force kernel without autotuning (0 plain, 1 grouped, 2 warp)")
     p.add_argument("--group", type=int, default=16, help="lanes per group of the grouped kernel")
     p.add_argument("--kfac", type=int, default=1, help="cell-size factor without autotuning")
-    p.add_argument("--sections", default="main,batched,learned,shear,equilibrium",
+    p.add_argument("--sections", default="main,batched,learned,shear,equilibrium,integrate",
                    help="comma list of main, batched, learned, shear, equilibrium")
     p.add_argument("--batch-steps", type=int, default=10)
     p.add_argument("--learned-strains", type=int, default=64,
@@ -765,6 +768,63 @@ def section_equilibrium(args, world, dev, torch, nemd, W):
             "roofline_frac": (ops / S) / ((k_ms / k_n) * 1e-3) / peak}
 
 
+def section_integrate(args, dev, torch, nemd, W):
+    """Time integration under the flow (nemd_integrate): the runtime comparison
+    of Sec. 5 (1728 WCA particles, 10,000 steps; dynamic offset against dynamic
+    size) on the general KR flow, and the N = 2^20 LJ system for 50 steps."""
+    def run(ser, w, p0, dt, nsteps, variant, kernel, autotune=False):
+        ctx = nemd.Context(dev.index)
+        ctx.set_flow(ser.A, ser.L0, ser.M, ser.period)
+        ctx.set_potential(nemd.NEMD_WCA if w.kind == W.POT_WCA else nemd.NEMD_LJ, 1.0, 1.0, 1)
+        q = torch.from_numpy(np.ascontiguousarray(w.q)).to(dev)
+        if autotune:
+            ctx.set_state(q, w.t)
+            ctx.autotune(nemd.NEMD_AUTO_HEURISTIC, w.rc, reps=2)
+            ctx.set_option(nemd.NEMD_OPT_AUTOTUNED, 1)
+        else:
+            ctx.set_option(nemd.NEMD_OPT_KERNEL, kernel)
+        # untimed warm-up run, then the timed one from the same initial state
+        qw, pw = q.clone(), torch.from_numpy(p0).to(dev)
+        ctx.integrate(qw, pw, w.t, dt, min(nsteps, 20), variant, w.rc, 1)
+        ctx.sync()
+        p = torch.from_numpy(p0).to(dev)
+        st = torch.cuda.current_stream(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(st)
+        ctx.integrate(q, p, w.t, dt, nsteps, variant, w.rc, 1)
+        e1.record(st)
+        ctx.sync()
+        torch.cuda.synchronize(dev)
+        ctx.close()
+        return e0.elapsed_time(e1) / nsteps
+
+    out = {}
+    small = W.StrainSeries(W.M_GENERAL, 8, 41, kind=W.POT_WCA, vacancies=4 * 8 ** 3 - 1728)
+    w = small.workload(0.0)
+    p0 = W.maxwell_momenta(w.n, 1.0, seed=42)
+    steps = 10000
+    ms = {"plain_ds": run(small, w, p0, 0.004, steps, nemd.NEMD_DS, 0),
+          "plain_do": run(small, w, p0, 0.004, steps, nemd.NEMD_DO, 0),
+          "tuned": run(small, w, p0, 0.004, steps, nemd.NEMD_AUTO_HEURISTIC, 2, autotune=True)}
+    out["n1728"] = {"workload": f"N={w.n} WCA (FCC 8^3 with vacancies), rho=0.8442, general KR flow, dt=0.004, "
+                                f"kT=1 isokinetic, {steps} steps",
+                    "ms_per_step": ms, "do_over_ds_time": ms["plain_do"] / ms["plain_ds"],
+                    "paper_do_over_ds_time": 0.717,
+                    "note": "the paper's ratio is one CPU core on a uniaxial flow; at this size every step here "
+                            "is a few dozen launches of near-empty kernels"}
+    big = W.general_series(k=64)
+    wb = big.workload(0.0)
+    pb = W.maxwell_momenta(wb.n, 0.8, seed=43)
+    msb = {"plain_ds": run(big, wb, pb, 0.002, 50, nemd.NEMD_DS, 0),
+           "plain_do": run(big, wb, pb, 0.002, 50, nemd.NEMD_DO, 0),
+           "tuned": run(big, wb, pb, 0.002, 50, nemd.NEMD_AUTO_HEURISTIC, 2, autotune=True)}
+    out["n1m"] = {"workload": f"N={wb.n} LJ rc=2.5 general KR flow, dt=0.002, kT=0.8 isokinetic, 50 steps",
+                  "ms_per_step": msb, "do_over_ds_time": msb["plain_do"] / msb["plain_ds"],
+                  "tuned_speedup_over_best_plain": min(msb["plain_ds"], msb["plain_do"]) / msb["tuned"]}
+    return out
+
+
 def main():
     args = parse()
     rank, world, local = dist_init(args)
@@ -792,6 +852,7 @@ def main():
         learned = section_learned(args, dev, torch, nemd, W) if "learned" in sections else None
         shear = section_shear(args, world, dev, torch, nemd, W) if "shear" in sections else None
         equilibrium = section_equilibrium(args, world, dev, torch, nemd, W) if "equilibrium" in sections else None
+        integ = section_integrate(args, dev, torch, nemd, W) if "integrate" in sections else None
     if rank == 0:
         line = {
             "metric": "interacting pairs/s per force eval", "value": main_part["value"], "unit": "pairs/s",
@@ -806,6 +867,7 @@ def main():
         line["learned"] = learned
         line["shear"] = shear
         line["equilibrium"] = equilibrium
+        line["integrate"] = integ
         print(json.dumps(line), flush=True)
     barrier(world)
     if world > 1:

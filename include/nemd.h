@@ -170,6 +170,31 @@ int nemd_build_cells(nemd_ctx *ctx, int variant, double rc);
  * Any of F, U, W may be NULL to skip it. */
 int nemd_compute_forces(nemd_ctx *ctx, float *F, double *U, double *W);
 
+/* Time integration under the flow (Sec. 2.1: a particle (q, p) has images
+ * (q + L_t n, p + A L_t n), so in peculiar momenta p - A q every image carries
+ * the same momentum).  The paper fixes no integrator; this one integrates the
+ * SLLOD equations for unit mass,
+ *     dq/dt = p + A q,   dp/dt = F(q, t) - A p  (- alpha p, isokinetic),
+ * with p the peculiar momentum, by a symmetric splitting per step of dt:
+ *     p <- exp(-A dt/2) (p + F dt/2);  isokinetic rescale;
+ *     q <- exp(A dt) q + Phi(dt) p,  Phi(dt) = int_0^dt exp(sA) ds  (exact for fixed p);
+ *     t <- t + dt;  q wrapped into the unit cell of L(t);  F <- F(q, t);
+ *     p <- F dt/2 + exp(-A dt/2) p;  isokinetic rescale.
+ * The rescale (thermostat = 1) multiplies p by sqrt(K0 / sum |p|^2), K0 the
+ * initial sum |p|^2 (Gaussian isokinetic in its velocity-rescaling form);
+ * thermostat = 0 leaves it out.  Every force evaluation is the hot path of
+ * this library (nemd_set_state, nemd_build_cells(variant, rc),
+ * nemd_compute_forces) with the context's potential and options.
+ *   q, p: N x 3 float64 DEVICE arrays (state at time t0), updated in place to
+ *         t0 + nsteps dt: q wrapped into the unit cell, p peculiar momenta;
+ *         they must stay valid until nemd_sync returns.
+ *   dt > 0 finite; nsteps >= 0.  Asynchronous (enqueues every step); the
+ *   context's time afterwards is t0 + nsteps dt.
+ * Errors: NEMD_ERR_ARG (host arrays, n < 0, bad dt or nsteps), NEMD_ERR_ORDER
+ * (no flow), and the errors of the force evaluation. */
+int nemd_integrate(nemd_ctx *ctx, double *q, double *p, int64_t n, double t0, double dt, int64_t nsteps,
+                   int variant, double rc, int thermostat);
+
 /* Wait for the stream and return any deferred device error. */
 int nemd_sync(nemd_ctx *ctx);
 

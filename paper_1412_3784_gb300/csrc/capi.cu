@@ -233,7 +233,7 @@ int nemd_destroy(nemd_ctx *c) {
   void *ptrs[] = {c->geo,  c->q_copy, c->relc,     c->relr, c->posr, c->rank,     c->count,    c->start, c->chunks, c->nchunks, c->recheck, c->nrecheck,
                   c->block_sums, c->perm, c->pos4, c->cell_sorted, c->rows, c->rowcnt,
                   c->partials, c->uw_out, c->f_dev, c->pair_buf, c->pair_count, c->counters,
-                  c->chunk_cnt, c->chunk_off};
+                  c->chunk_cnt, c->chunk_off, c->int_state, c->int_part, c->f_int};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->copy_stream) {

@@ -1,0 +1,274 @@
+// integrate.cu -- time integration under the flow (the step after the force
+// evaluation): SLLOD equations of motion for unit mass in peculiar momenta,
+//     dq/dt = p + A q,   dp/dt = F - A p,
+// which make every periodic image (q + L_t n, p + A L_t n) of Sec. 2.1 carry
+// the same peculiar momentum, integrated by a symmetric splitting:
+//     p <- exp(-A h) (p + h F);  rescale;  q <- exp(A dt) q + Phi(dt) p;
+//     t <- t + dt;  wrap q into the unit cell of L(t);  F <- F(q, t);
+//     p <- h F + exp(-A h) p;  rescale                       (h = dt / 2)
+// with Phi(dt) = int_0^dt exp(sA) ds (the drift is exact for fixed p: with
+// p = 0 a particle moves affinely with the box, q = L_t s at fixed s).  The
+// rescale multiplies p by sqrt(K0 / sum |p|^2) (isokinetic; K0 the initial
+// sum), or is skipped.  Sums of |p|^2 are per-block float64 partials added in
+// a fixed order, so a run repeats bit for bit.  The paper gives no integrator:
+// this is the reading stated with nemd_integrate in include/nemd.h.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <algorithm>
+
+#include "nemd_device.cuh"
+
+namespace nemd {
+
+namespace {
+
+constexpr int kIntThreads = 256;
+// int_state layout (doubles)
+constexpr int kE = 0, kEh = 9, kPhi = 18, kK0 = 27, kScale = 28, kH = 29, kThermo = 30, kIntState = 32;
+
+__device__ __forceinline__ void mat3(const double *a, const double *b, double *c) {
+  double t[9];
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) t[3 * i + j] = a[3 * i] * b[j] + a[3 * i + 1] * b[3 + j] + a[3 * i + 2] * b[6 + j];
+  for (int k = 0; k < 9; k++) c[k] = t[k];
+}
+
+// exp(B) and int_0^1 exp(sB) ds for a 3x3 B: scaling by 2^-s until
+// |B|_1 <= 1/8, Taylor polynomials of degree 16 for both, then s doublings
+// exp(2X) = exp(X)^2 and Phi(2X) = (I + exp(X)) Phi(X) (Phi scaled by the step).
+__device__ void expm_phi(const double *B, double *E, double *Phi) {
+  double nrm = 0.0;
+  for (int j = 0; j < 3; j++) nrm = fmax(nrm, fabs(B[j]) + fabs(B[3 + j]) + fabs(B[6 + j]));
+  int s = 0;
+  if (nrm > 0.125) frexp(nrm * 8.0, &s);
+  double X[9];
+  for (int k = 0; k < 9; k++) X[k] = ldexp(B[k], -s);
+  // Horner: E = I + X (I + X/2 (I + X/3 (...))); P = I + X/2 (I + X/3 (I + ...)) so Phi = P
+  double Et[9], Pt[9];
+  const int deg = 16;
+  for (int k = 0; k < 9; k++) {
+    Et[k] = (k % 4 == 0 ? 1.0 : 0.0) + X[k] / deg;
+    Pt[k] = (k % 4 == 0 ? 1.0 : 0.0) + X[k] / (deg + 1);
+  }
+  for (int m = deg - 1; m >= 1; m--) {
+    double T1[9], T2[9];
+    mat3(X, Et, T1);
+    mat3(X, Pt, T2);
+    for (int k = 0; k < 9; k++) {
+      Et[k] = (k % 4 == 0 ? 1.0 : 0.0) + T1[k] / m;
+      Pt[k] = (k % 4 == 0 ? 1.0 : 0.0) + T2[k] / (m + 1);
+    }
+  }
+  // Et = exp(X); Pt = sum_k X^k / (k+1)! = int_0^1 exp(sX) ds
+  for (int r = 0; r < s; r++) {
+    double T[9], Ip[9];
+    for (int k = 0; k < 9; k++) Ip[k] = (k % 4 == 0 ? 1.0 : 0.0) + Et[k];
+    mat3(Ip, Pt, T);  // int_0^1 exp(2 s X) ds = (I + exp(X)) int_0^1 exp(sX) ds / 2
+    for (int k = 0; k < 9; k++) Pt[k] = 0.5 * T[k];
+    mat3(Et, Et, Et);
+  }
+  for (int k = 0; k < 9; k++) {
+    E[k] = Et[k];
+    Phi[k] = Pt[k];
+  }
+}
+
+// Propagators of the step: exp(A dt), exp(-A dt/2), Phi(dt) = dt int_0^1 exp(s dt A) ds.
+__global__ void k_int_setup(double *st, Geo *g, double dt, int thermostat) {
+  if (threadIdx.x != 0) return;
+  double B[9], Bh[9], P[9], Ph[9];
+  for (int k = 0; k < 9; k++) {
+    B[k] = dt * g->A[k];
+    Bh[k] = -0.5 * dt * g->A[k];
+  }
+  expm_phi(B, st + kE, P);
+  for (int k = 0; k < 9; k++) st[kPhi + k] = dt * P[k];
+  expm_phi(Bh, st + kEh, Ph);
+  st[kScale] = 1.0;
+  st[kH] = 0.5 * dt;
+  st[kThermo] = thermostat;
+}
+
+// Per-block partial of sum |p|^2 (fixed grid-stride order, shuffle tree).
+__device__ __forceinline__ void block_p2(double x, double *part) {
+  __shared__ double sh[kIntThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double y = 0.0;
+    for (int w = 0; w < kIntThreads / 32; w++) y += sh[w];
+    part[blockIdx.x] = y;
+  }
+}
+
+__global__ void __launch_bounds__(kIntThreads) k_int_p2(const double *__restrict__ p, int n, double *part) {
+  double x = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    x += (p[3 * (size_t)i] * p[3 * (size_t)i] + p[3 * (size_t)i + 1] * p[3 * (size_t)i + 1]) +
+         p[3 * (size_t)i + 2] * p[3 * (size_t)i + 2];
+  block_p2(x, part);
+}
+
+// mode 0: K0 = sum of the partials; 1: scale = sqrt(K0 / sum) when thermostatted
+__global__ void k_int_sum(double *st, const double *part, int nb, int mode) {
+  if (threadIdx.x != 0) return;
+  double y = 0.0;
+  for (int b = 0; b < nb; b++) y += part[b];
+  if (mode == 0) {
+    st[kK0] = y;
+    st[kScale] = 1.0;
+  } else {
+    st[kScale] = (st[kThermo] != 0.0 && y > 0.0) ? sqrt(st[kK0] / y) : 1.0;
+  }
+}
+
+__device__ __forceinline__ void mv3(const double *M, double x, double y, double z, double &ox, double &oy,
+                                    double &oz) {
+  ox = (M[0] * x + M[1] * y) + M[2] * z;
+  oy = (M[3] * x + M[4] * y) + M[5] * z;
+  oz = (M[6] * x + M[7] * y) + M[8] * z;
+}
+
+// first half: p <- exp(-A h) (scale p + h F); partial sum |p|^2
+__global__ void __launch_bounds__(kIntThreads) k_int_kick1(double *__restrict__ p, const float *__restrict__ F,
+                                                           int n, const double *__restrict__ st, double *part) {
+  const double h = st[kH], sc = st[kScale];
+  double x2 = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double a = sc * p[3 * (size_t)i] + h * (double)F[3 * (size_t)i];
+    const double b = sc * p[3 * (size_t)i + 1] + h * (double)F[3 * (size_t)i + 1];
+    const double c = sc * p[3 * (size_t)i + 2] + h * (double)F[3 * (size_t)i + 2];
+    double ox, oy, oz;
+    mv3(st + kEh, a, b, c, ox, oy, oz);
+    p[3 * (size_t)i] = ox;
+    p[3 * (size_t)i + 1] = oy;
+    p[3 * (size_t)i + 2] = oz;
+    x2 += (ox * ox + oy * oy) + oz * oz;
+  }
+  block_p2(x2, part);
+}
+
+// drift: p <- scale p; q <- exp(A dt) q + Phi p, then q wrapped into the unit
+// cell of the lattice already evolved to the new time (g)
+__global__ void __launch_bounds__(kIntThreads) k_int_drift(double *__restrict__ q, double *__restrict__ p, int n,
+                                                           const double *__restrict__ st, const Geo *g) {
+  const double sc = st[kScale];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double px = sc * p[3 * (size_t)i], py = sc * p[3 * (size_t)i + 1], pz = sc * p[3 * (size_t)i + 2];
+    p[3 * (size_t)i] = px;
+    p[3 * (size_t)i + 1] = py;
+    p[3 * (size_t)i + 2] = pz;
+    double ex, ey, ez, fx, fy, fz;
+    mv3(st + kE, q[3 * (size_t)i], q[3 * (size_t)i + 1], q[3 * (size_t)i + 2], ex, ey, ez);
+    mv3(st + kPhi, px, py, pz, fx, fy, fz);
+    double s[3], qp[3];
+    frac_wrap(g->Linv, ex + fx, ey + fy, ez + fz, s);
+    frac_to_cart(g->L, s, qp);
+    q[3 * (size_t)i] = qp[0];
+    q[3 * (size_t)i + 1] = qp[1];
+    q[3 * (size_t)i + 2] = qp[2];
+  }
+}
+
+// second half: p <- h F + exp(-A h) p; partial sum |p|^2
+__global__ void __launch_bounds__(kIntThreads) k_int_kick2(double *__restrict__ p, const float *__restrict__ F,
+                                                           int n, const double *__restrict__ st, double *part) {
+  const double h = st[kH];
+  double x2 = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double ox, oy, oz;
+    mv3(st + kEh, p[3 * (size_t)i], p[3 * (size_t)i + 1], p[3 * (size_t)i + 2], ox, oy, oz);
+    ox += h * (double)F[3 * (size_t)i];
+    oy += h * (double)F[3 * (size_t)i + 1];
+    oz += h * (double)F[3 * (size_t)i + 2];
+    p[3 * (size_t)i] = ox;
+    p[3 * (size_t)i + 1] = oy;
+    p[3 * (size_t)i + 2] = oz;
+    x2 += (ox * ox + oy * oy) + oz * oz;
+  }
+  block_p2(x2, part);
+}
+
+__global__ void __launch_bounds__(kIntThreads) k_int_final(double *__restrict__ p, int n,
+                                                           const double *__restrict__ st) {
+  const double sc = st[kScale];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 3 * n; i += gridDim.x * blockDim.x) p[i] *= sc;
+}
+
+int int_err(nemd_ctx *c, int code, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(c->msg, sizeof c->msg, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+bool on_device(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+}  // namespace nemd
+
+extern "C" {
+
+int nemd_integrate(nemd_ctx *c, double *q, double *p, int64_t n, double t0, double dt, int64_t nsteps,
+                   int variant, double rc, int thermostat) {
+  if (!c) return NEMD_ERR_ARG;
+  if (!c->have_flow) return nemd::int_err(c, NEMD_ERR_ORDER, "integrate before set_flow");
+  if (n < 0 || n > (int64_t)0x7fffffff / 4 || nsteps < 0 || !(dt > 0.0) || !isfinite(dt) || !isfinite(t0))
+    return nemd::int_err(c, NEMD_ERR_ARG, "integrate: bad n, dt or nsteps");
+  if (n > 0 && (!q || !p || !nemd::on_device(q) || !nemd::on_device(p)))
+    return nemd::int_err(c, NEMD_ERR_ARG, "integrate: q and p must be device arrays");
+  if (cudaSetDevice(c->device) != cudaSuccess) return NEMD_ERR_CUDA;
+  using namespace nemd;
+  const int nb = (int)std::min<int64_t>(std::max<int64_t>((n + kIntThreads - 1) / kIntThreads, 1), 4 * (int64_t)c->sms);
+  if (!c->int_state && cudaMalloc((void **)&c->int_state, sizeof(double) * kIntState) != cudaSuccess)
+    return nemd::int_err(c, NEMD_ERR_NOMEM, "integrate: state");
+  if (!c->int_part && cudaMalloc((void **)&c->int_part, sizeof(double) * 4 * (size_t)c->sms) != cudaSuccess)
+    return nemd::int_err(c, NEMD_ERR_NOMEM, "integrate: partials");
+  if (c->f_int_cap < n) {
+    if (c->f_int) cudaFree(c->f_int);
+    c->f_int = nullptr;
+    c->f_int_cap = 0;
+    if (cudaMalloc((void **)&c->f_int, sizeof(float) * 3 * (size_t)std::max<int64_t>(n, 1)) != cudaSuccess)
+      return nemd::int_err(c, NEMD_ERR_NOMEM, "integrate: forces");
+    c->f_int_cap = n;
+  }
+  int r;
+  // forces of the initial state
+  if ((r = nemd_set_state(c, q, n, t0))) return r;
+  k_int_setup<<<1, 32, 0, c->stream>>>(c->int_state, c->geo, dt, thermostat ? 1 : 0);
+  k_int_p2<<<nb, kIntThreads, 0, c->stream>>>(p, (int)n, c->int_part);
+  k_int_sum<<<1, 32, 0, c->stream>>>(c->int_state, c->int_part, nb, 0);
+  c->launches += 3;
+  if ((r = nemd_build_cells(c, variant, rc))) return r;
+  if ((r = nemd_compute_forces(c, c->f_int, nullptr, nullptr))) return r;
+  for (int64_t k = 0; k < nsteps; k++) {
+    k_int_kick1<<<nb, kIntThreads, 0, c->stream>>>(p, c->f_int, (int)n, c->int_state, c->int_part);
+    k_int_sum<<<1, 32, 0, c->stream>>>(c->int_state, c->int_part, nb, 1);
+    // the lattice at the new time, then the drift wraps into its unit cell
+    if ((r = nemd_set_state(c, q, n, t0 + (double)(k + 1) * dt))) return r;
+    k_int_drift<<<nb, kIntThreads, 0, c->stream>>>(q, p, (int)n, c->int_state, c->geo);
+    if ((r = nemd_build_cells(c, variant, rc))) return r;
+    if ((r = nemd_compute_forces(c, c->f_int, nullptr, nullptr))) return r;
+    k_int_kick2<<<nb, kIntThreads, 0, c->stream>>>(p, c->f_int, (int)n, c->int_state, c->int_part);
+    k_int_sum<<<1, 32, 0, c->stream>>>(c->int_state, c->int_part, nb, 1);
+    c->launches += 5;
+  }
+  k_int_final<<<nb, kIntThreads, 0, c->stream>>>(p, (int)n, c->int_state);
+  c->launches += 1;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? NEMD_OK : nemd::int_err(c, NEMD_ERR_CUDA, "integrate: %s", cudaGetErrorString(e));
+}
+
+}  // extern "C"

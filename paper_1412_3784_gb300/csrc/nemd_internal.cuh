@@ -230,6 +230,12 @@ struct nemd_ctx {
   double *aq[2];              // positions copied from the host
   float *af[2];               // forces copied to the host
   double *auw[2];             // U, W copied to the host
+  // time integration (nemd_integrate): propagators and thermostat state,
+  // per-block sums of |p|^2, forces of the current step
+  double *int_state;
+  double *int_part;
+  float *f_int;
+  int64_t f_int_cap;
 };
 
 namespace nemd {

@@ -37,7 +37,7 @@ NEMD_OPT_REMAP = 9
 NEMD_OPT_ASYNC_HOST = 10
 
 EXPORTED = ["nemd_create", "nemd_destroy", "nemd_set_flow", "nemd_set_potential", "nemd_set_state",
-            "nemd_build_cells", "nemd_compute_forces", "nemd_sync", "nemd_last_error",
+            "nemd_build_cells", "nemd_compute_forces", "nemd_integrate", "nemd_sync", "nemd_last_error",
             "nemd_set_option", "nemd_get_lattice", "nemd_get_stats", "nemd_get_pairs",
             "nemd_get_kernel_time", "nemd_measure_peaks", "nemd_forces_noalloc", "nemd_autotune",
             "nemd_tune_save", "nemd_tune_load", "nemd_features", "nemd_time_options", "nemd_model_train",
@@ -91,6 +91,8 @@ _sig = {
     "nemd_set_state": ([_vp, _vp, ctypes.c_int64, ctypes.c_double], ctypes.c_int),
     "nemd_build_cells": ([_vp, ctypes.c_int, ctypes.c_double], ctypes.c_int),
     "nemd_compute_forces": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+    "nemd_integrate": ([_vp, _vp, _vp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                        ctypes.c_int, ctypes.c_double, ctypes.c_int], ctypes.c_int),
     "nemd_sync": ([_vp], ctypes.c_int),
     "nemd_last_error": ([_vp], ctypes.c_char_p),
     "nemd_set_option": ([_vp, ctypes.c_int, ctypes.c_int64], ctypes.c_int),
@@ -221,6 +223,14 @@ class Context:
 
     def compute_forces(self, F=None, U=None, W=None):
         return self._check(nemd_compute_forces(self.h, _ptr(F), _ptr(U), _ptr(W)))
+
+    def integrate(self, q, p, t0, dt, nsteps, variant, rc, thermostat=1):
+        """Advance device float64 (N, 3) positions q and peculiar momenta p in place
+        by nsteps steps of dt from time t0 (see nemd_integrate)."""
+        self._keep["q"] = q
+        self._keep["p"] = p
+        return self._check(nemd_integrate(self.h, _ptr(q), _ptr(p), int(q.shape[0]), float(t0), float(dt),
+                                          int(nsteps), int(variant), float(rc), int(thermostat)))
 
     def sync(self):
         return self._check(nemd_sync(self.h))

@@ -286,6 +286,14 @@ def batched_systems(nsys: int = 256, seed: int = 3, nmin: int = 1000, nmax: int 
     return out
 
 
+def maxwell_momenta(n: int, kT: float, seed: int) -> np.ndarray:
+    """(n, 3) float64 momenta of unit-mass particles drawn from N(0, kT) per
+    component (seeded), with the mean removed (zero total momentum)."""
+    rng = np.random.default_rng(seed)
+    p = rng.normal(0.0, math.sqrt(kT), size=(n, 3))
+    return np.ascontiguousarray(p - p.mean(axis=0))
+
+
 def uniform_random(n: int, L: np.ndarray, seed: int, rc: float = LJ_RC,
                    kind: int = POT_LJ) -> Workload:
     """Uniform random points in a static box L (A = 0), for statistical checks."""
