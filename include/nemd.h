@@ -102,6 +102,11 @@ typedef enum nemd_option {
                                    are written by that copy stream and are valid after
                                    the next nemd_sync.  0 (default): a call that writes
                                    host outputs synchronises before it returns.          */
+    NEMD_OPT_INT_GRAPH = 11,    /* nemd_integrate: 1 (default) captures one step in a
+                                   CUDA graph and replays it for the remaining steps
+                                   (same results bit for bit); 0 launches every step.
+                                   Steps are launched eagerly anyway with
+                                   NEMD_OPT_ASYNC_HOST or NEMD_OPT_TIMING on.            */
     NEMD_OPT_REMAP = 9          /* remap instant within a period: 0 (default) at its end,
                                    tau = t - T floor(t/T) in [0, T); 1 half way,
                                    tau = t - T floor(t/T + 1/2) in [-T/2, T/2) -- the

@@ -190,6 +190,7 @@ int nemd_create(nemd_ctx **out, int device, void *stream) {
   if (!c) return NEMD_ERR_NOMEM;
   c->device = device;
   c->stream = (cudaStream_t)stream;
+  c->int_graph = 1;
   cudaError_t e = cudaSetDevice(device);
   if (e != cudaSuccess) {
     free(c);
@@ -236,6 +237,7 @@ int nemd_destroy(nemd_ctx *c) {
                   c->chunk_cnt, c->chunk_off, c->int_state, c->int_part, c->f_int};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->copy_stream) {
     cudaStreamSynchronize(c->copy_stream);
     cudaStreamSynchronize(c->copy_back);
@@ -512,6 +514,10 @@ int nemd_set_option(nemd_ctx *c, int key, int64_t value) {
         CK(cudaStreamSynchronize(c->copy_back));
       }
       c->async_host = value ? 1 : 0;
+      return NEMD_OK;
+    case NEMD_OPT_INT_GRAPH:
+      if (value != 0 && value != 1) return set_err(c, NEMD_ERR_ARG, "int_graph %lld (0 or 1)", (long long)value);
+      c->int_graph = (int)value;
       return NEMD_OK;
     case NEMD_OPT_REMAP:
       if (value != 0 && value != 1) return set_err(c, NEMD_ERR_ARG, "remap %lld (0 or 1)", (long long)value);

@@ -26,7 +26,13 @@ namespace {
 
 constexpr int kIntThreads = 256;
 // int_state layout (doubles)
-constexpr int kE = 0, kEh = 9, kPhi = 18, kK0 = 27, kScale = 28, kH = 29, kThermo = 30, kIntState = 32;
+constexpr int kE = 0, kEh = 9, kPhi = 18, kK0 = 27, kScale = 28, kH = 29, kThermo = 30, kT0 = 31, kDt = 32,
+              kStep = 33, kTnow = 34, kIntState = 36;
+
+// The flow matrix by value.
+struct Mat9 {
+  double a[9];
+};
 
 __device__ __forceinline__ void mat3(const double *a, const double *b, double *c) {
   double t[9];
@@ -75,13 +81,14 @@ __device__ void expm_phi(const double *B, double *E, double *Phi) {
   }
 }
 
-// Propagators of the step: exp(A dt), exp(-A dt/2), Phi(dt) = dt int_0^1 exp(s dt A) ds.
-__global__ void k_int_setup(double *st, Geo *g, double dt, int thermostat) {
+// Propagators of the step: exp(A dt), exp(-A dt/2), Phi(dt) = dt int_0^1 exp(s dt A) ds;
+// the clock: t_k = t0 + k dt, k = 0.
+__global__ void k_int_setup(double *st, Mat9 A, double t0, double dt, int thermostat) {
   if (threadIdx.x != 0) return;
   double B[9], Bh[9], P[9], Ph[9];
   for (int k = 0; k < 9; k++) {
-    B[k] = dt * g->A[k];
-    Bh[k] = -0.5 * dt * g->A[k];
+    B[k] = dt * A.a[k];
+    Bh[k] = -0.5 * dt * A.a[k];
   }
   expm_phi(B, st + kE, P);
   for (int k = 0; k < 9; k++) st[kPhi + k] = dt * P[k];
@@ -89,6 +96,18 @@ __global__ void k_int_setup(double *st, Geo *g, double dt, int thermostat) {
   st[kScale] = 1.0;
   st[kH] = 0.5 * dt;
   st[kThermo] = thermostat;
+  st[kT0] = t0;
+  st[kDt] = dt;
+  st[kStep] = 0.0;
+  st[kTnow] = t0;
+}
+
+// Advance the clock one step: t = t0 + k dt (each operation rounded once).
+__global__ void k_int_tick(double *st) {
+  if (threadIdx.x != 0) return;
+  const double k = st[kStep] + 1.0;
+  st[kStep] = k;
+  st[kTnow] = __dadd_rn(st[kT0], __dmul_rn(k, st[kDt]));
 }
 
 // Per-block partial of sum |p|^2 (fixed grid-stride order, shuffle tree).
@@ -219,6 +238,43 @@ bool on_device(const void *p) {
 
 }  // namespace nemd
 
+namespace nemd {
+namespace {
+
+// The lattice at the context's device clock, as nemd_set_state does for a
+// device array (no host query: callable while a stream is being captured).
+int int_state_at_clock(nemd_ctx *c, double *q, int64_t n, double t_host) {
+  c->n = n;
+  c->t = t_host;
+  c->q_dev = n > 0 ? q : nullptr;
+  cudaError_t e = launch_lattice(c, 0, 0.0);
+  if (e != cudaSuccess) return int_err(c, NEMD_ERR_CUDA, "integrate lattice: %s", cudaGetErrorString(e));
+  c->have_state = true;
+  c->have_cells = false;
+  return NEMD_OK;
+}
+
+// One step after the first: clock, first kick, lattice at the new time,
+// drift and wrap, the force evaluation, second kick.
+int int_step(nemd_ctx *c, double *q, double *p, int64_t n, double t_host, int variant, double rc, int nb) {
+  int r;
+  k_int_tick<<<1, 32, 0, c->stream>>>(c->int_state);
+  k_int_kick1<<<nb, kIntThreads, 0, c->stream>>>(p, c->f_int, (int)n, c->int_state, c->int_part);
+  k_int_sum<<<1, 32, 0, c->stream>>>(c->int_state, c->int_part, nb, 1);
+  if ((r = int_state_at_clock(c, q, n, t_host))) return r;
+  k_int_drift<<<nb, kIntThreads, 0, c->stream>>>(q, p, (int)n, c->int_state, c->geo);
+  if ((r = nemd_build_cells(c, variant, rc))) return r;
+  if ((r = nemd_compute_forces(c, c->f_int, nullptr, nullptr))) return r;
+  k_int_kick2<<<nb, kIntThreads, 0, c->stream>>>(p, c->f_int, (int)n, c->int_state, c->int_part);
+  k_int_sum<<<1, 32, 0, c->stream>>>(c->int_state, c->int_part, nb, 1);
+  c->launches += 6;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? NEMD_OK : int_err(c, NEMD_ERR_CUDA, "integrate: %s", cudaGetErrorString(e));
+}
+
+}  // namespace
+}  // namespace nemd
+
 extern "C" {
 
 int nemd_integrate(nemd_ctx *c, double *q, double *p, int64_t n, double t0, double dt, int64_t nsteps,
@@ -244,29 +300,70 @@ int nemd_integrate(nemd_ctx *c, double *q, double *p, int64_t n, double t0, doub
       return nemd::int_err(c, NEMD_ERR_NOMEM, "integrate: forces");
     c->f_int_cap = n;
   }
-  int r;
-  // forces of the initial state
-  if ((r = nemd_set_state(c, q, n, t0))) return r;
-  k_int_setup<<<1, 32, 0, c->stream>>>(c->int_state, c->geo, dt, thermostat ? 1 : 0);
-  k_int_p2<<<nb, kIntThreads, 0, c->stream>>>(p, (int)n, c->int_part);
-  k_int_sum<<<1, 32, 0, c->stream>>>(c->int_state, c->int_part, nb, 0);
-  c->launches += 3;
-  if ((r = nemd_build_cells(c, variant, rc))) return r;
-  if ((r = nemd_compute_forces(c, c->f_int, nullptr, nullptr))) return r;
-  for (int64_t k = 0; k < nsteps; k++) {
-    k_int_kick1<<<nb, kIntThreads, 0, c->stream>>>(p, c->f_int, (int)n, c->int_state, c->int_part);
-    k_int_sum<<<1, 32, 0, c->stream>>>(c->int_state, c->int_part, nb, 1);
-    // the lattice at the new time, then the drift wraps into its unit cell
-    if ((r = nemd_set_state(c, q, n, t0 + (double)(k + 1) * dt))) return r;
-    k_int_drift<<<nb, kIntThreads, 0, c->stream>>>(q, p, (int)n, c->int_state, c->geo);
-    if ((r = nemd_build_cells(c, variant, rc))) return r;
-    if ((r = nemd_compute_forces(c, c->f_int, nullptr, nullptr))) return r;
-    k_int_kick2<<<nb, kIntThreads, 0, c->stream>>>(p, c->f_int, (int)n, c->int_state, c->int_part);
-    k_int_sum<<<1, 32, 0, c->stream>>>(c->int_state, c->int_part, nb, 1);
-    c->launches += 5;
-  }
-  k_int_final<<<nb, kIntThreads, 0, c->stream>>>(p, (int)n, c->int_state);
+  int r = NEMD_OK;
+  // the time of every step comes from the device clock (t0 + k dt, rounded the
+  // same way whether the step is launched or replayed)
+  Mat9 A;
+  for (int k = 0; k < 9; k++) A.a[k] = c->A[k];
+  k_int_setup<<<1, 32, 0, c->stream>>>(c->int_state, A, t0, dt, thermostat ? 1 : 0);
   c->launches += 1;
+  c->t_dev = c->int_state + kTnow;
+  do {
+    if ((r = nemd_set_state(c, q, n, t0))) break;
+    k_int_p2<<<nb, kIntThreads, 0, c->stream>>>(p, (int)n, c->int_part);
+    k_int_sum<<<1, 32, 0, c->stream>>>(c->int_state, c->int_part, nb, 0);
+    c->launches += 2;
+    if ((r = nemd_build_cells(c, variant, rc))) break;
+    if ((r = nemd_compute_forces(c, c->f_int, nullptr, nullptr))) break;
+    int64_t k = 0;
+    // the first step is launched (it sizes every buffer); then, unless the
+    // options need per-step host work, one step is captured and replayed
+    if (nsteps > 0) {
+      if ((r = int_step(c, q, p, n, t0 + dt, variant, rc, nb))) break;
+      k = 1;
+    }
+    if (nsteps > 2 && c->int_graph && !c->async_host && !c->timing) {
+      // capture on a private stream (the context's may be the legacy default
+      // stream, which cannot be captured); replay on the context's stream.  A
+      // capture that fails leaves nothing executed: the steps are then launched.
+      if (!c->cap_stream) cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      const int64_t l0 = c->launches;
+      cudaStream_t home = c->stream;
+      bool ok = c->cap_stream && cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+      if (ok) {
+        c->stream = c->cap_stream;
+        const int rs = int_step(c, q, p, n, t0 + 2.0 * dt, variant, rc, nb);
+        c->stream = home;
+        ok = cudaStreamEndCapture(c->cap_stream, &graph) == cudaSuccess && rs == NEMD_OK;
+        ok = ok && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+      }
+      cudaGetLastError();
+      const int64_t per_step = c->launches - l0;
+      c->launches = l0;
+      if (ok) {
+        for (; k < nsteps; k++) {
+          if (cudaGraphLaunch(exec, c->stream) != cudaSuccess) {
+            r = int_err(c, NEMD_ERR_CUDA, "integrate: step graph launch failed");
+            break;
+          }
+          c->launches += per_step;
+        }
+      }
+      if (exec) cudaGraphExecDestroy(exec);
+      if (graph) cudaGraphDestroy(graph);
+      if (r) break;
+    }
+    for (; k < nsteps; k++)
+      if ((r = int_step(c, q, p, n, t0 + (double)(k + 1) * dt, variant, rc, nb))) break;
+    if (r) break;
+    k_int_final<<<nb, kIntThreads, 0, c->stream>>>(p, (int)n, c->int_state);
+    c->launches += 1;
+  } while (false);
+  c->t_dev = nullptr;
+  c->t = t0 + (double)nsteps * dt;
+  if (r) return r;
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? NEMD_OK : nemd::int_err(c, NEMD_ERR_CUDA, "integrate: %s", cudaGetErrorString(e));
 }

@@ -72,7 +72,7 @@ __device__ __forceinline__ void lattice_body(Geo *g, const LatIn &in) {
   if (validate) {
     tau = tau_in;
   } else {
-    const double T = in.T, t = in.t;
+    const double T = in.T, t = in.t_dev ? *in.t_dev : in.t;
     if (!(T > 0.0))
       tau = t;
     else if (in.centered)
@@ -86,7 +86,7 @@ __device__ __forceinline__ void lattice_body(Geo *g, const LatIn &in) {
   }
   if (lane == 0) {
     g->T = in.T;
-    g->t = in.t;
+    g->t = in.t_dev ? *in.t_dev : in.t;
     if (!validate) g->error = 0;
   }
 
@@ -499,6 +499,7 @@ cudaError_t launch_lattice(nemd_ctx *c, int validate, double tau) {
   in.tau = tau;
   in.validate = validate;
   in.centered = c->remap_centered;
+  in.t_dev = c->t_dev;
   k_lattice<<<1, 32, 0, c->stream>>>(c->geo, in);
   c->launches += 1;
   return cudaGetLastError();

@@ -88,6 +88,7 @@ struct LatIn {
   double T, t, tau;
   int validate;
   int centered;  // remap half way through the period: tau in [-T/2, T/2)
+  const double *t_dev = nullptr;  // when set, t is read here (device memory: captured steps)
 };
 
 struct GridIn {
@@ -236,6 +237,9 @@ struct nemd_ctx {
   double *int_part;
   float *f_int;
   int64_t f_int_cap;
+  const double *t_dev;  // while integrating: the lattice reads the time from here
+  int int_graph;        // NEMD_OPT_INT_GRAPH: replay a captured step (default 1)
+  cudaStream_t cap_stream;  // private stream the step is captured on
 };
 
 namespace nemd {

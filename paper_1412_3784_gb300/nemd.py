@@ -35,6 +35,7 @@ NEMD_OPT_GROUP = 7
 NEMD_OPT_AUTOTUNED = 8
 NEMD_OPT_REMAP = 9
 NEMD_OPT_ASYNC_HOST = 10
+NEMD_OPT_INT_GRAPH = 11
 
 EXPORTED = ["nemd_create", "nemd_destroy", "nemd_set_flow", "nemd_set_potential", "nemd_set_state",
             "nemd_build_cells", "nemd_compute_forces", "nemd_integrate", "nemd_sync", "nemd_last_error",

@@ -29,9 +29,10 @@ def _ctx(w):
     return ctx
 
 
-def run_gpu(w, p0, dt, nsteps, variant, thermostat=1, kernel=2):
+def run_gpu(w, p0, dt, nsteps, variant, thermostat=1, kernel=2, graph=1):
     ctx = _ctx(w)
     ctx.set_option(nemd.NEMD_OPT_KERNEL, kernel)
+    ctx.set_option(nemd.NEMD_OPT_INT_GRAPH, graph)
     q = torch.from_numpy(np.ascontiguousarray(w.q)).cuda()
     p = torch.from_numpy(np.ascontiguousarray(p0)).cuda()
     ctx.integrate(q, p, w.t, dt, nsteps, variant, w.rc, thermostat)
@@ -122,12 +123,20 @@ def test_energy_is_conserved_without_flow_or_thermostat():
 
 
 def test_repeats_bit_for_bit_and_validates_arguments():
+    """Two runs, and the replayed step graph against launching every step,
+    agree bit for bit; bad arguments are refused."""
     ser = W.StrainSeries(W.M_GENERAL, 6, 30, kind=W.POT_WCA)
     w = ser.workload(0.2)
     p0 = W.maxwell_momenta(w.n, 1.0, seed=31)
     a = run_gpu(w, p0, 0.004, 10, DO)
     b = run_gpu(w, p0, 0.004, 10, DO)
+    c = run_gpu(w, p0, 0.004, 10, DO, graph=0)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert np.array_equal(a[0], c[0]) and np.array_equal(a[1], c[1])
+    for m in (0, 1, 2, 3):
+        d = run_gpu(w, p0, 0.004, m, DS)
+        e = run_gpu(w, p0, 0.004, m, DS, graph=0)
+        assert np.array_equal(d[0], e[0]) and np.array_equal(d[1], e[1])
     ctx = _ctx(w)
     q = torch.from_numpy(np.ascontiguousarray(w.q)).cuda()
     p = torch.from_numpy(np.ascontiguousarray(p0)).cuda()
