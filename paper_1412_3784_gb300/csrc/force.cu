@@ -441,8 +441,13 @@ __global__ void k_b_fixup(BatchView v) {
 // order (fixed), halved for the full neighbourhoods, the virial rotated back to
 // Cartesian for the dynamic offset frame (W = Q W_R Q^T).
 __global__ void __launch_bounds__(256) k_b_reduce(BatchView v) {
-  constexpr int K = 8;
-  __shared__ double sh[256][K];
+  // float32 pair sums accumulated in float-float (the float64 pipe runs at
+  // 1/64 of the float32 rate here), pair counts in 64-bit integers; a fixed
+  // order throughout (threads over particles, shuffle tree, warps in order)
+  constexpr int K = 7;
+  constexpr int kW = 256 / 32;
+  __shared__ float shh[kW][K], shl[kW][K];
+  __shared__ long long shn[kW];
   const int s = blockIdx.x;
   Geo *g = v.geo + s;
   const bool ok = !(g->error & (ERRB_BOX | ERRB_CAPACITY));
@@ -452,37 +457,57 @@ __global__ void __launch_bounds__(256) k_b_reduce(BatchView v) {
     b = v.start[coff];
     e = v.start[coff + g->ncells];
   }
-  double a[K];
+  ff a[K];
 #pragma unroll
-  for (int k = 0; k < K; k++) a[k] = 0.0;
+  for (int k = 0; k < K; k++) a[k] = {0.f, 0.f};
+  long long np = 0;
   for (int k = b + threadIdx.x; k < e; k += blockDim.x) {
     const float4 p0 = v.ppart[2 * (size_t)k], p1 = v.ppart[2 * (size_t)k + 1];
-    a[0] += p0.x;
-    a[1] += p0.y;
-    a[2] += p0.z;
-    a[3] += p0.w;
-    a[4] += p1.x;
-    a[5] += p1.y;
-    a[6] += p1.z;
-    a[7] += (double)__float_as_int(p1.w);
+    a[0] = ff_add(a[0], ff{p0.x, 0.f});
+    a[1] = ff_add(a[1], ff{p0.y, 0.f});
+    a[2] = ff_add(a[2], ff{p0.z, 0.f});
+    a[3] = ff_add(a[3], ff{p0.w, 0.f});
+    a[4] = ff_add(a[4], ff{p1.x, 0.f});
+    a[5] = ff_add(a[5], ff{p1.y, 0.f});
+    a[6] = ff_add(a[6], ff{p1.z, 0.f});
+    np += __float_as_int(p1.w);
   }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int k = 0; k < K; k++) sh[threadIdx.x][k] = a[k];
+  for (int k = 0; k < K; k++)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      a[k] = ff_add(a[k], ff{__shfl_down_sync(0xffffffffu, a[k].hi, o), __shfl_down_sync(0xffffffffu, a[k].lo, o)});
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) np += __shfl_down_sync(0xffffffffu, np, o);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      shh[warp][k] = a[k].hi;
+      shl[warp][k] = a[k].lo;
+    }
+    shn[warp] = np;
+  }
   __syncthreads();
-  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-    if ((int)threadIdx.x < st)
-#pragma unroll
-      for (int k = 0; k < K; k++) sh[threadIdx.x][k] += sh[threadIdx.x + st][k];
-    __syncthreads();
+  double sh0[K + 1];
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < K; k++) {
+      double x = 0.0;
+      for (int w = 0; w < kW; w++) x += (double)shh[w][k] + (double)shl[w][k];
+      sh0[k] = x;
+    }
+    long long n2 = 0;
+    for (int w = 0; w < kW; w++) n2 += shn[w];
+    sh0[K] = (double)n2;
   }
   if (threadIdx.x == 0) {
     double Wr[9];
-    Wr[0] = 0.5 * sh[0][1];
-    Wr[4] = 0.5 * sh[0][2];
-    Wr[8] = 0.5 * sh[0][3];
-    Wr[1] = Wr[3] = 0.5 * sh[0][4];
-    Wr[2] = Wr[6] = 0.5 * sh[0][5];
-    Wr[5] = Wr[7] = 0.5 * sh[0][6];
+    Wr[0] = 0.5 * sh0[1];
+    Wr[4] = 0.5 * sh0[2];
+    Wr[8] = 0.5 * sh0[3];
+    Wr[1] = Wr[3] = 0.5 * sh0[4];
+    Wr[2] = Wr[6] = 0.5 * sh0[5];
+    Wr[5] = Wr[7] = 0.5 * sh0[6];
     double W[9];
     if (g->variant == NEMD_DO) {
       double T9[9];
@@ -496,10 +521,10 @@ __global__ void __launch_bounds__(256) k_b_reduce(BatchView v) {
       for (int k = 0; k < 9; k++) W[k] = Wr[k];
     }
     if (v.UW) {
-      v.UW[10 * (size_t)s] = ok ? 0.5 * sh[0][0] : 0.0;
+      v.UW[10 * (size_t)s] = ok ? 0.5 * sh0[0] : 0.0;
       for (int k = 0; k < 9; k++) v.UW[10 * (size_t)s + 1 + k] = ok ? W[k] : 0.0;
     }
-    v.sys_pairs[s] = (unsigned long long)(0.5 * sh[0][7] + 0.25);
+    v.sys_pairs[s] = (unsigned long long)(0.5 * sh0[7] + 0.25);
     g->sticky |= g->error;
   }
 }
