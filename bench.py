@@ -63,8 +63,8 @@ C_PAIR = 24    # FP32 instructions per interacting pair (force, energy, virial, 
 # DRAM bytes (read + write) of one k_force_warp launch on the N = 2^20 system,
 # from the ncu capture summarised in profiles/k_force_warp_general_n1m.md; valid
 # only while the kernel's sources are the ones captured (sha1 prefixes).
-WARP_TRAFFIC = {"bytes": 39.407104e6 + 0.407552e6,
-                "sha1": {"paper_1412_3784_gb300/csrc/force_warp.cu": "e3ccfad894aa",
+WARP_TRAFFIC = {"bytes": 39.401472e6 + 0.320768e6,
+                "sha1": {"paper_1412_3784_gb300/csrc/force_warp.cu": "0f4e047dcf2b",
                          "paper_1412_3784_gb300/csrc/force_common.cuh": "2c912e007080"}}
 
 

@@ -33,18 +33,19 @@ namespace nemd {
 
 // Shape of the kernel (compile-time): threads per block, staged particles per
 // warp, queue entries per lane, resident blocks the register allocation aims
-// at.  Measured on GB300 (N = 2^20 general flow): 224 staged particles and five
-// blocks of four warps per SM (96 registers, 43 KB of shared memory per block)
-// beat 256 particles at four blocks by 16 %; more staging at fewer resident
-// warps and less staging at more are both slower.
+// at.  Measured on GB300 (N = 2^20 general flow): five blocks of four warps per
+// SM (96 registers, 45 KB of shared memory per block) beat 256 particles at
+// four blocks by 16 %; within the same shared memory, 208 staged particles and
+// an 80-entry queue beat 224 and 64 by 5.5 % (fewer, fuller flushes), while
+// queues of 96-128 entries with 192-160 staged particles are slower again.
 #ifndef NEMD_WARP_THREADS
 #define NEMD_WARP_THREADS 128
 #endif
 #ifndef NEMD_WARP_STAGE
-#define NEMD_WARP_STAGE 224
+#define NEMD_WARP_STAGE 208
 #endif
 #ifndef NEMD_WARP_QUEUE
-#define NEMD_WARP_QUEUE 64
+#define NEMD_WARP_QUEUE 80
 #endif
 #ifndef NEMD_WARP_MINBLOCKS
 #define NEMD_WARP_MINBLOCKS 5
