@@ -10,8 +10,9 @@
 // p = 0 a particle moves affinely with the box, q = L_t s at fixed s).  The
 // rescale multiplies p by sqrt(K0 / sum |p|^2) (isokinetic; K0 the initial
 // sum), or is skipped.  Sums of |p|^2 are per-block float64 partials added in
-// a fixed order, so a run repeats bit for bit.  The paper gives no integrator:
-// this is the reading stated with nemd_integrate in include/nemd.h.
+// a fixed order by the last block of each kick, so a run repeats bit for bit.
+// The paper gives no integrator: this is the reading stated with
+// nemd_integrate in include/nemd.h.
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -27,7 +28,7 @@ namespace {
 constexpr int kIntThreads = 256;
 // int_state layout (doubles)
 constexpr int kE = 0, kEh = 9, kPhi = 18, kK0 = 27, kScale = 28, kH = 29, kThermo = 30, kT0 = 31, kDt = 32,
-              kStep = 33, kTnow = 34, kIntState = 36;
+              kStep = 33, kTnow = 34, kTicket = 35, kIntState = 36;
 
 // The flow matrix by value.
 struct Mat9 {
@@ -100,14 +101,7 @@ __global__ void k_int_setup(double *st, Mat9 A, double t0, double dt, int thermo
   st[kDt] = dt;
   st[kStep] = 0.0;
   st[kTnow] = t0;
-}
-
-// Advance the clock one step: t = t0 + k dt (each operation rounded once).
-__global__ void k_int_tick(double *st) {
-  if (threadIdx.x != 0) return;
-  const double k = st[kStep] + 1.0;
-  st[kStep] = k;
-  st[kTnow] = __dadd_rn(st[kT0], __dmul_rn(k, st[kDt]));
+  *reinterpret_cast<unsigned long long *>(st + kTicket) = 0ull;
 }
 
 // Per-block partial of sum |p|^2 (fixed grid-stride order, shuffle tree).
@@ -131,17 +125,38 @@ __global__ void __launch_bounds__(kIntThreads) k_int_p2(const double *__restrict
   block_p2(x, part);
 }
 
-// mode 0: K0 = sum of the partials; 1: scale = sqrt(K0 / sum) when thermostatted
-__global__ void k_int_sum(double *st, const double *part, int nb, int mode) {
+// K0 = sum of the partials (block order); no rescale before the first kick
+__global__ void k_int_k0(double *st, const double *part, int nb) {
   if (threadIdx.x != 0) return;
   double y = 0.0;
   for (int b = 0; b < nb; b++) y += part[b];
-  if (mode == 0) {
-    st[kK0] = y;
-    st[kScale] = 1.0;
-  } else {
-    st[kScale] = (st[kThermo] != 0.0 && y > 0.0) ? sqrt(st[kK0] / y) : 1.0;
+  st[kK0] = y;
+  st[kScale] = 1.0;
+}
+
+// After every block has written its partial of sum |p|^2: the last block to
+// arrive (ticket in st, returned to zero) sets the rescale factor from the
+// partials in block order and, with tick, advances the clock one step,
+// t = t0 + k dt (each operation rounded once).
+template <bool TICK>
+__device__ __forceinline__ void last_block_scale(double *st, const double *part) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0)
+    last = atomicAdd(reinterpret_cast<unsigned long long *>(st + kTicket), 1ull) == (unsigned long long)(gridDim.x - 1);
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  double y = 0.0;
+  for (int b = 0; b < (int)gridDim.x; b++) y += __ldcg(part + b);
+  st[kScale] = (st[kThermo] != 0.0 && y > 0.0) ? sqrt(st[kK0] / y) : 1.0;
+  if (TICK) {
+    const double k = st[kStep] + 1.0;
+    st[kStep] = k;
+    st[kTnow] = __dadd_rn(st[kT0], __dmul_rn(k, st[kDt]));
   }
+  *reinterpret_cast<unsigned long long *>(st + kTicket) = 0ull;
 }
 
 __device__ __forceinline__ void mv3(const double *M, double x, double y, double z, double &ox, double &oy,
@@ -151,9 +166,10 @@ __device__ __forceinline__ void mv3(const double *M, double x, double y, double 
   oz = (M[6] * x + M[7] * y) + M[8] * z;
 }
 
-// first half: p <- exp(-A h) (scale p + h F); partial sum |p|^2
+// first half: p <- exp(-A h) (scale p + h F); the new rescale factor, and the
+// clock advanced to the step's end time
 __global__ void __launch_bounds__(kIntThreads) k_int_kick1(double *__restrict__ p, const float *__restrict__ F,
-                                                           int n, const double *__restrict__ st, double *part) {
+                                                           int n, double *st, double *part) {
   const double h = st[kH], sc = st[kScale];
   double x2 = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -168,10 +184,14 @@ __global__ void __launch_bounds__(kIntThreads) k_int_kick1(double *__restrict__ 
     x2 += (ox * ox + oy * oy) + oz * oz;
   }
   block_p2(x2, part);
+  last_block_scale<true>(st, part);
 }
 
 // drift: p <- scale p; q <- exp(A dt) q + Phi p, then q wrapped into the unit
-// cell of the lattice already evolved to the new time (g)
+// cell of the lattice already evolved to the new time (g).  A particle whose
+// fractional coordinates (estimated in float32, error ~1e-6) lie within
+// [1e-3, 1 - 1e-3] is inside the cell already and keeps its drifted q; the
+// others take the float64 wrap q = L frac(L^-1 q)
 __global__ void __launch_bounds__(kIntThreads) k_int_drift(double *__restrict__ q, double *__restrict__ p, int n,
                                                            const double *__restrict__ st, const Geo *g) {
   const double sc = st[kScale];
@@ -183,18 +203,32 @@ __global__ void __launch_bounds__(kIntThreads) k_int_drift(double *__restrict__ 
     double ex, ey, ez, fx, fy, fz;
     mv3(st + kE, q[3 * (size_t)i], q[3 * (size_t)i + 1], q[3 * (size_t)i + 2], ex, ey, ez);
     mv3(st + kPhi, px, py, pz, fx, fy, fz);
-    double s[3], qp[3];
-    frac_wrap(g->Linv, ex + fx, ey + fy, ez + fz, s);
-    frac_to_cart(g->L, s, qp);
-    q[3 * (size_t)i] = qp[0];
-    q[3 * (size_t)i + 1] = qp[1];
-    q[3 * (size_t)i + 2] = qp[2];
+    const double xx = ex + fx, yy = ey + fy, zz = ez + fz;
+    const float xf = __double2float_rn(xx), yf = __double2float_rn(yy), zf = __double2float_rn(zz);
+    bool inside = true;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      const float sa = fmaf(g->Linvff[3 * a + 2].x, zf, fmaf(g->Linvff[3 * a + 1].x, yf, g->Linvff[3 * a].x * xf));
+      inside = inside && sa > 1e-3f && sa < 0.999f;
+    }
+    if (inside) {
+      q[3 * (size_t)i] = xx;
+      q[3 * (size_t)i + 1] = yy;
+      q[3 * (size_t)i + 2] = zz;
+    } else {
+      double s[3], qp[3];
+      frac_wrap(g->Linv, xx, yy, zz, s);
+      frac_to_cart(g->L, s, qp);
+      q[3 * (size_t)i] = qp[0];
+      q[3 * (size_t)i + 1] = qp[1];
+      q[3 * (size_t)i + 2] = qp[2];
+    }
   }
 }
 
-// second half: p <- h F + exp(-A h) p; partial sum |p|^2
+// second half: p <- h F + exp(-A h) p; the new rescale factor
 __global__ void __launch_bounds__(kIntThreads) k_int_kick2(double *__restrict__ p, const float *__restrict__ F,
-                                                           int n, const double *__restrict__ st, double *part) {
+                                                           int n, double *st, double *part) {
   const double h = st[kH];
   double x2 = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -209,6 +243,7 @@ __global__ void __launch_bounds__(kIntThreads) k_int_kick2(double *__restrict__ 
     x2 += (ox * ox + oy * oy) + oz * oz;
   }
   block_p2(x2, part);
+  last_block_scale<false>(st, part);
 }
 
 __global__ void __launch_bounds__(kIntThreads) k_int_final(double *__restrict__ p, int n,
@@ -254,20 +289,17 @@ int int_state_at_clock(nemd_ctx *c, double *q, int64_t n, double t_host) {
   return NEMD_OK;
 }
 
-// One step after the first: clock, first kick, lattice at the new time,
-// drift and wrap, the force evaluation, second kick.
+// One step: first kick (which also advances the device clock), lattice at the
+// new time, drift and wrap, the force evaluation, second kick.
 int int_step(nemd_ctx *c, double *q, double *p, int64_t n, double t_host, int variant, double rc, int nb) {
   int r;
-  k_int_tick<<<1, 32, 0, c->stream>>>(c->int_state);
   k_int_kick1<<<nb, kIntThreads, 0, c->stream>>>(p, c->f_int, (int)n, c->int_state, c->int_part);
-  k_int_sum<<<1, 32, 0, c->stream>>>(c->int_state, c->int_part, nb, 1);
   if ((r = int_state_at_clock(c, q, n, t_host))) return r;
   k_int_drift<<<nb, kIntThreads, 0, c->stream>>>(q, p, (int)n, c->int_state, c->geo);
   if ((r = nemd_build_cells(c, variant, rc))) return r;
   if ((r = nemd_compute_forces(c, c->f_int, nullptr, nullptr))) return r;
   k_int_kick2<<<nb, kIntThreads, 0, c->stream>>>(p, c->f_int, (int)n, c->int_state, c->int_part);
-  k_int_sum<<<1, 32, 0, c->stream>>>(c->int_state, c->int_part, nb, 1);
-  c->launches += 6;
+  c->launches += 3;
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? NEMD_OK : int_err(c, NEMD_ERR_CUDA, "integrate: %s", cudaGetErrorString(e));
 }
@@ -311,7 +343,7 @@ int nemd_integrate(nemd_ctx *c, double *q, double *p, int64_t n, double t0, doub
   do {
     if ((r = nemd_set_state(c, q, n, t0))) break;
     k_int_p2<<<nb, kIntThreads, 0, c->stream>>>(p, (int)n, c->int_part);
-    k_int_sum<<<1, 32, 0, c->stream>>>(c->int_state, c->int_part, nb, 0);
+    k_int_k0<<<1, 32, 0, c->stream>>>(c->int_state, c->int_part, nb);
     c->launches += 2;
     if ((r = nemd_build_cells(c, variant, rc))) break;
     if ((r = nemd_compute_forces(c, c->f_int, nullptr, nullptr))) break;
