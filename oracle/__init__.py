@@ -2,7 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY: tests, the smoke check and the benchmark's
 CPU-baseline leg use it; the product path never does.  The C code in
-oracle.c states, per function, the passage of the paper it follows.
+oracle.c states, per function, the passage of the paper it follows; the
+time-integration oracle is in oracle/integrate.py.
 """
 from __future__ import annotations
 
