@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Bars (stated with the benchmark spec's targets):
+Bars:
   pair sets            bit-exact (i, j, n) against the oracle
   forces               max|dF| / max|F| <= 1e-5   (float32 pair arithmetic)
   energy, virial       rel <= 1e-9 in precise mode (float64 accepted pairs);
