@@ -10,8 +10,12 @@ mathematics fixes, independent of the oracle's own formulas:
   solution q(t) = exp(tA) q0 + V diag(sinh(t lam)/lam) V^T p0;
 * A = 0, no thermostat (velocity Verlet): energy error O(dt^2) and exact time
   reversibility;
+* no forces under Lees-Edwards shear (A^2 = 0): the closed form
+  p = (I - tA) p0, q = (I + tA) q0 + t p0, across the centred remap;
 * isokinetic thermostat: |p|^2 stays at its initial value.
 """
+from dataclasses import replace
+
 import numpy as np
 import pytest
 
@@ -92,6 +96,29 @@ def test_free_flight_momenta_exact_positions_second_order():
     assert errs[0] > 0
     r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
     assert 3.5 < r1 < 4.5 and 3.5 < r2 < 4.5, errs
+
+
+def test_free_flight_under_shear_closed_form():
+    """Lees-Edwards shear (A = g e_x e_y^T, A^2 = 0), no forces, no thermostat:
+    p(t) = (I - tA) p0 and q(t) = (I + tA) q0 + t p0 exactly, modulo the
+    lattice; the splitting is exact here (every propagator is a polynomial of
+    degree one in A), and the centred remap of Sec. 2.2 is crossed."""
+    sh = W.shear_series(k=2, seed=3, rate=0.9)
+    w = replace(sh.workload(0.3 * sh.period), rc=0.05)
+    rng = np.random.default_rng(12)
+    p0 = 0.01 * rng.normal(size=(w.n, 3))
+    lat0 = oracle.lattice(w.A, w.L0, w.T, w.t, centered=True)
+    _, q0 = oracle.wrap(lat0["L"], lat0["Linv"], w.q)
+    dt, m = sh.period / 17.0, 20                      # crosses t = T/2 (the remap)
+    q, p, t = OI.integrate(w, p0, dt, m, thermostat=False)
+    tt = t - w.t
+    pe = p0 @ (np.eye(3) - tt * w.A).T
+    qe = q0 @ (np.eye(3) + tt * w.A).T + tt * p0
+    assert np.abs(p - pe).max() <= 1e-14
+    lat = oracle.lattice(w.A, w.L0, w.T, t, centered=True)
+    d = (q - qe) @ lat["Linv"].T
+    d -= np.rint(d)
+    assert np.abs(d @ lat["L"].T).max() <= 1e-12
 
 
 def _equilibrium(kind, seed=11):
