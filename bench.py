@@ -382,7 +382,11 @@ def section_main(args, rank, world, dev, torch, nemd, W):
                 "kernel": kernel_name.get(tuned_kernel, "?"), "ops_per_launch": ops_per_launch,
                 "avg_launch_ms": avg_launch_s * 1e3,
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x {peak_mhz:.0f} MHz (FP32 instruction "
-                              f"lane-ops/s; derived from unit counts and the clock, not measured)"}
+                              f"lane-ops/s; derived from unit counts and the clock, not measured)",
+                # the force kernel alone, and the ideal roofline that counts only the
+                # pair arithmetic (C_PAIR per interacting pair, no candidate tests)
+                "force_kernel_pairs_per_s": (pairs_per_step / S) / avg_launch_s,
+                "pair_only_frac": (C_PAIR * pairs_per_step / S) / avg_launch_s / peak}
 
     # end to end through the C ABI with pinned host buffers
     # Se strains spread evenly over the period, so that the e2e workload has
