@@ -7,7 +7,9 @@
  *
  * One force evaluation is the call sequence
  *     nemd_set_state(q, t)  ->  nemd_build_cells(variant, rc)  ->  nemd_compute_forces(F, U, W)
- * after a one-time nemd_set_flow(A, L0, M, T) and nemd_set_potential(...).
+ * after a one-time nemd_set_flow(A, L0, M, T) and nemd_set_potential(...);
+ * nemd_integrate steps positions and momenta through many such evaluations,
+ * and nemd_batch_* evaluates many independent systems at once.
  * Every step runs as CUDA kernels on the context's stream:
  *   set_state      lattice L(t) = exp(A (t mod T)) L0, its inverse, heights, QR  (Sec. 2.1, 2.2)
  *   build_cells    cell grid and neighbour stencil from the deformed metric,
