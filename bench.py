@@ -61,7 +61,7 @@ C_TEST = 7     # FP32 instructions per candidate test: 3 FADD, 1 FMUL, 2 FFMA, 1
 C_PAIR = 24    # FP32 instructions per interacting pair (force, energy, virial, both sides)
 
 # DRAM bytes (read + write) of one k_force_warp launch on the N = 2^20 system,
-# from the ncu capture summarised in profiles/k_force_warp_general_n1m.md; valid
+# from one ncu capture of that launch (dram__bytes_read.sum + dram__bytes_write.sum); valid
 # only while the kernel's sources are the ones captured (sha1 prefixes).
 WARP_TRAFFIC = {"bytes": 39.401472e6 + 0.320768e6,
                 "sha1": {"paper_1412_3784_gb300/csrc/force_warp.cu": "0f4e047dcf2b",

@@ -33,6 +33,20 @@ def test_kr_identity(M):
     assert np.abs(lat["L"] - L0 @ M).max() / 33.59 < 1e-13
 
 
+@pytest.mark.parametrize("M", [W.M_PLANAR, W.M_GENERAL])
+def test_kr_residual_flags_a_non_kr_flow(M):
+    """The residual of Eq. kr is large when exp(A T) L0 is not L0 M: a flow
+    rate 10 % off, a period 10 % off and a different M all fail it."""
+    A, _, _ = W.kr_flow(M)
+    L0 = 33.59 * np.eye(3)
+    assert oracle.kr_residual(1.1 * A, L0, M, 1.0) > 1e-3
+    assert oracle.kr_residual(A, L0, M, 1.1) > 1e-3
+    other = W.M_GENERAL if M is W.M_PLANAR else W.M_PLANAR
+    assert oracle.kr_residual(A, L0, other, 1.0) > 1e-3
+    # the residual is relative to |L0|: the same flow on a scaled box is still KR
+    assert oracle.kr_residual(A, 7.0 * L0, M, 1.0) < 1e-14
+
+
 @pytest.mark.parametrize("seed", range(4))
 def test_expm_against_scipy(seed):
     """Both expm paths (Jacobi for symmetric A, Pade otherwise) against scipy's expm."""
@@ -361,6 +375,55 @@ def test_do_tight_rule_within_fixed_rule():
             assert cnt <= oracle.do_fixed_count(l, iy, iz)
         if t == 0.0:
             assert set(per.values()) == {27}
+
+
+def test_do_total_stencil_cells():
+    """The dynamic offset search-volume count is 27 l1 l2 l3 in an undeformed box
+    and, at every strain, l1 times the number of cells in the stencil rows of
+    every (iy, iz) class (Sec. 5.2: each of the l1 home cells of a class has the
+    class's neighbourhood)."""
+    A, _, _ = W.kr_flow(W.M_GENERAL)
+    L0 = 40.0 * np.eye(3)
+    for kfac in (1, 2):
+        lat = oracle.lattice(A, L0, 1.0, 0.0)
+        l = oracle.do_counts(lat["R"], 2.5, kfac)
+        side = (2 * kfac + 1) ** 3
+        assert oracle.do_total_stencil_cells(lat["R"], 2.5, kfac) == side * int(np.prod(l))
+    for t in (0.13, 0.5, 0.77, W.NEAR_REMAP_T):
+        lat = oracle.lattice(A, L0, 1.0, t)
+        l, rows = oracle.do_stencil(lat["R"], 2.5)
+        total = int(sum((hi - lo + 1) for _, _, _, _, lo, hi in rows)) * int(l[0])
+        assert oracle.do_total_stencil_cells(lat["R"], 2.5) == total
+        # every home class has its rows, so the count lies between 27 and 36 cells
+        # per home cell (the paper's four cases)
+        ncell = int(np.prod(l))
+        assert 27 * ncell <= total <= 36 * ncell
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_sample_forces_equal_brute_force_rows(seed):
+    """Particle-by-particle brute force (forces, neighbour counts, half energies
+    of sampled particles) equals the rows of the all-pairs brute force on small
+    skewed boxes, including self-image pairs in boxes of one to three cut-offs."""
+    rng = np.random.default_rng(300 + seed)
+    rc = 1.3
+    L, q = W.small_random_box(rng, 50, rc, 1.0, 3.0)
+    s, qp = oracle.wrap(L, np.linalg.inv(L), q)
+    rb = oracle.brute(L, s, qp, rc)
+    n = q.shape[0]
+    cnt = np.zeros(n, dtype=np.int64)
+    for i, j, *_ in rb.pairs:
+        cnt[i] += 1
+        cnt[j] += 1
+    idx = np.arange(n, dtype=np.int64)
+    F, c, uh = oracle.sample_forces(L, s, qp, idx, rc)
+    assert np.array_equal(c, cnt)
+    assert np.abs(F - rb.F).max() <= 1e-12 * max(1.0, np.abs(rb.F).max())
+    assert abs(uh.sum() - rb.U) <= 1e-12 * max(1.0, abs(rb.U))
+    # a subset in another order gives the same rows
+    sub = rng.permutation(n)[:7]
+    F2, c2, _ = oracle.sample_forces(L, s, qp, sub, rc)
+    assert np.array_equal(c2, cnt[sub]) and np.abs(F2 - F[sub]).max() == 0.0
 
 
 def test_search_efficiency_equilibrium():
