@@ -87,8 +87,10 @@ typedef enum nemd_option {
                                    memory), 3 warp with half neighbourhoods (each
                                    unordered pair evaluated once, partner forces added
                                    with atomics: F is not bitwise reproducible from run
-                                   to run; pair records use kernel 2).  1-3 need k <= 2,
-                                   otherwise the plain kernel runs                         */
+                                   to run; pair records use kernel 2), 4 row (one chunk of
+                                   32 per warp, each lane testing only its own window
+                                   along the row, coarse test in half precision).  1-4
+                                   need k <= 2, otherwise the plain kernel runs            */
     NEMD_OPT_CELL_FACTOR = 4,   /* k >= 1: cells at least rc/k wide, stencil reach k    */
     NEMD_OPT_BLOCK = 5,         /* threads per block of the force kernel (multiple of 32) */
     NEMD_OPT_TIMING = 6,        /* 1: record CUDA events around every force-kernel launch
@@ -237,7 +239,7 @@ int nemd_get_kernel_time(nemd_ctx *ctx, double *ms_total, int64_t *nlaunch);
  *
  * The paper has no counterpart (its cells are always at least the cut-off
  * wide, Sec. 4).  Every candidate configuration -- force kernel (plain, warp,
- * warp with half neighbourhoods, grouped), lanes per group (4, 8, 16),
+ * warp with half neighbourhoods, grouped, row), lanes per group (4, 8, 16),
  * cell-size factor k (1, 2) -- gives the same pair set and, up to rounding,
  * the same forces; only the time differs. */
 typedef struct nemd_tune_config {
@@ -463,7 +465,9 @@ int nemd_batch_autotune(nemd_batch *b, int reps, nemd_tune_entry *times, int cap
  * 10 float64, DEVICE, receives U then W (row-major); status -- optional int,
  * DEVICE, receives the deferred device error bits (0 = OK, 1 = box too small,
  * 2 = non-finite position, 4 = capacity); stream -- a cudaStream_t (NULL =
- * legacy default stream).  All work is asynchronous on `stream`. */
+ * legacy default stream).  All work is asynchronous on `stream`.  q, F, UW and
+ * status must be memory of the current device (or managed memory); a pointer
+ * of another device or of the host is refused with NEMD_ERR_ARG. */
 #define NEMD_NOALLOC_MAX_N 16384
 #define NEMD_NOALLOC_MAX_CELLS 16384
 #define NEMD_NOALLOC_SCRATCH_BYTES 11154432

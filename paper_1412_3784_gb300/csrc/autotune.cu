@@ -21,9 +21,9 @@ struct Candidate {
 };
 
 // plain kernel; warp kernel at k = 1, 2; grouped kernel with 4, 8, 16 lanes at
-// k = 1, 2; warp kernel with half neighbourhoods at k = 1, 2
-const Candidate kCandidates[] = {{0, 16, 1}, {2, 32, 1}, {2, 32, 2}, {1, 4, 1}, {1, 8, 1},  {1, 16, 1},
-                                 {1, 4, 2},  {1, 8, 2},  {1, 16, 2}, {3, 32, 1}, {3, 32, 2}};
+// k = 1, 2; warp kernel with half neighbourhoods at k = 1, 2; row kernel at k = 1, 2
+const Candidate kCandidates[] = {{0, 16, 1}, {2, 32, 1}, {2, 32, 2}, {1, 4, 1},  {1, 8, 1},  {1, 16, 1}, {1, 4, 2},
+                                 {1, 8, 2},  {1, 16, 2}, {3, 32, 1}, {3, 32, 2}, {4, 32, 1}, {4, 32, 2}};
 constexpr int kNumCandidates = sizeof(kCandidates) / sizeof(kCandidates[0]);
 static_assert(kNumCandidates == nemd::kTuneCandidates, "cache layout");
 
@@ -168,7 +168,7 @@ int nemd_autotune(nemd_ctx *c, int variant, double rc, int reps, nemd_tune_confi
 // u64 FNV-1a of everything before it.
 int nemd_tune_save(nemd_ctx *c, const char *path) {
   if (!c || !path) return NEMD_ERR_ARG;
-  const uint32_t version = 1, count = (uint32_t)c->ntune, ncand = kNumCandidates;
+  const uint32_t version = 2, count = (uint32_t)c->ntune, ncand = kNumCandidates;
   size_t n = 8 + 12 + (size_t)count * sizeof(nemd::TuneEntry);
   unsigned char *buf = (unsigned char *)malloc(n + 8);
   if (!buf) return NEMD_ERR_NOMEM;
@@ -203,7 +203,7 @@ int nemd_tune_load(nemd_ctx *c, const char *path) {
   memcpy(&version, head + 8, 4);
   memcpy(&count, head + 12, 4);
   memcpy(&ncand, head + 16, 4);
-  if (version != 1 || ncand != (uint32_t)kNumCandidates || count > (uint32_t)nemd::kMaxTuneClasses) {
+  if (version != 2 || ncand != (uint32_t)kNumCandidates || count > (uint32_t)nemd::kMaxTuneClasses) {
     fclose(f);
     return NEMD_ERR_ARG;
   }

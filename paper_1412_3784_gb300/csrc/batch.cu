@@ -135,9 +135,9 @@ cudaError_t enqueue_step(nemd_batch *b, cudaStream_t st) {
   return nemd::launch_batch_finish(st, v);
 }
 
-// lattice, grid, stencil, bin (wrap, 3 scan, scatter, sort, pack), chunks
+// lattice, grid, stencil, bin (wrap, 3 scan, scatter, sort and pack), chunks
 // (count, 3 scan, write), force, fix-up, reduce
-constexpr int64_t kStepLaunches = 3 + 7 + 5 + 1 + 2;
+constexpr int64_t kStepLaunches = 3 + 6 + 5 + 1 + 2;
 
 }  // namespace
 

@@ -10,9 +10,12 @@
 //               step's quantum plus a float32 residual, rank = atomicAdd(count[cell])
 //   k_scan_*    exclusive scan of the per-cell counts -> start[]
 //   k_scatter   perm[start[cell] + rank] = i
-//   k_cellsort  per cell, particles in increasing input index (stable order,
-//               so sums are reproducible from run to run)
-//   k_pack      sorted float4 {rel position, input index}, residuals, cell ids
+//   k_sortpack  one warp per cell: the cell's particles in increasing kappa
+//               (the coordinate along the x-row of cells), ties by input index,
+//               written as sorted float4 {rel position, input index},
+//               {residual, kappa} and cell ids.  The order depends only on the
+//               positions, so sums are reproducible from run to run, and every
+//               x-row of cells is one kappa-sorted run of particles.
 #include <math.h>
 
 #include "batch_internal.cuh"
@@ -103,8 +106,11 @@ __device__ __forceinline__ void wrap_body(Geo *g, const double *__restrict__ q, 
   }
   const int cell = cell_base + idx[0] + l1 * (idx[1] + l2 * idx[2]);
   (void)l3;
+  // kappa of the quantised position: the cell-units coordinate along the
+  // x-row, in [-1/2, 1/2] inside the cell (the within-cell sort key)
+  const float kap = fmaf(g->kap[2], rq[2], fmaf(g->kap[1], rq[1], g->kap[0] * rq[0]));
   relc[i] = make_float4(rq[0], rq[1], rq[2], __int_as_float(cell));
-  relr[i] = make_float4(rr[0], rr[1], rr[2], 0.0f);
+  relr[i] = make_float4(rr[0], rr[1], rr[2], kap);
   rank[i] = atomicAdd(&count[cell], 1);
 }
 
@@ -217,38 +223,64 @@ __global__ void k_scatter(const Geo *g, const float4 *__restrict__ relc, const i
   perm[start[cell] + rank[i]] = i;
 }
 
-// Insertion sort of one cell's slice of perm (cells hold a few tens of particles).
-__device__ __forceinline__ void cellsort_body(const int *__restrict__ start, int *__restrict__ perm, int c) {
-  const int b = start[c], e = start[c + 1];
-  for (int k = b + 1; k < e; k++) {
-    int v = perm[k];
-    int j = k - 1;
-    while (j >= b && perm[j] > v) {
-      perm[j + 1] = perm[j];
-      j--;
+// (kappa, input index) of particle i: the within-cell order.
+__device__ __forceinline__ bool sort_before(float ka, int ia, float kb, int ib) {
+  return ka < kb || (ka == kb && ia < ib);
+}
+
+// One warp sorts cell c (its slice of perm, in arrival order) by (kappa, input
+// index) and writes the sorted slots.  The rank of each particle is the number
+// of particles of the cell that sort before it (one comparison per pair, the
+// cell's keys staged in shared memory); cells longer than kSortStage compare
+// against global memory instead.
+constexpr int kSortWarps = 8;
+constexpr int kSortStage = 128;
+
+__device__ __forceinline__ void sortpack_cell(const int *__restrict__ start, const int *__restrict__ perm,
+                                              const float4 *__restrict__ relc, const float4 *__restrict__ relr,
+                                              float4 *__restrict__ pos4, float4 *__restrict__ posr,
+                                              int *__restrict__ cell_sorted, int c, float *skey, int *sidx,
+                                              int lane) {
+  const int b = start[c], n = start[c + 1] - b;
+  if (n <= 0) return;
+  const bool staged = n <= kSortStage;
+  __syncwarp();
+  if (staged)
+    for (int t = lane; t < n; t += 32) {
+      const int i = perm[b + t];
+      sidx[t] = i;
+      skey[t] = relr[i].w;
     }
-    perm[j + 1] = v;
+  __syncwarp();
+  for (int t = lane; t < n; t += 32) {
+    const int i = staged ? sidx[t] : perm[b + t];
+    const float k = staged ? skey[t] : relr[i].w;
+    int rank = 0;
+    for (int m = 0; m < n; m++) {
+      const int im = staged ? sidx[m] : perm[b + m];
+      const float km = staged ? skey[m] : relr[im].w;
+      rank += sort_before(km, im, k, i) ? 1 : 0;
+    }
+    const float4 r = relc[i];
+    pos4[b + rank] = make_float4(r.x, r.y, r.z, __int_as_float(i));
+    posr[b + rank] = relr[i];
+    cell_sorted[b + rank] = __float_as_int(r.w);
   }
 }
 
-__global__ void k_cellsort(const Geo *g, const int *__restrict__ start, int *__restrict__ perm) {
+__global__ void __launch_bounds__(32 * kSortWarps) k_sortpack(const Geo *g, const int *__restrict__ start,
+                                                                const int *__restrict__ perm,
+                                                                const float4 *__restrict__ relc,
+                                                                const float4 *__restrict__ relr,
+                                                                float4 *__restrict__ pos4, float4 *__restrict__ posr,
+                                                                int *__restrict__ cell_sorted) {
+  __shared__ float skey[kSortWarps][kSortStage];
+  __shared__ int sidx[kSortWarps][kSortStage];
   if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ncells = g->ncells;
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x)
-    cellsort_body(start, perm, c);
-}
-
-__global__ void k_pack(const Geo *g, const float4 *__restrict__ relc, const float4 *__restrict__ relr,
-                       const int *__restrict__ perm, float4 *__restrict__ pos4, float4 *__restrict__ posr,
-                       int *__restrict__ cell_sorted, int n) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
-  const int i = perm[k];
-  const float4 r = relc[i];
-  pos4[k] = make_float4(r.x, r.y, r.z, __int_as_float(i));
-  posr[k] = relr[i];
-  cell_sorted[k] = __float_as_int(r.w);
+  for (int c = blockIdx.x * kSortWarps + warp; c < ncells; c += gridDim.x * kSortWarps)
+    sortpack_cell(start, perm, relc, relr, pos4, posr, cell_sorted, c, skey[warp], sidx[warp], lane);
 }
 
 cudaError_t launch_bin(nemd_ctx *c) {
@@ -270,11 +302,11 @@ cudaError_t launch_bin(nemd_ctx *c) {
     const int tb = 256;
     const int nb = (n + tb - 1) / tb;
     k_scatter<<<nb, tb, 0, c->stream>>>(c->geo, c->relc, c->rank, c->start, c->perm, n);
-    int64_t cb = (c->cap_cells + 255) / 256;
-    if (cb > 8 * (int64_t)c->sms) cb = 8 * (int64_t)c->sms;
-    k_cellsort<<<(int)cb, 256, 0, c->stream>>>(c->geo, c->start, c->perm);
-    k_pack<<<nb, tb, 0, c->stream>>>(c->geo, c->relc, c->relr, c->perm, c->pos4, c->posr, c->cell_sorted, n);
-    c->launches += 3;
+    int64_t cb = (c->cap_cells + kSortWarps - 1) / kSortWarps;
+    if (cb > 16 * (int64_t)c->sms) cb = 16 * (int64_t)c->sms;
+    k_sortpack<<<(int)cb, 32 * kSortWarps, 0, c->stream>>>(c->geo, c->start, c->perm, c->relc, c->relr, c->pos4,
+                                                            c->posr, c->cell_sorted);
+    c->launches += 2;
   }
   return cudaGetLastError();
 }
@@ -367,20 +399,13 @@ __global__ void k_b_scatter(BatchView v) {
   v.perm[v.start[cell] + v.rank[i]] = i;
 }
 
-__global__ void k_b_cellsort(BatchView v) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < v.ncells; c += gridDim.x * blockDim.x)
-    cellsort_body(v.start, v.perm, c);
-}
-
-// Sorted slots [0, start[ncells]): the particles of every system that binned.
-__global__ void k_b_pack(BatchView v) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= v.start[v.ncells]) return;
-  const int i = v.perm[k];
-  const float4 r = v.relc[i];
-  v.pos4[k] = make_float4(r.x, r.y, r.z, __int_as_float(i));
-  v.posr[k] = v.relr[i];
-  v.cell_sorted[k] = __float_as_int(r.w);
+// Every system's cells (the cell slots of all systems are one array).
+__global__ void __launch_bounds__(32 * kSortWarps) k_b_sortpack(BatchView v) {
+  __shared__ float skey[kSortWarps][kSortStage];
+  __shared__ int sidx[kSortWarps][kSortStage];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c = blockIdx.x * kSortWarps + warp; c < v.ncells; c += gridDim.x * kSortWarps)
+    sortpack_cell(v.start, v.perm, v.relc, v.relr, v.pos4, v.posr, v.cell_sorted, c, skey[warp], sidx[warp], lane);
 }
 
 cudaError_t launch_batch_bin(cudaStream_t st, const BatchView &v, int sms) {
@@ -392,11 +417,10 @@ cudaError_t launch_batch_bin(cudaStream_t st, const BatchView &v, int sms) {
   e = launch_fixed_scan(st, v.count, v.start, v.tiles, v.ncells);
   if (e != cudaSuccess) return e;
   k_b_scatter<<<nb, tb, 0, st>>>(v);
-  int cb = (v.ncells + 255) / 256;
-  if (cb > 8 * sms) cb = 8 * sms;
+  int cb = (v.ncells + kSortWarps - 1) / kSortWarps;
+  if (cb > 16 * sms) cb = 16 * sms;
   if (cb < 1) cb = 1;
-  k_b_cellsort<<<cb, 256, 0, st>>>(v);
-  k_b_pack<<<nb, tb, 0, st>>>(v);
+  k_b_sortpack<<<cb, 32 * kSortWarps, 0, st>>>(v);
   return cudaGetLastError();
 }
 

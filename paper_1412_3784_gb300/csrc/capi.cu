@@ -524,7 +524,7 @@ int nemd_set_option(nemd_ctx *c, int key, int64_t value) {
       c->remap_centered = (int)value;
       return NEMD_OK;
     case NEMD_OPT_KERNEL:
-      if (value < 0 || value > 3) return set_err(c, NEMD_ERR_ARG, "kernel %lld", (long long)value);
+      if (value < 0 || value > 4) return set_err(c, NEMD_ERR_ARG, "kernel %lld", (long long)value);
       c->kernel = (int)value;
       return NEMD_OK;
     case NEMD_OPT_CELL_FACTOR:

@@ -354,24 +354,29 @@ cudaError_t launch_forces(nemd_ctx *c, float *F_dev, double *UW_dev) {
     cudaError_t e = cudaMemsetAsync(c->nrecheck, 0, sizeof(int), c->stream);
     if (e != cudaSuccess) return e;
   }
-  // the grouped and warp kernels have no float64 pair path: precise mode runs the
-  // plain kernel; pair records take the full-neighbourhood warp kernel
+  // the grouped and warp kernels have no precise pair path: precise mode runs the
+  // plain kernel for them (the row kernel has its own float-float path); pair
+  // records take the full-neighbourhood warp kernel
   const bool grouped = c->kernel == 1 && !c->precise && chunk_kernel_applies(c);
   const bool warped = (c->kernel == 2 || c->kernel == 3) && !c->precise && warp_kernel_applies(c);
+  const bool rowk = c->kernel == 4 && row_kernel_applies(c);
   const bool half = warped && c->kernel == 3 && c->record_cap == 0;
   if (half && F_dev && c->n > 0) {
     // half neighbourhoods add the partners' forces with atomics: start from zero
     cudaError_t e = cudaMemsetAsync(F_dev, 0, sizeof(float) * 3 * (size_t)c->n, c->stream);
     if (e != cudaSuccess) return e;
   }
-  if (grouped || warped) {
-    cudaError_t e = launch_chunk_build(c, warped ? 32 : c->group);
+  if (grouped || warped || rowk) {
+    cudaError_t e = launch_chunk_build(c, (warped || rowk) ? 32 : c->group);
     if (e != cudaSuccess) return e;
   }
   const bool timed = c->timing && c->ev && c->ev_n < c->ev_cap;
   if (timed) cudaEventRecord(c->ev[2 * c->ev_n], c->stream);
   int nblocks;
-  if (warped) {
+  if (rowk) {
+    cudaError_t e = launch_force_row(c, F_dev, &nblocks);
+    if (e != cudaSuccess) return e;
+  } else if (warped) {
     cudaError_t e = launch_force_warp(c, F_dev, &nblocks, half);
     if (e != cudaSuccess) return e;
   } else if (grouped) {
@@ -392,7 +397,8 @@ cudaError_t launch_forces(nemd_ctx *c, float *F_dev, double *UW_dev) {
   int nfix = kFixupBlocks;
   if (nblocks + nfix > c->cap_partials) nfix = (int)(c->cap_partials - nblocks);
   k_recheck_fixup<<<nfix, 256, 0, c->stream>>>(c->geo, c->recheck, c->nrecheck, c->pos4, c->q_dev, make_pot(c),
-                                               F_dev, c->partials, nblocks, half ? 1 : 0, c->precise ? 1 : 0, UW_dev,
+                                               F_dev, c->partials, nblocks, half ? 1 : 0,
+                                               (c->precise && !rowk) ? 1 : 0, UW_dev,
                                                c->counters);
   c->launches += 1;
   return cudaGetLastError();

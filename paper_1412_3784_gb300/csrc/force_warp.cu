@@ -238,6 +238,11 @@ __device__ __forceinline__ void warp_chunk(const int4 cd, const Row *__restrict_
   const float ai = (float)(ixu - ixlo);
   const float3 Xi = make_float3(fmaf(ai, sx, pi.x), fmaf(ai, sy, pi.y), fmaf(ai, sz, pi.z));
   const float3 Ri = make_float3(fmaf(ai, srx, pir.x), fmaf(ai, sry, pir.y), fmaf(ai, srz, pir.z));
+  if (nr > kRowsStaged) {
+    // more rows than the stage holds (cell factor > 2): refused as a capacity error
+    if (lane == 0) atomicOr(err, ERRB_CAPACITY);
+    nr = kRowsStaged;
+  }
   {
     const float4 *src = reinterpret_cast<const float4 *>(crow);
     __syncwarp();

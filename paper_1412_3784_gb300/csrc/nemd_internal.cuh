@@ -132,7 +132,7 @@ constexpr int kMlpParams = kMlpHidden * kMlpIn + kMlpHidden + kMlpHidden * kMlpH
 
 // Autotuner cache: per shape class, the summed mean time and the number of
 // measurements of every candidate configuration.
-constexpr int kTuneCandidates = 11;
+constexpr int kTuneCandidates = 13;
 constexpr int kMaxTuneClasses = 64;
 struct TuneEntry {
   int32_t key[2];
@@ -256,6 +256,9 @@ bool chunk_kernel_applies(const nemd_ctx *c);
 bool warp_kernel_applies(const nemd_ctx *c);
 cudaError_t launch_chunk_build(nemd_ctx *c, int gs);
 cudaError_t launch_force_warp(nemd_ctx *c, float *F_dev, int *nblocks, bool half);
+// row kernel (per-lane kappa windows, half-precision coarse test)
+bool row_kernel_applies(const nemd_ctx *c);
+cudaError_t launch_force_row(nemd_ctx *c, float *F_dev, int *nblocks);
 // autotuner cache lookup (autotune.cu)
 void tune_apply(nemd_ctx *c, double rc);
 // learned selector inference for this step (mlp.cu)

@@ -81,13 +81,15 @@ int setup_device(int dev, unsigned char **ptr, int *sms) {
   return NEMD_OK;
 }
 
-bool on_device(const void *p) {
+// p is device (or managed) memory of device dev, the device the call runs on.
+bool on_device(const void *p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -108,11 +110,10 @@ extern "C" int nemd_forces_noalloc(const double A[9], const double L0[9], double
   if (!(V > 0.0)) return NEMD_ERR_ARG;
   const double cell_bound = V / (rc * rc * rc) * (1.0 + 1e-9) + 1.0;
   if (cell_bound > (double)kMaxCells) return NEMD_ERR_CAPACITY;  // more cells than the static scratch holds
-  if (n > 0 && (!on_device(q) || !on_device(F))) return NEMD_ERR_ARG;
-  if (!on_device(UW) || (status && !on_device(status))) return NEMD_ERR_ARG;
-
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return NEMD_ERR_CUDA;
+  if (n > 0 && (!on_device(q, dev) || !on_device(F, dev))) return NEMD_ERR_ARG;
+  if (!on_device(UW, dev) || (status && !on_device(status, dev))) return NEMD_ERR_ARG;
   unsigned char *base = nullptr;
   int sms = 0;
   int r = setup_device(dev, &base, &sms);

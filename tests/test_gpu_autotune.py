@@ -32,7 +32,7 @@ def test_autotune_picks_fastest_and_keeps_results(tmp_path):
     ctx = make_ctx(w, nemd, torch)
     ctx.set_state(q, w.t)
     best, times = ctx.autotune(nemd.NEMD_AUTO_HEURISTIC, w.rc, reps=2)
-    assert len(times) == 11
+    assert len(times) == 13
     fastest = min(times, key=lambda x: x[1])[0]
     assert best == fastest          # first call: the class mean is this call's time
     F, st = evaluate(ctx, w, q, nemd.NEMD_AUTO_HEURISTIC)

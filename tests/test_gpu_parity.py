@@ -33,8 +33,10 @@ def keys(p):
     return oracle.canonical_pair_keys(p)
 
 
-KERNELS = [(0, 16), (2, 32), (3, 32), (1, 16), (1, 4)]   # (kernel, group): plain, warp, warp-half, grouped
-DETERMINISTIC = [(0, 16), (2, 32)]                   # kernels whose forces repeat bit for bit
+KERNELS = [(0, 16), (2, 32), (3, 32), (1, 16), (1, 4), (4, 32)]   # (kernel, group): plain, warp, warp-half,
+#                                                                   grouped, row
+DETERMINISTIC = [(0, 16), (2, 32), (4, 32)]          # kernels whose forces repeat bit for bit
+MAIN = [(0, 16), (2, 32), (3, 32), (4, 32)]          # plain, warp, warp-half, row
 
 
 def check_against(w, variant, ref, *, pairs=True, precise=True, kfac=1, kernel=(0, 16)):
@@ -48,7 +50,7 @@ def check_against(w, variant, ref, *, pairs=True, precise=True, kfac=1, kernel=(
     assert rel(g["U"], ref.U) <= UW_TOL_FAST
     assert mat_rel(g["W"], ref.W) <= UW_TOL_FAST
     if precise:
-        gp = run(w, variant, precise=True, kfac=kfac)
+        gp = run(w, variant, precise=True, kfac=kfac, kernel=kernel)
         assert gp["stats"]["pairs"] == ref.npairs
         assert rel(gp["U"], ref.U) <= UW_TOL_PRECISE
         assert mat_rel(gp["W"], ref.W) <= UW_TOL_PRECISE
@@ -88,7 +90,7 @@ def test_config0_wca_equilibrium(variant, kernel):
 
 # ------------------------------------------------------ flows at strains ----
 
-@pytest.mark.parametrize("kernel", KERNELS[:3])
+@pytest.mark.parametrize("kernel", MAIN)
 @pytest.mark.parametrize("i", [0, 17, 40, 63])
 @pytest.mark.parametrize("variant", [DS, DO])
 def test_planar_flow_strains(i, variant, kernel):
@@ -106,7 +108,7 @@ def test_general_flow_incl_max_skew(t, variant, kernel):
     check_against(w, variant, ref, kernel=kernel)
 
 
-@pytest.mark.parametrize("kernel", KERNELS[:3])
+@pytest.mark.parametrize("kernel", MAIN)
 @pytest.mark.parametrize("variant", [DS, DO])
 def test_planar_config_full_size(variant, kernel):
     """The planar-flow configuration at its full size (N = 32000) at two strains."""

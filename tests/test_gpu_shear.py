@@ -17,7 +17,7 @@ if not torch.cuda.is_available():
 
 from paper_1412_3784_gb300 import nemd  # noqa: E402
 
-KERNELS = [(0, 16), (2, 32), (3, 32)]
+KERNELS = [(0, 16), (2, 32), (3, 32), (4, 32)]
 STRAINS = [0.0, 0.23, 0.4999999, 0.5, 0.77]
 
 
