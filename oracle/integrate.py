@@ -56,9 +56,10 @@ def forces(w, q, t, method="ds"):
     return evaluate(replace(w, q=np.ascontiguousarray(q), t=float(t)), method).F
 
 
-def integrate(w, p0, dt, nsteps, thermostat=True, method="ds"):
-    """The steps above from w.q, p0 at time w.t.  Returns (q, p, t): q wrapped
-    into the unit cell at t = w.t + nsteps dt, p the peculiar momenta."""
+def trajectory(w, p0, dt, nsteps, thermostat=True, method="ds"):
+    """The steps above from w.q, p0 at time w.t, yielding after each step
+    (k, q, p, t): q wrapped into the unit cell at t = w.t + k dt, p the peculiar
+    momenta before the final rescale."""
     centered = bool(getattr(w, "remap", 0))
     E = expm(w.A, dt)
     Eh = expm(w.A, -0.5 * dt)
@@ -82,6 +83,17 @@ def integrate(w, p0, dt, nsteps, thermostat=True, method="ds"):
         F = forces(w, q, t, method)
         p = h * F + p @ Eh.T
         scale = math.sqrt(k0 / float(np.sum(p * p))) if thermostat else 1.0
+        yield k + 1, q, p, t, scale
+
+
+def integrate(w, p0, dt, nsteps, thermostat=True, method="ds"):
+    """The steps above from w.q, p0 at time w.t.  Returns (q, p, t): q wrapped
+    into the unit cell at t = w.t + nsteps dt, p the peculiar momenta."""
+    lat = lattice(w.A, w.L0, w.T, w.t, bool(getattr(w, "remap", 0)))
+    _, q = wrap(lat["L"], lat["Linv"], np.asarray(w.q, dtype=np.float64))
+    p, t, scale = np.array(p0, dtype=np.float64, copy=True), w.t, 1.0
+    for _, q, p, t, scale in trajectory(w, p0, dt, nsteps, thermostat, method):
+        pass
     return q, scale * p, t
 
 
