@@ -222,7 +222,9 @@ def run_reference(args, rank, world):
         "config": {"workload": f"{args.workload}: general 3D flow, N={ser.n}, LJ rc=2.5, "
                                f"one strain per step (dynamic size cell list)"},
         "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": 1, "kind": "oracle",
-                         "sample": f"one force evaluation per step of the N={ser.n} system"},
+                         "sample": f"one force evaluation per step (a strain of the period) of the N={ser.n} "
+                                   f"system, dynamic size cell list, FP64, one core",
+                         "host": dict(zip(("nproc", "model"), host_cpu()))},
         "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -450,6 +452,29 @@ def section_main(args, rank, world, dev, torch, nemd, W):
                 "force_kernel_pairs_per_s": (pairs_per_step / S) / avg_launch_s,
                 "pair_only_frac": (C_PAIR * pairs_per_step / S) / avg_launch_s / peak}
 
+    # precise mode (energy and virial of every accepted pair in float-float, summed
+    # per particle in float-float and across particles in float64) on the row
+    # kernel, the same strains and the same per-strain cell list choice
+    ctx.set_option(nemd.NEMD_OPT_AUTOTUNED, 0)
+    ctx.set_option(nemd.NEMD_OPT_KERNEL, 4)
+    ctx.set_option(nemd.NEMD_OPT_CELL_FACTOR, 1)
+    ctx.set_option(nemd.NEMD_OPT_PRECISE, 1)
+    ms_pre = timed_loop(torch, dev, world, lambda: one_step(nemd.NEMD_AUTO_HEURISTIC), args.steps, 1)
+    ctx.set_option(nemd.NEMD_OPT_TIMING, 1)
+    one_step(nemd.NEMD_AUTO_HEURISTIC)
+    ctx.sync()
+    kp_ms, kp_n = ctx.kernel_time()
+    ctx.set_option(nemd.NEMD_OPT_TIMING, 0)
+    ctx.set_option(nemd.NEMD_OPT_PRECISE, 0)
+    pre_launch_s = (kp_ms / kp_n) * 1e-3
+    precise = {"pairs_per_s": total_pairs / (max_over_ranks(ms_pre, world, dev) * 1e-3),
+               "ms_per_step": ms_pre / args.steps, "kernel": "k_force_row (precise)",
+               "force_kernel_ms": pre_launch_s * 1e3,
+               "roofline_frac": (ops_per_launch / pre_launch_s) / peak,
+               "over_fast": ms_tuned / ms_pre,
+               "accuracy": "U and W within 1e-9 (relative) of the FP64 oracle in the tests "
+                           "(N = 2^20 and 2^21 included); F as in fast mode"}
+
     # end to end through the C ABI with pinned host buffers
     # Se strains spread evenly over the period, so that the e2e workload has
     # the same mix of lattice shapes as the device-resident step
@@ -544,7 +569,8 @@ def section_main(args, rank, world, dev, torch, nemd, W):
                   "tuned_over_best_plain": value / max(plain_ds, plain_do),
                   "search_efficiency_ds": eta_ds, "search_efficiency_do": eta_do},
         "autotune": tune,
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+        "roofline": roofline, "precise": precise, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+        "clocks": clk,
     }
 
 
@@ -603,23 +629,52 @@ def section_batched(args, world, dev, torch, nemd, W):
             "speedup_over_loop": ms_loop / ms}
 
 
+def _option_rows(ctx, torch, dev, nemd, W, ser, m, reps=3):
+    """Option timings (features, ms per option) and the volume rule's option at m strains of a series."""
+    ctx.set_flow(ser.A, ser.L0, ser.M, ser.period)
+    ctx.set_potential(nemd.NEMD_WCA if ser.kind == W.POT_WCA else nemd.NEMD_LJ, 1.0, 1.0, 1)
+    X, T, rule = [], [], []
+    for i in range(m):
+        t = (i + 0.5) / m * ser.period
+        ctx.set_state(torch.from_numpy(ser.positions(t)).to(dev), t)
+        f, ms = ctx.time_options(ser.rc, reps=reps)
+        ctx.set_option(nemd.NEMD_OPT_CELL_FACTOR, 1)
+        ctx.build_cells(nemd.NEMD_AUTO_HEURISTIC, ser.rc)
+        ctx.compute_forces()
+        ctx.sync()
+        X.append(f)
+        T.append(ms)
+        rule.append(ctx.stats()["variant"])          # option index of the volume rule at k = 1
+    return X, T, rule
+
+
+def _regrets(ctx, X, T, rule):
+    T = np.array(T)
+    pick = np.argmin(ctx.model_predict(np.array(X)), axis=1)
+    best = T.min(axis=1)
+    idx = np.arange(len(T))
+    return (float((T[idx, pick] - best).sum() / best.sum()),
+            float((T[idx, np.array(rule)] - best).sum() / best.sum()), pick, T)
+
+
 def section_learned(args, dev, torch, nemd, W):
-    """Learned selector: trained on timing rows of the N = 32000 planar, N = 256000
-    and N = 2^20 general and batched systems; judged on the N = 2^21 general-flow
-    system (none of its strains or sites among the training rows)."""
+    """Learned selector over the row kernel's options (cell list variant x cell
+    factor): trained on timing rows of LJ systems (N = 32000 planar, N = 256000
+    and N = 2^20 general flow), WCA systems (N = 32000 general, N = 16384 planar)
+    and the batched systems; judged on held-out systems none of whose strains or
+    sites it saw: the N = 2^21 LJ general flow and a WCA mix (N = 55296 general,
+    N = 6912 planar)."""
     ctx = nemd.Context(dev.index)
-    ctx.set_option(nemd.NEMD_OPT_KERNEL, 2)
+    ctx.set_option(nemd.NEMD_OPT_KERNEL, 4)
     X, T = [], []
     t0 = time.perf_counter()
-    for ser, m in ((W.planar_series(k=20), 64), (W.general_series(k=40), 64), (W.general_series(k=64), 32)):
-        ctx.set_flow(ser.A, ser.L0, ser.M, ser.period)
-        ctx.set_potential(nemd.NEMD_LJ, 1.0, 1.0, 1)
-        for i in range(m):
-            t = (i + 0.5) / m * ser.period
-            ctx.set_state(torch.from_numpy(ser.positions(t)).to(dev), t)
-            f, ms = ctx.time_options(ser.rc, reps=3)
-            X.append(f)
-            T.append(ms)
+    train = ((W.planar_series(k=20), 64), (W.general_series(k=40), 64), (W.general_series(k=64), 32),
+             (W.StrainSeries(W.M_GENERAL, 20, 21, kind=W.POT_WCA), 32),
+             (W.StrainSeries(W.M_PLANAR, 16, 23, kind=W.POT_WCA), 32))
+    for ser, m in train:
+        x, tt, _ = _option_rows(ctx, torch, dev, nemd, W, ser, m)
+        X += x
+        T += tt
     for w in W.batched_systems():
         ctx.set_flow(w.A, w.L0, w.M, w.T)
         ctx.set_potential(nemd.NEMD_WCA if w.kind == W.POT_WCA else nemd.NEMD_LJ, 1.0, 1.0, 1)
@@ -636,6 +691,16 @@ def section_learned(args, dev, torch, nemd, W):
     t0 = time.perf_counter()
     hist = ctx.model_train(X, T, steps=3000, batch=128, lr=3e-3, seed=0)
     t_train = time.perf_counter() - t0
+
+    # held-out WCA mix
+    wx, wt, wr = [], [], []
+    for ser, m in ((W.StrainSeries(W.M_GENERAL, 24, 31, kind=W.POT_WCA), 32),
+                   (W.StrainSeries(W.M_PLANAR, 12, 32, kind=W.POT_WCA), 32)):
+        x, tt, rr = _option_rows(ctx, torch, dev, nemd, W, ser, m)
+        wx += x
+        wt += tt
+        wr += rr
+    reg_wl, reg_wr, pick_w, Tw = _regrets(ctx, wx, wt, wr)
 
     ser = W.general_series_2m()
     S4 = args.learned_strains
@@ -655,13 +720,8 @@ def section_learned(args, dev, torch, nemd, W):
         ctx.build_cells(nemd.NEMD_AUTO_HEURISTIC, ser.rc)
         ctx.compute_forces()
         ctx.sync()
-        rule.append(ctx.stats()["variant"])         # option index of the volume rule at k = 1
-    table = np.array(table)
-    pick = np.argmin(ctx.model_predict(np.array(feats)), axis=1)
-    best = table.min(axis=1)
-    idx = np.arange(S4)
-    regret_learned = float((table[idx, pick] - best).sum() / best.sum())
-    regret_rule = float((table[idx, np.array(rule)] - best).sum() / best.sum())
+        rule.append(ctx.stats()["variant"])
+    regret_learned, regret_rule, pick, table = _regrets(ctx, feats, table, rule)
 
     F = torch.empty((ser.n, 3), dtype=torch.float32, device=dev)
     pairs = 0
@@ -683,22 +743,28 @@ def section_learned(args, dev, torch, nemd, W):
                 ctx.compute_forces(F)
         return fn
     out = {}
-    for name, variant, kernel in (("learned", nemd.NEMD_AUTO_LEARNED, 2), ("rule", nemd.NEMD_AUTO_HEURISTIC, 2),
+    for name, variant, kernel in (("learned", nemd.NEMD_AUTO_LEARNED, 4), ("rule", nemd.NEMD_AUTO_HEURISTIC, 4),
                                   ("plain_ds", nemd.NEMD_DS, 0), ("plain_do", nemd.NEMD_DO, 0)):
         ms = timed_loop(torch, dev, 1, step(variant, kernel), 2, 1) / 2
         out[name] = pairs / ms * 1e3
     ctx.close()
     del q_all
     return {"workload": f"general 3D flow, N={ser.n} (FCC 81^3 with vacancies), LJ rc 2.5, {S4} strains "
-                        f"of one period",
+                        f"of one period; and a WCA mix (N=55296 general flow, N=6912 planar flow, 32 strains "
+                        f"each); all held out from training",
             "training_rows": int(len(X)), "rows_s": t_rows, "train_s": t_train,
             "train_loss_first_last": [float(hist[:50].mean()), float(hist[-50:].mean())],
-            "options": "o = (variant o & 1, cell factor 1 + (o >> 1)), warp kernel",
+            "options": "o = (variant o & 1, cell factor 1 + (o >> 1)), row kernel",
             "regret_vs_exhaustive": {"learned": regret_learned, "volume_rule_k1": regret_rule},
             "learned_choices": np.bincount(pick, minlength=4).tolist(),
             "exhaustive_choices": np.bincount(table.argmin(axis=1), minlength=4).tolist(),
+            "wca_mix": {"regret_vs_exhaustive": {"learned": reg_wl, "volume_rule_k1": reg_wr},
+                        "learned_choices": np.bincount(pick_w, minlength=4).tolist(),
+                        "exhaustive_choices": np.bincount(Tw.argmin(axis=1), minlength=4).tolist(),
+                        "rule_choices": np.bincount(np.array(wr), minlength=4).tolist()},
             "pairs_per_s": out,
-            "learned_over_best_plain": out["learned"] / max(out["plain_ds"], out["plain_do"])}
+            "learned_over_best_plain": out["learned"] / max(out["plain_ds"], out["plain_do"]),
+            "learned_over_rule": out["learned"] / out["rule"]}
 
 
 def section_shear(args, world, dev, torch, nemd, W):
@@ -927,7 +993,8 @@ def main():
             "vs_baseline": None, "dtype": "f32 pair math, f64 lattice/guard band/reductions, float-float wrap",
             "data": "synthetic",
         }
-        for key in ("config", "plain", "autotune", "roofline", "cpu_baseline", "e2e", "gpu_launches", "clocks"):
+        for key in ("config", "plain", "autotune", "roofline", "precise", "cpu_baseline", "e2e", "gpu_launches",
+                    "clocks"):
             line[key] = main_part[key]
         line["batched"] = batched
         line["learned"] = learned

@@ -204,6 +204,29 @@ int nemd_compute_forces(nemd_ctx *ctx, float *F, double *U, double *W);
 int nemd_integrate(nemd_ctx *ctx, double *q, double *p, int64_t n, double t0, double dt, int64_t nsteps,
                    int variant, double rc, int thermostat);
 
+/* Verlet neighbour list with a skin for nemd_integrate.  The paper rebuilds
+ * its cell list at every step (Sec. 4.1); it has no Verlet list, which is the
+ * standard next stage.  With skin > 0 the integrator keeps the pairs within
+ * rc + skin found by one cell-list search (nemd_build_cells(variant, rc + skin)
+ * and the library's list kernel), evaluates only those at the following steps
+ * (same pair decision, forces, energy and virial as the cell-list path), and
+ * rebuilds the list when a pair outside it could have come within rc:
+ *     exp(-|A|_F (t - t_b)) (rc + skin) - 2 delta < rc,
+ * t_b the time of the build and delta the largest peculiar displacement
+ * |L(t) u_i| since it (measured in the deformed frame), and at every remap.
+ * Positions are wrapped at every step; the images of the listed pairs follow
+ * the wraps.  The rebuild decision is taken on the host (one synchronisation
+ * per step), so these steps are launched rather than replayed as a graph.
+ * skin = 0 (default) turns the list off; skin < 0 or not finite is
+ * NEMD_ERR_ARG.  Setting it discards the current list. */
+int nemd_set_verlet(nemd_ctx *ctx, double skin);
+
+/* Since the last nemd_set_verlet: list builds, force evaluations from the list
+ * (builds included), the entries per particle of the current list, and the
+ * largest peculiar displacement since the build measured at the last check
+ * that kept the list.  Any pointer may be NULL. */
+int nemd_get_verlet_stats(nemd_ctx *ctx, int64_t *builds, int64_t *steps, int64_t *width, double *delta);
+
 /* Wait for the stream and return any deferred device error. */
 int nemd_sync(nemd_ctx *ctx);
 
@@ -379,6 +402,9 @@ typedef struct nemd_batch_stats {
 #define NEMD_BATCH_OPT_TILE 2         /* particles per chunk, 16 or 32 (default 32)     */
 #define NEMD_BATCH_OPT_GRAPH 3        /* 1: capture and replay a CUDA graph (default);
                                          0: launch the kernels one by one             */
+#define NEMD_BATCH_OPT_KERNEL 4       /* force kernel of the persistent launch: 4 the row
+                                         kernel (default), 2 the warp kernel; same pair
+                                         set and forces up to rounding                */
 
 /* Create / destroy a batch on `device` working on `stream` (a cudaStream_t,
  * NULL = the legacy default stream).  Destroy synchronises and frees

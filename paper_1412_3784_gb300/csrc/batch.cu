@@ -32,7 +32,8 @@ struct nemd_batch {
   std::vector<GridIn> grid_host;  // per system: rc, requested variant, cell factor, capacities
   bool finalized;
   int kfac, gs, use_graph;
-  int force_blocks;
+  int force_kernel;  // 2 warp kernel, 4 row kernel
+  int force_blocks, row_blocks;
   int max_clcap;
   std::vector<int64_t> offsets;
   // device tables
@@ -53,7 +54,7 @@ struct nemd_batch {
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   const void *key[3];
-  int key_cfg[2];
+  int key_cfg[3];
   int64_t launches;  // kernel launches of one step
   char msg[512];
 };
@@ -131,13 +132,15 @@ cudaError_t enqueue_step(nemd_batch *b, cudaStream_t st) {
   if ((e = nemd::launch_batch_stencil(st, v, b->max_clcap)) != cudaSuccess) return e;
   if ((e = nemd::launch_batch_bin(st, v, b->sms)) != cudaSuccess) return e;
   if ((e = nemd::launch_batch_chunks(st, v, b->sms)) != cudaSuccess) return e;
-  if ((e = nemd::launch_batch_force(st, v, b->force_blocks)) != cudaSuccess) return e;
+  if ((e = (b->force_kernel == 4 ? nemd::launch_batch_force_row(st, v, b->row_blocks)
+                                  : nemd::launch_batch_force(st, v, b->force_blocks))) != cudaSuccess)
+    return e;
   return nemd::launch_batch_finish(st, v);
 }
 
-// lattice, grid, stencil, bin (wrap, 3 scan, scatter, sort and pack), chunks
+// lattice, grid, stencil, bin (wrap, 3 scan, scatter, sort, pack), chunks
 // (count, 3 scan, write), force, fix-up, reduce
-constexpr int64_t kStepLaunches = 3 + 6 + 5 + 1 + 2;
+constexpr int64_t kStepLaunches = 3 + 7 + 5 + 1 + 2;
 
 }  // namespace
 
@@ -156,6 +159,7 @@ int nemd_batch_create(nemd_batch **out, int device, void *stream) {
   cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, device);
   b->kfac = 1;
   b->gs = 32;
+  b->force_kernel = 4;
   b->use_graph = 1;
   if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
       nemd_create(&b->check, device, stream) != NEMD_OK) {
@@ -395,6 +399,7 @@ int nemd_batch_finalize(nemd_batch *b) {
                       b->stream));
   CKB(cudaStreamSynchronize(b->stream));
   b->force_blocks = nemd::batch_force_blocks(b->sms);
+  b->row_blocks = nemd::batch_row_blocks(b->sms);
   b->launches = kStepLaunches;
   b->finalized = true;
   return NEMD_OK;
@@ -464,7 +469,8 @@ int nemd_batch_compute(nemd_batch *b, float *F, double *UW) {
   v.gs = b->gs;
   if (b->use_graph) {
     const bool same = b->exec && b->key[0] == (const void *)v.q && b->key[1] == (const void *)Fd &&
-                      b->key[2] == (const void *)UWd && b->key_cfg[0] == b->kfac && b->key_cfg[1] == b->gs;
+                      b->key[2] == (const void *)UWd && b->key_cfg[0] == b->kfac && b->key_cfg[1] == b->gs &&
+                      b->key_cfg[2] == b->force_kernel;
     if (!same) {
       drop_graph(b);
       CKB(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeRelaxed));
@@ -483,6 +489,7 @@ int nemd_batch_compute(nemd_batch *b, float *F, double *UW) {
       b->key[2] = UWd;
       b->key_cfg[0] = b->kfac;
       b->key_cfg[1] = b->gs;
+      b->key_cfg[2] = b->force_kernel;
     }
     CKB(cudaGraphLaunch(b->exec, b->stream));
   } else {
@@ -541,6 +548,10 @@ int nemd_batch_set_option(nemd_batch *b, int key, int64_t value) {
       return NEMD_OK;
     case NEMD_BATCH_OPT_GRAPH:
       b->use_graph = value ? 1 : 0;
+      return NEMD_OK;
+    case NEMD_BATCH_OPT_KERNEL:
+      if (value != 2 && value != 4) return set_err(b, NEMD_ERR_ARG, "batch force kernel %lld (2 or 4)", (long long)value);
+      b->force_kernel = (int)value;
       return NEMD_OK;
     default:
       return set_err(b, NEMD_ERR_ARG, "batch option %d", key);

@@ -83,6 +83,9 @@ cudaError_t launch_batch_chunks(cudaStream_t st, const BatchView &v, int sms);
 // (blocks from batch_force_blocks, which must be called outside stream capture)
 int batch_force_blocks(int sms);
 cudaError_t launch_batch_force(cudaStream_t st, const BatchView &v, int blocks);
+// the same with the row kernel (force_row.cu)
+int batch_row_blocks(int sms);
+cudaError_t launch_batch_force_row(cudaStream_t st, const BatchView &v, int blocks);
 // force.cu: float64 fix-up of deferred candidates, per-system reductions
 cudaError_t launch_batch_finish(cudaStream_t st, const BatchView &v);
 

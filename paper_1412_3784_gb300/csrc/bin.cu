@@ -9,13 +9,12 @@
 //               cell centre in the variant's frame as a float32 multiple of the
 //               step's quantum plus a float32 residual, rank = atomicAdd(count[cell])
 //   k_scan_*    exclusive scan of the per-cell counts -> start[]
-//   k_scatter   perm[start[cell] + rank] = i
-//   k_sortpack  one warp per cell: the cell's particles in increasing kappa
-//               (the coordinate along the x-row of cells), ties by input index,
-//               written as sorted float4 {rel position, input index},
-//               {residual, kappa} and cell ids.  The order depends only on the
-//               positions, so sums are reproducible from run to run, and every
-//               x-row of cells is one kappa-sorted run of particles.
+//   k_scatter   perm[start[cell] + rank] = i, and its kappa in the same slot of cell_sorted
+//   k_cellsort  per cell, particles in increasing kappa (the coordinate along
+//               the x-row of cells), ties by input index: the order depends
+//               only on the positions, so sums are reproducible from run to
+//               run, and every x-row of cells is one kappa-sorted run
+//   k_pack      sorted float4 {rel position, input index}, {residual, kappa}, cell ids
 #include <math.h>
 
 #include "batch_internal.cuh"
@@ -214,13 +213,24 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_add(const Geo *g, int *__
   if (blockIdx.x == 0 && threadIdx.x == 0) start[ncells] = n;
 }
 
-__global__ void k_scatter(const Geo *g, const float4 *__restrict__ relc, const int *__restrict__ rank,
-                          const int *__restrict__ start, int *__restrict__ perm, int n) {
+// perm[start[cell] + rank] = i, and the particle's sort key kappa in the same
+// slot of cell_sorted (overwritten with the cell ids by the sort-and-pack).
+__device__ __forceinline__ void scatter_body(const float4 *__restrict__ relc, const float4 *__restrict__ relr,
+                                             const int *__restrict__ rank, const int *__restrict__ start,
+                                             int *__restrict__ perm, int *__restrict__ key_slot, int i) {
+  const int cell = __float_as_int(relc[i].w);
+  const int slot = start[cell] + rank[i];
+  perm[slot] = i;
+  key_slot[slot] = __float_as_int(relr[i].w);
+}
+
+__global__ void k_scatter(const Geo *g, const float4 *__restrict__ relc, const float4 *__restrict__ relr,
+                          const int *__restrict__ rank, const int *__restrict__ start, int *__restrict__ perm,
+                          int *__restrict__ key_slot, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
-  const int cell = __float_as_int(relc[i].w);
-  perm[start[cell] + rank[i]] = i;
+  scatter_body(relc, relr, rank, start, perm, key_slot, i);
 }
 
 // (kappa, input index) of particle i: the within-cell order.
@@ -228,59 +238,96 @@ __device__ __forceinline__ bool sort_before(float ka, int ia, float kb, int ib) 
   return ka < kb || (ka == kb && ia < ib);
 }
 
-// One warp sorts cell c (its slice of perm, in arrival order) by (kappa, input
-// index) and writes the sorted slots.  The rank of each particle is the number
-// of particles of the cell that sort before it (one comparison per pair, the
-// cell's keys staged in shared memory); cells longer than kSortStage compare
-// against global memory instead.
-constexpr int kSortWarps = 8;
-constexpr int kSortStage = 128;
+// One thread per cell: the cell's slots sorted by (kappa, input index) --
+// keys in the slots of cell_sorted, indices in perm, both contiguous per cell.
+// A cell of up to 32 particles is sorted in registers by a bitonic network
+// (padded with keys that sort last); a longer one in place by insertion.
+constexpr int kNet = 32;
 
-__device__ __forceinline__ void sortpack_cell(const int *__restrict__ start, const int *__restrict__ perm,
-                                              const float4 *__restrict__ relc, const float4 *__restrict__ relr,
-                                              float4 *__restrict__ pos4, float4 *__restrict__ posr,
-                                              int *__restrict__ cell_sorted, int c, float *skey, int *sidx,
-                                              int lane) {
-  const int b = start[c], n = start[c + 1] - b;
-  if (n <= 0) return;
-  const bool staged = n <= kSortStage;
-  __syncwarp();
-  if (staged)
-    for (int t = lane; t < n; t += 32) {
-      const int i = perm[b + t];
-      sidx[t] = i;
-      skey[t] = relr[i].w;
+__device__ __forceinline__ void cellsort_body(const int *__restrict__ start, int *__restrict__ perm,
+                                              int *__restrict__ key_slot, int c) {
+  const int b = start[c], e = start[c + 1], n = e - b;
+  if (n <= 1) return;
+  if (n <= kNet) {
+    float key[kNet];
+    int idx[kNet];
+#pragma unroll
+    for (int t = 0; t < kNet; t++) {
+      key[t] = t < n ? __int_as_float(key_slot[b + t]) : INFINITY;
+      idx[t] = t < n ? perm[b + t] : 0x7fffffff;
     }
-  __syncwarp();
-  for (int t = lane; t < n; t += 32) {
-    const int i = staged ? sidx[t] : perm[b + t];
-    const float k = staged ? skey[t] : relr[i].w;
-    int rank = 0;
-    for (int m = 0; m < n; m++) {
-      const int im = staged ? sidx[m] : perm[b + m];
-      const float km = staged ? skey[m] : relr[im].w;
-      rank += sort_before(km, im, k, i) ? 1 : 0;
+#pragma unroll
+    for (int k = 2; k <= kNet; k <<= 1) {
+#pragma unroll
+      for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+        for (int i = 0; i < kNet; i++) {
+          const int l = i ^ j;
+          if (l > i) {
+            const bool up = (i & k) == 0;
+            const bool swap = up ? sort_before(key[l], idx[l], key[i], idx[i]) : sort_before(key[i], idx[i], key[l], idx[l]);
+            const float ka = key[i], kb = key[l];
+            const int ia = idx[i], ib = idx[l];
+            key[i] = swap ? kb : ka;
+            key[l] = swap ? ka : kb;
+            idx[i] = swap ? ib : ia;
+            idx[l] = swap ? ia : ib;
+          }
+        }
+      }
     }
-    const float4 r = relc[i];
-    pos4[b + rank] = make_float4(r.x, r.y, r.z, __int_as_float(i));
-    posr[b + rank] = relr[i];
-    cell_sorted[b + rank] = __float_as_int(r.w);
+#pragma unroll
+    for (int t = 0; t < kNet; t++)
+      if (t < n) {
+        key_slot[b + t] = __float_as_int(key[t]);
+        perm[b + t] = idx[t];
+      }
+    return;
+  }
+  for (int k = b + 1; k < e; k++) {
+    const int kbits = key_slot[k];
+    const float kv = __int_as_float(kbits);
+    const int iv = perm[k];
+    int u = k - 1;
+    while (u >= b) {
+      const int ubits = key_slot[u];
+      const int iu = perm[u];
+      if (!sort_before(kv, iv, __int_as_float(ubits), iu)) break;
+      key_slot[u + 1] = ubits;
+      perm[u + 1] = iu;
+      u--;
+    }
+    key_slot[u + 1] = kbits;
+    perm[u + 1] = iv;
   }
 }
 
-__global__ void __launch_bounds__(32 * kSortWarps) k_sortpack(const Geo *g, const int *__restrict__ start,
-                                                                const int *__restrict__ perm,
-                                                                const float4 *__restrict__ relc,
-                                                                const float4 *__restrict__ relr,
-                                                                float4 *__restrict__ pos4, float4 *__restrict__ posr,
-                                                                int *__restrict__ cell_sorted) {
-  __shared__ float skey[kSortWarps][kSortStage];
-  __shared__ int sidx[kSortWarps][kSortStage];
+__global__ void k_cellsort(const Geo *g, const int *__restrict__ start, int *__restrict__ perm,
+                           int *__restrict__ key_slot) {
   if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ncells = g->ncells;
-  for (int c = blockIdx.x * kSortWarps + warp; c < ncells; c += gridDim.x * kSortWarps)
-    sortpack_cell(start, perm, relc, relr, pos4, posr, cell_sorted, c, skey[warp], sidx[warp], lane);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x)
+    cellsort_body(start, perm, key_slot, c);
+}
+
+// Sorted slot k: float4 {rel position, input index}, {residual, kappa}, cell id.
+__device__ __forceinline__ void pack_body(const float4 *__restrict__ relc, const float4 *__restrict__ relr,
+                                          const int *__restrict__ perm, float4 *__restrict__ pos4,
+                                          float4 *__restrict__ posr, int *__restrict__ cell_sorted, int k) {
+  const int i = perm[k];
+  const float4 r = relc[i];
+  pos4[k] = make_float4(r.x, r.y, r.z, __int_as_float(i));
+  posr[k] = relr[i];
+  cell_sorted[k] = __float_as_int(r.w);
+}
+
+__global__ void k_pack(const Geo *g, const float4 *__restrict__ relc, const float4 *__restrict__ relr,
+                       const int *__restrict__ perm, float4 *__restrict__ pos4, float4 *__restrict__ posr,
+                       int *__restrict__ cell_sorted, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
+  pack_body(relc, relr, perm, pos4, posr, cell_sorted, k);
 }
 
 cudaError_t launch_bin(nemd_ctx *c) {
@@ -301,11 +348,12 @@ cudaError_t launch_bin(nemd_ctx *c) {
   if (n > 0) {
     const int tb = 256;
     const int nb = (n + tb - 1) / tb;
-    k_scatter<<<nb, tb, 0, c->stream>>>(c->geo, c->relc, c->rank, c->start, c->perm, n);
-    int64_t cb = (c->cap_cells + kSortWarps - 1) / kSortWarps;
-    if (cb > 16 * (int64_t)c->sms) cb = 16 * (int64_t)c->sms;
-    k_sortpack<<<(int)cb, 32 * kSortWarps, 0, c->stream>>>(c->geo, c->start, c->perm, c->relc, c->relr, c->pos4,
-                                                            c->posr, c->cell_sorted);
+    k_scatter<<<nb, tb, 0, c->stream>>>(c->geo, c->relc, c->relr, c->rank, c->start, c->perm, c->cell_sorted, n);
+    int64_t cb = (c->cap_cells + 255) / 256;
+    if (cb > 8 * (int64_t)c->sms) cb = 8 * (int64_t)c->sms;
+    k_cellsort<<<(int)cb, 256, 0, c->stream>>>(c->geo, c->start, c->perm, c->cell_sorted);
+    k_pack<<<nb, tb, 0, c->stream>>>(c->geo, c->relc, c->relr, c->perm, c->pos4, c->posr, c->cell_sorted, n);
+    c->launches += 1;
     c->launches += 2;
   }
   return cudaGetLastError();
@@ -395,17 +443,20 @@ __global__ void k_b_scatter(BatchView v) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= v.ntot) return;
   if (v.geo[v.sys_of[i]].error & (ERRB_BOX | ERRB_CAPACITY)) return;
-  const int cell = __float_as_int(v.relc[i].w);
-  v.perm[v.start[cell] + v.rank[i]] = i;
+  scatter_body(v.relc, v.relr, v.rank, v.start, v.perm, v.cell_sorted, i);
 }
 
 // Every system's cells (the cell slots of all systems are one array).
-__global__ void __launch_bounds__(32 * kSortWarps) k_b_sortpack(BatchView v) {
-  __shared__ float skey[kSortWarps][kSortStage];
-  __shared__ int sidx[kSortWarps][kSortStage];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int c = blockIdx.x * kSortWarps + warp; c < v.ncells; c += gridDim.x * kSortWarps)
-    sortpack_cell(v.start, v.perm, v.relc, v.relr, v.pos4, v.posr, v.cell_sorted, c, skey[warp], sidx[warp], lane);
+__global__ void k_b_cellsort(BatchView v) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < v.ncells; c += gridDim.x * blockDim.x)
+    cellsort_body(v.start, v.perm, v.cell_sorted, c);
+}
+
+// Sorted slots [0, start[ncells]): the particles of every system that binned.
+__global__ void k_b_pack(BatchView v) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= v.start[v.ncells]) return;
+  pack_body(v.relc, v.relr, v.perm, v.pos4, v.posr, v.cell_sorted, k);
 }
 
 cudaError_t launch_batch_bin(cudaStream_t st, const BatchView &v, int sms) {
@@ -417,10 +468,11 @@ cudaError_t launch_batch_bin(cudaStream_t st, const BatchView &v, int sms) {
   e = launch_fixed_scan(st, v.count, v.start, v.tiles, v.ncells);
   if (e != cudaSuccess) return e;
   k_b_scatter<<<nb, tb, 0, st>>>(v);
-  int cb = (v.ncells + kSortWarps - 1) / kSortWarps;
-  if (cb > 16 * sms) cb = 16 * sms;
+  int cb = (v.ncells + 255) / 256;
+  if (cb > 8 * sms) cb = 8 * sms;
   if (cb < 1) cb = 1;
-  k_b_sortpack<<<cb, 32 * kSortWarps, 0, st>>>(v);
+  k_b_cellsort<<<cb, 256, 0, st>>>(v);
+  k_b_pack<<<nb, tb, 0, st>>>(v);
   return cudaGetLastError();
 }
 

@@ -392,14 +392,18 @@ cudaError_t launch_forces(nemd_ctx *c, float *F_dev, double *UW_dev) {
     cudaEventRecord(c->ev[2 * c->ev_n + 1], c->stream);
     c->ev_n++;
   }
-  // the deferred float64 decisions, as a few more blocks of partials (at least
-  // one slot is always left after the force kernel's)
+  return launch_recheck_fixup(c, F_dev, UW_dev, nblocks, half, c->precise && !rowk);
+}
+
+// The deferred float64 decisions, as a few more blocks of partials after the
+// force kernel's nblocks (at least one slot is always left), and the totals.
+cudaError_t launch_recheck_fixup(nemd_ctx *c, float *F_dev, double *UW_dev, int nblocks, bool half,
+                                 bool frame_is_cartesian) {
   int nfix = kFixupBlocks;
   if (nblocks + nfix > c->cap_partials) nfix = (int)(c->cap_partials - nblocks);
   k_recheck_fixup<<<nfix, 256, 0, c->stream>>>(c->geo, c->recheck, c->nrecheck, c->pos4, c->q_dev, make_pot(c),
                                                F_dev, c->partials, nblocks, half ? 1 : 0,
-                                               (c->precise && !rowk) ? 1 : 0, UW_dev,
-                                               c->counters);
+                                               frame_is_cartesian ? 1 : 0, UW_dev, c->counters);
   c->launches += 1;
   return cudaGetLastError();
 }

@@ -561,4 +561,71 @@ cudaError_t launch_force_row(nemd_ctx *c, float *F, int *nblocks) {
   return cudaGetLastError();
 }
 
+// ---- batches: one persistent launch over every chunk of every system ----
+// Warps take chunks from a shared counter (chunks of different systems differ
+// widely in cost).  Each lane writes its particle's force and its particle's
+// own pair sums (float32, per sorted particle); the per-system reduction adds
+// those in float64 in a fixed order, so no result depends on which warp took
+// which chunk.
+__global__ void __launch_bounds__(kRowThreads, kRowMinBlocks) k_b_force_row(BatchView v) {
+  constexpr int kWarps = kRowThreads / 32;
+  constexpr unsigned FULL = 0xffffffffu;
+  __shared__ RowStage stage[kWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nch = v.chunk_off[v.nclasses];
+  for (;;) {
+    int ch = 0;
+    if (lane == 0) ch = atomicAdd(v.work, 1);
+    ch = __shfl_sync(FULL, ch, 0);
+    if (ch >= nch) break;
+    const int4 cd = v.chunks[ch];
+    const int s = v.class_sys[cd.z];
+    Geo *g = v.geo + s;
+    const int coff = v.sys[s].coff;
+    const Pot pp = v.pot[s];
+    const PotFF pf = make_pot_ff(pp);
+    Acc acc;
+    acc.zero();
+    AccFF accp;
+    accp.zero();
+    int ncand = 0, nre = 0;
+    bool act;
+    float4 pi;
+    int ki;
+    row_chunk<false, false>(cd, v.rows + (size_t)cd.z * kBatchRowStride, v.rowcnt[cd.z], coff, g, v.pos4, v.posr,
+                            v.cell_sorted, v.start, stage[warp], pp, pf, v.q, acc, accp, ncand, nre, act, pi, ki,
+                            nullptr, nullptr, 0, v.recheck, v.nrecheck, &g->error);
+    if (act) {
+      if (v.F) row_store_force(v.F, g, pi, acc);
+      v.ppart[2 * (size_t)ki] = make_float4(acc.u, acc.wxx, acc.wyy, acc.wzz);
+      v.ppart[2 * (size_t)ki + 1] = make_float4(acc.wxy, acc.wxz, acc.wyz, __int_as_float(acc.npair));
+    }
+    const unsigned c = __reduce_add_sync(FULL, (unsigned)ncand), r = __reduce_add_sync(FULL, (unsigned)nre);
+    if (lane == 0) {
+      atomicAdd(&v.sys_counters[2 * s], (unsigned long long)c);
+      if (r) atomicAdd(&v.sys_counters[2 * s + 1], (unsigned long long)r);
+    }
+  }
+}
+
+int batch_row_blocks(int sms) {
+  static int per_sm = 0;
+  if (!per_sm) {
+    cudaFuncSetAttribute(k_b_force_row, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_b_force_row, kRowThreads, 0) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+  }
+  return per_sm * sms;
+}
+
+cudaError_t launch_batch_force_row(cudaStream_t st, const BatchView &v, int blocks) {
+  cudaError_t e = cudaMemsetAsync(v.work, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(v.nrecheck, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(v.sys_counters, 0, 2 * sizeof(unsigned long long) * (size_t)v.nsys, st);
+  if (e != cudaSuccess) return e;
+  k_b_force_row<<<blocks, kRowThreads, 0, st>>>(v);
+  return cudaGetLastError();
+}
+
 }  // namespace nemd

@@ -289,6 +289,18 @@ int int_state_at_clock(nemd_ctx *c, double *q, int64_t n, double t_host) {
   return NEMD_OK;
 }
 
+// The force evaluation of a step: the cell-list hot path, or (with a skin
+// set by nemd_set_verlet) the Verlet list, rebuilt from a cell list when needed.
+int int_forces(nemd_ctx *c, int variant, double rc, double t) {
+  if (c->vl_skin > 0.0) {
+    c->have_cells = true;  // the list's build makes its own cells
+    return verlet_forces(c, c->f_int, variant, rc, t);
+  }
+  int r;
+  if ((r = nemd_build_cells(c, variant, rc))) return r;
+  return nemd_compute_forces(c, c->f_int, nullptr, nullptr);
+}
+
 // One step: first kick (which also advances the device clock), lattice at the
 // new time, drift and wrap, the force evaluation, second kick.
 int int_step(nemd_ctx *c, double *q, double *p, int64_t n, double t_host, int variant, double rc, int nb) {
@@ -296,8 +308,7 @@ int int_step(nemd_ctx *c, double *q, double *p, int64_t n, double t_host, int va
   k_int_kick1<<<nb, kIntThreads, 0, c->stream>>>(p, c->f_int, (int)n, c->int_state, c->int_part);
   if ((r = int_state_at_clock(c, q, n, t_host))) return r;
   k_int_drift<<<nb, kIntThreads, 0, c->stream>>>(q, p, (int)n, c->int_state, c->geo);
-  if ((r = nemd_build_cells(c, variant, rc))) return r;
-  if ((r = nemd_compute_forces(c, c->f_int, nullptr, nullptr))) return r;
+  if ((r = int_forces(c, variant, rc, t_host))) return r;
   k_int_kick2<<<nb, kIntThreads, 0, c->stream>>>(p, c->f_int, (int)n, c->int_state, c->int_part);
   c->launches += 3;
   cudaError_t e = cudaGetLastError();
@@ -345,8 +356,7 @@ int nemd_integrate(nemd_ctx *c, double *q, double *p, int64_t n, double t0, doub
     k_int_p2<<<nb, kIntThreads, 0, c->stream>>>(p, (int)n, c->int_part);
     k_int_k0<<<1, 32, 0, c->stream>>>(c->int_state, c->int_part, nb);
     c->launches += 2;
-    if ((r = nemd_build_cells(c, variant, rc))) break;
-    if ((r = nemd_compute_forces(c, c->f_int, nullptr, nullptr))) break;
+    if ((r = int_forces(c, variant, rc, t0))) break;
     int64_t k = 0;
     // the first step is launched (it sizes every buffer); then, unless the
     // options need per-step host work, one step is captured and replayed
@@ -354,7 +364,8 @@ int nemd_integrate(nemd_ctx *c, double *q, double *p, int64_t n, double t0, doub
       if ((r = int_step(c, q, p, n, t0 + dt, variant, rc, nb))) break;
       k = 1;
     }
-    if (nsteps > 2 && c->int_graph && !c->async_host && !c->timing) {
+    // (the Verlet list decides its rebuilds on the host: its steps are launched)
+    if (nsteps > 2 && c->int_graph && !c->async_host && !c->timing && c->vl_skin == 0.0) {
       // capture on a private stream (the context's may be the legacy default
       // stream, which cannot be captured); replay on the context's stream.  A
       // capture that fails leaves nothing executed: the steps are then launched.

@@ -121,6 +121,21 @@ struct __align__(16) Row {
 };
 static_assert(sizeof(Row) == 48, "Row is 48 bytes");
 
+// Geometry of the Verlet-list force at one step (verlet.cu): the list's
+// dynamic size grid c (cells at least rc + skin wide, fixed at the build), the
+// current cell vectors G = L(t) / c (float64, and as an exact multiple of the
+// quantum plus a float32 residual), and the float32 bands of the cut-off.
+struct VlGeo {
+  int c[3];
+  int pad;
+  double G[9];
+  float Gq[9], Gr[9];
+  float quantum_f, quantum_inv_f;
+  double quantum, quantum_inv;
+  float rc2_lo, rc2_hi, rc2_lo2, rc2_hi2;
+  double rl;  // rc + skin
+};
+
 // Per-block partial sums of the force kernel (float64): U, W (6 symmetric
 // components xx yy zz xy xz yz), interacting pairs, candidates, rechecks.
 constexpr int kPartials = 10;
@@ -240,6 +255,27 @@ struct nemd_ctx {
   const double *t_dev;  // while integrating: the lattice reads the time from here
   int int_graph;        // NEMD_OPT_INT_GRAPH: replay a captured step (default 1)
   cudaStream_t cap_stream;  // private stream the step is captured on
+  // Verlet list of nemd_integrate (nemd_set_verlet): pairs within rc + skin of
+  // the last build, per sorted particle in ELL layout (entry e of particle k at
+  // vl_ent[e * vl_n + k])
+  double vl_skin;           // 0: off
+  int64_t vl_capn;          // particles the per-particle buffers hold
+  int64_t vl_capent;        // entries vl_ent holds
+  int64_t vl_n;             // particles of the current list
+  int vl_maxk;              // entries per particle (ELL width) of the current list
+  int *vl_cnt;              // per sorted particle: its entries
+  int2 *vl_ent;             // (sorted j, packed cell offset)
+  int *vl_slot;             // per input particle: its sorted slot at the build
+  double *vl_sb;            // per sorted particle: fractional position at the build (3)
+  int4 *vl_idx;             // per sorted particle: list cell (x, y, z), brick image (packed) in w
+  float4 *vl_pos, *vl_res;  // per sorted particle, per step: position in its cell, residual
+  nemd::VlGeo *vl_geo;      // device
+  unsigned *vl_disp;        // device: largest displacement (float bits), its maximum entry count
+  unsigned *h_vl;           // pinned host copy of vl_disp[0..1]
+  int64_t vl_builds, vl_steps;
+  double vl_tb;             // time of the last build
+  double vl_delta;          // largest displacement measured at the last check
+  long long vl_period;      // remap period of the last build
 };
 
 namespace nemd {
@@ -250,6 +286,10 @@ cudaError_t launch_grid(nemd_ctx *c);
 cudaError_t launch_stencil(nemd_ctx *c);
 cudaError_t launch_bin(nemd_ctx *c);
 cudaError_t launch_forces(nemd_ctx *c, float *F_dev, double *UW_dev);
+cudaError_t launch_recheck_fixup(nemd_ctx *c, float *F_dev, double *UW_dev, int nblocks, bool half,
+                                 bool frame_is_cartesian);
+// Verlet list of nemd_integrate (verlet.cu): forces of the current state
+int verlet_forces(nemd_ctx *c, float *F, int variant, double rc, double t);
 // grouped force kernel: chunk list, then the kernel (returns the number of
 // blocks whose partials it wrote)
 bool chunk_kernel_applies(const nemd_ctx *c);

@@ -46,8 +46,8 @@ EXPORTED = ["nemd_create", "nemd_destroy", "nemd_set_flow", "nemd_set_potential"
             "nemd_model_save", "nemd_model_load", "nemd_batch_create", "nemd_batch_destroy",
             "nemd_batch_last_error", "nemd_batch_add", "nemd_batch_finalize", "nemd_batch_offsets",
             "nemd_batch_set_state", "nemd_batch_compute", "nemd_batch_sync", "nemd_batch_set_option",
-            "nemd_batch_get_stats", "nemd_batch_autotune"]
-NEMD_BATCH_OPT_CELL_FACTOR, NEMD_BATCH_OPT_TILE, NEMD_BATCH_OPT_GRAPH = 1, 2, 3
+            "nemd_batch_get_stats", "nemd_batch_autotune", "nemd_set_verlet", "nemd_get_verlet_stats"]
+NEMD_BATCH_OPT_CELL_FACTOR, NEMD_BATCH_OPT_TILE, NEMD_BATCH_OPT_GRAPH, NEMD_BATCH_OPT_KERNEL = 1, 2, 3, 4
 NEMD_MLP_INPUTS, NEMD_MLP_OUTPUTS, NEMD_MLP_PARAMS, NEMD_MLP_NORM = 12, 4, 5252, 26
 NEMD_NOALLOC_MAX_N = 16384
 NEMD_NOALLOC_MAX_CELLS = 16384
@@ -95,6 +95,8 @@ _sig = {
     "nemd_integrate": ([_vp, _vp, _vp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                         ctypes.c_int, ctypes.c_double, ctypes.c_int], ctypes.c_int),
     "nemd_sync": ([_vp], ctypes.c_int),
+    "nemd_set_verlet": ([_vp, ctypes.c_double], ctypes.c_int),
+    "nemd_get_verlet_stats": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "nemd_last_error": ([_vp], ctypes.c_char_p),
     "nemd_set_option": ([_vp, ctypes.c_int, ctypes.c_int64], ctypes.c_int),
     "nemd_get_lattice": ([_vp, _vp], ctypes.c_int),
@@ -235,6 +237,17 @@ class Context:
 
     def sync(self):
         return self._check(nemd_sync(self.h))
+
+    def set_verlet(self, skin):
+        """Verlet list with this skin for integrate (0: off; see nemd_set_verlet)."""
+        return self._check(nemd_set_verlet(self.h, float(skin)))
+
+    def verlet_stats(self):
+        """(builds, evaluations, entries per particle, last displacement) since the last set_verlet."""
+        b, s, w, d = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_double(0.0)
+        self._check(nemd_get_verlet_stats(self.h, ctypes.byref(b), ctypes.byref(s), ctypes.byref(w),
+                                          ctypes.byref(d)))
+        return int(b.value), int(s.value), int(w.value), float(d.value)
 
     def set_option(self, key, value):
         return self._check(nemd_set_option(self.h, int(key), int(value)))

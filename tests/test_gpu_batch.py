@@ -46,7 +46,7 @@ def test_batch_equals_single_contexts_and_oracle():
     b = nemd.Batch([spec(w, v) for w, v in zip(ws, vs)])
     F, UW = evaluate(b, ws)
     st, launches = b.stats()
-    assert launches == 17
+    assert launches == 18
     for s, (w, v) in enumerate(zip(ws, vs)):
         lo, hi = b.offsets[s], b.offsets[s + 1]
         one = run(w, v, kernel=(2, 32))
@@ -59,8 +59,8 @@ def test_batch_equals_single_contexts_and_oracle():
         ref = oracle.evaluate(w, "ds")
         assert st[s]["pairs"] == ref.npairs
         assert force_err(F[lo:hi], ref.F) <= 1e-5, s
-        assert rel(UW[s, 0], ref.U) <= 5e-6
-        assert mat_rel(UW[s, 1:].reshape(3, 3), ref.W) <= 5e-6
+        assert rel(UW[s, 0], ref.U) <= 3e-6
+        assert mat_rel(UW[s, 1:].reshape(3, 3), ref.W) <= 3e-6
         assert st[s]["status"] == 0
     b.close()
 
@@ -93,7 +93,7 @@ def test_strains_advance_each_system():
             lo, hi = b.offsets[s], b.offsets[s + 1]
             assert st[s]["pairs"] == ref.npairs
             assert force_err(F[lo:hi], ref.F) <= 1e-5
-            assert rel(UW[s, 0], ref.U) <= 5e-6
+            assert rel(UW[s, 0], ref.U) <= 3e-6
     b.close()
 
 
@@ -110,7 +110,7 @@ def test_cell_factor_and_tile_keep_results(kfac, tile):
         lo, hi = b.offsets[s], b.offsets[s + 1]
         assert st[s]["pairs"] == ref.npairs and st[s]["cell_factor"] == kfac
         assert force_err(F[lo:hi], ref.F) <= 1e-5
-        assert rel(UW[s, 0], ref.U) <= 5e-6
+        assert rel(UW[s, 0], ref.U) <= 3e-6
     b.close()
 
 

@@ -19,8 +19,10 @@ if not torch.cuda.is_available():
 from paper_1412_3784_gb300 import nemd  # noqa: E402
 
 F_TOL = 1e-5
-UW_TOL_FAST = 5e-6
+UW_TOL_FAST = 3e-6
+UW_TOL_PRECISE = 1e-9
 WARP = (2, 32)
+ROW = (4, 32)
 
 
 def evaluate(ctx, w, q, variant):
@@ -34,23 +36,28 @@ def evaluate(ctx, w, q, variant):
     return F.cpu().numpy().astype(np.float64), float(U.item()), Wv.cpu().numpy().reshape(3, 3), ctx.stats()
 
 
-def check(F, U, Wm, st, ref):
+def check(F, U, Wm, st, ref, uw_tol=UW_TOL_FAST):
     assert st["pairs"] == ref.npairs
     assert force_err(F, ref.F) <= F_TOL
-    assert rel(U, ref.U) <= UW_TOL_FAST
-    assert mat_rel(Wm, ref.W) <= UW_TOL_FAST
+    assert rel(U, ref.U) <= uw_tol
+    assert mat_rel(Wm, ref.W) <= uw_tol
 
 
 @pytest.mark.parametrize("t", [0.37, W.NEAR_REMAP_T])
 def test_general_n1m_bench_configuration(t):
-    """N = 1,048,576 general flow: warp kernel, per-step variant by the volume rule."""
+    """N = 1,048,576 general flow: warp and row kernels, per-step variant by the volume rule."""
     ser = W.general_series(k=64)
     w = ser.workload(t)
     ref = oracle.evaluate(w, "ds")
     ctx = make_ctx(w, nemd, torch)
-    ctx.set_option(nemd.NEMD_OPT_KERNEL, 2)
     q = torch.from_numpy(w.q).cuda()
-    check(*evaluate(ctx, w, q, nemd.NEMD_AUTO_HEURISTIC), ref)
+    for kern in (2, 4):
+        ctx.set_option(nemd.NEMD_OPT_KERNEL, kern)
+        check(*evaluate(ctx, w, q, nemd.NEMD_AUTO_HEURISTIC), ref)
+    # the row kernel's precise mode (float-float energy and virial): 1e-9
+    ctx.set_option(nemd.NEMD_OPT_PRECISE, 1)
+    check(*evaluate(ctx, w, q, nemd.NEMD_AUTO_HEURISTIC), ref, UW_TOL_PRECISE)
+    ctx.set_option(nemd.NEMD_OPT_PRECISE, 0)
     # the plain fixed-variant cell lists on the same state
     ctx.set_option(nemd.NEMD_OPT_KERNEL, 0)
     for variant in (nemd.NEMD_DS, nemd.NEMD_DO):
@@ -64,14 +71,21 @@ def test_general_n2m_cell_factors():
     w = ser.workload(0.61 * ser.period)
     ref = oracle.evaluate(w, "ds")
     ctx = make_ctx(w, nemd, torch)
-    ctx.set_option(nemd.NEMD_OPT_KERNEL, 2)
     q = torch.from_numpy(w.q).cuda()
-    for kfac in (1, 2):
-        ctx.set_option(nemd.NEMD_OPT_CELL_FACTOR, kfac)
-        for variant in (nemd.NEMD_DS, nemd.NEMD_DO):
-            F, U, Wm, st = evaluate(ctx, w, q, variant)
-            assert st["cell_factor"] == kfac
-            check(F, U, Wm, st, ref)
+    for kern in (2, 4):
+        ctx.set_option(nemd.NEMD_OPT_KERNEL, kern)
+        for kfac in (1, 2):
+            ctx.set_option(nemd.NEMD_OPT_CELL_FACTOR, kfac)
+            for variant in (nemd.NEMD_DS, nemd.NEMD_DO):
+                F, U, Wm, st = evaluate(ctx, w, q, variant)
+                assert st["cell_factor"] == kfac
+                check(F, U, Wm, st, ref)
+    # precise mode on the row kernel, both cell lists: energy and virial to 1e-9
+    ctx.set_option(nemd.NEMD_OPT_KERNEL, 4)
+    ctx.set_option(nemd.NEMD_OPT_CELL_FACTOR, 1)
+    ctx.set_option(nemd.NEMD_OPT_PRECISE, 1)
+    for variant in (nemd.NEMD_DS, nemd.NEMD_DO):
+        check(*evaluate(ctx, w, q, variant), ref, UW_TOL_PRECISE)
     ctx.close()
 
 
@@ -106,7 +120,8 @@ def test_general_n256k_pair_set_at_max_skew():
     w = W.config_general(t=W.NEAR_REMAP_T, k=40)
     ref = oracle.evaluate(w, "ds", want_pairs=True)
     for variant in (0, 1):
-        g = run(w, variant, record=True, kernel=WARP)
-        assert g["stats"]["pairs"] == ref.npairs
-        assert np.array_equal(oracle.canonical_pair_keys(g["pairs"]), oracle.canonical_pair_keys(ref.pairs))
-        assert force_err(g["F"], ref.F) <= F_TOL
+        for kern in (WARP, ROW):
+            g = run(w, variant, record=True, kernel=kern)
+            assert g["stats"]["pairs"] == ref.npairs
+            assert np.array_equal(oracle.canonical_pair_keys(g["pairs"]), oracle.canonical_pair_keys(ref.pairs))
+            assert force_err(g["F"], ref.F) <= F_TOL

@@ -82,18 +82,26 @@ def test_device_inference_picks_argmin_of_predictions(tmp_path):
     ctx.close()
 
 
-def test_learned_choice_regret_not_worse_than_volume_rule():
-    """Measured timings of the four options on strained systems: the model,
-    trained on some strains, is judged on others against the exhaustive
-    choice, next to the paper's neighbourhood-volume rule (k = 1)."""
+def test_learned_choice_beats_volume_rule_on_held_out_strains():
+    """Measured timings of the four options (cell list variant x cell factor) of
+    the row kernel on strained LJ and WCA systems: the model, trained on two
+    thirds of the strains, is judged on the others against the exhaustive
+    choice, next to the paper's neighbourhood-volume rule (k = 1).  The rule
+    counts cells; the row kernel's cost is not proportional to them (each lane
+    searches only its own window along the row), and for WCA the rule often
+    picks the dynamic offset list where the dynamic size one is faster."""
     rows_f, rows_t, rule = [], [], []
-    for ser in (W.general_series(k=14, seed=11), W.planar_series(k=16, seed=12)):
+    series = (W.general_series(k=14, seed=11), W.planar_series(k=16, seed=12),
+              W.StrainSeries(W.M_GENERAL, 14, 13, kind=W.POT_WCA), W.StrainSeries(W.M_PLANAR, 12, 14, kind=W.POT_WCA))
+    for ser in series:
         ctx = make_ctx(ser.workload(0.0), nemd, torch)
+        ctx.set_option(nemd.NEMD_OPT_KERNEL, 4)
         for i in range(24):
             t = (i + 0.5) / 24 * ser.period
             q = torch.from_numpy(ser.positions(t)).cuda()
             ctx.set_state(q, t)
-            f, ms = ctx.time_options(ser.rc, reps=2)
+            f, ms = ctx.time_options(ser.rc, reps=3)
+            ctx.set_option(nemd.NEMD_OPT_CELL_FACTOR, 1)
             ctx.build_cells(nemd.NEMD_AUTO_HEURISTIC, ser.rc)
             ctx.compute_forces()
             rows_f.append(f)
@@ -110,5 +118,5 @@ def test_learned_choice_regret_not_worse_than_volume_rule():
     best = T[test].min(axis=1)
     regret_learned = float((T[test][np.arange(test.sum()), pick] - best).sum())
     regret_rule = float((T[test][np.arange(test.sum()), np.array(rule)[test]] - best).sum())
-    assert regret_learned <= regret_rule + 0.05 * best.sum()
+    assert regret_learned < regret_rule
     ctx.close()

@@ -3,11 +3,16 @@
 Bars:
   pair sets            bit-exact (i, j, n) against the oracle
   forces               max|dF| / max|F| <= 1e-5   (float32 pair arithmetic)
-  energy, virial       rel <= 1e-9 in precise mode (float64 accepted pairs);
+  energy, virial       rel <= 1e-9 in precise mode (accepted pairs in float64
+                       or float-float, summed in float64 / float-float);
                        fast mode (float32 pair terms summed per particle in
-                       float32, float64 across particles) <= 5e-6: each pair
-                       term carries ~13 roundings of 2^-24 amplified by at most
-                       the r^-12 slope, and ~55 terms are summed per particle
+                       float32, float64 across particles) <= 3e-6: the error
+                       is a few float32 roundings per pair term times the
+                       sum's condition number (sum of |terms| over |sum|), not a
+                       function of N; the worst measured is 1.4e-6 (virial of
+                       the 2^21-particle system compressed at t = 0.61 T; 2.8e-7
+                       on the smaller systems of this file), the bar leaves a
+                       factor 2
   lattice              |L_gpu - L_oracle| <= 1e-13 |L|
 """
 import numpy as np
@@ -26,7 +31,7 @@ if not torch.cuda.is_available():
 DS, DO = 0, 1
 F_TOL = 1e-5
 UW_TOL_PRECISE = 1e-9
-UW_TOL_FAST = 5e-6
+UW_TOL_FAST = 3e-6
 
 
 def keys(p):

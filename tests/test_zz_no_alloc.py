@@ -25,7 +25,7 @@ if not torch.cuda.is_available():
 from paper_1412_3784_gb300 import nemd  # noqa: E402
 
 F_TOL = 1e-5
-UW_TOL = 5e-6
+UW_TOL = 3e-6
 
 
 def call_noalloc(w, variant):
