@@ -86,8 +86,8 @@ __global__ void k_vl_init(const Geo *__restrict__ g, const double *__restrict__ 
 // candidate whose quantised distance passes the coarse test at rl (a superset
 // of the pairs within rl).  COUNT: entries per particle only.  Otherwise the
 // entries (sorted j, cell offset k = idx_j - idx_i + c n, n the pair's lattice
-// image) in ELL layout; a particle with more than maxk entries sets the
-// capacity error.
+// image) in ELL layout, at most maxk per particle; both report the largest
+// count in maxcnt (the host repeats the fill with more room if it exceeded maxk).
 template <bool COUNT>
 __global__ void __launch_bounds__(kVlThreads) k_vl_build(
     Geo *__restrict__ g, const float4 *__restrict__ pos, const int *__restrict__ cell_sorted,
@@ -144,12 +144,8 @@ __global__ void __launch_bounds__(kVlThreads) k_vl_build(
         }
       }
     }
-    if (COUNT) {
-      atomicMax(maxcnt, (unsigned)e);
-    } else {
-      if (e > maxk) atomicOr(&g->error, ERRB_CAPACITY);
-      cnt[k] = min(e, maxk);
-    }
+    atomicMax(maxcnt, (unsigned)e);
+    if (!COUNT) cnt[k] = min(e, maxk);
   }
 }
 
@@ -281,11 +277,22 @@ __global__ void __launch_bounds__(kVlThreads) k_vl_force(
     }
     const int ne = cnt[k];
     ncand = ne;
-    for (int e = 0; e < ne; e++) {
-      const int2 en = ent[(size_t)e * n + k];
+    constexpr int U = 4;  // entries loaded together (independent gathers in flight)
+    for (int e0 = 0; e0 < ne; e0 += U) {
+      int2 eu[U];
+      float4 pu[U];
+#pragma unroll
+      for (int h = 0; h < U; h++)
+        eu[h] = e0 + h < ne ? __ldcs(&ent[(size_t)(e0 + h) * n + k]) : make_int2(k, 0);
+#pragma unroll
+      for (int h = 0; h < U; h++) pu[h] = pos[eu[h].x];
+#pragma unroll
+      for (int h = 0; h < U; h++) {
+      if (e0 + h >= ne) break;
+      const int2 en = eu[h];
       const int j = en.x;
       const float k0 = (float)unpack_k(en.y, 0), k1 = (float)unpack_k(en.y, 1), k2 = (float)unpack_k(en.y, 2);
-      const float4 pj = pos[j];
+      const float4 pj = pu[h];
       // quantised part: exact (every term a multiple of the quantum, bounded)
       const float dx = (pj.x - pi.x) + ((Gq[0] * k0 + Gq[1] * k1) + Gq[2] * k2);
       const float dy = (pj.y - pi.y) + ((Gq[3] * k0 + Gq[4] * k1) + Gq[5] * k2);
@@ -320,6 +327,7 @@ __global__ void __launch_bounds__(kVlThreads) k_vl_force(
       if (!accept) continue;
       acc.add_r2(pp, cx, cy, cz, r2c);
       if (RECORD) record_pair(g, q, oi, __float_as_int(pj.w), nn[0], nn[1], nn[2], pair_buf, pair_count, pair_cap);
+      }
     }
     if (F) {
       F[3 * (size_t)oi] = acc.fx;
@@ -411,29 +419,58 @@ int verlet_forces(nemd_ctx *c, float *F, int variant, double rc, double t) {
     rebuild = !(sigma * rl - 2.0 * (double)delta >= rc * (1.0 + 1e-9));
   }
   if (rebuild) {
-    if ((r = nemd_build_cells(c, variant, rl))) return r;
+    // the search of the build on cells half as wide (cell factor 2): fewer
+    // candidates than at factor 1, same pairs
+    const int kf = c->kfac;
+    const bool tuned = c->autotuned;
+    c->kfac = 2;
+    c->autotuned = false;  // the tuned choice is for the force at rc
+    r = nemd_build_cells(c, variant, rl);
+    c->kfac = kf;
+    c->autotuned = tuned;
+    if (r) return r;
     k_vl_init<<<nb, kVlThreads, 0, c->stream>>>(c->geo, c->q_dev, c->pos4, (int)n, rl, c->vl_sb, c->vl_idx,
                                                 c->vl_slot, c->vl_geo);
-    if ((r = vl_cuda(c, cudaMemsetAsync(c->vl_disp + 1, 0, sizeof(unsigned), c->stream), "memset"))) return r;
-    k_vl_build<true><<<nb, kVlThreads, 0, c->stream>>>(c->geo, c->pos4, c->cell_sorted, c->start, c->rows,
-                                                       c->rowcnt, (int)n, c->vl_idx, c->vl_geo, nullptr, nullptr, 0,
-                                                       c->vl_disp + 1);
-    if ((r = vl_cuda(c, cudaMemcpyAsync(c->h_vl + 1, c->vl_disp + 1, sizeof(unsigned), cudaMemcpyDeviceToHost,
-                                        c->stream),
-                     "copy")))
-      return r;
-    if ((r = vl_cuda(c, cudaStreamSynchronize(c->stream), "sync"))) return r;
-    const int maxk = (int)c->h_vl[1] + 1;
-    if ((r = vl_grow(c, &c->vl_ent, (int64_t)maxk * n, &c->vl_capent))) return r;
-    k_vl_build<false><<<nb, kVlThreads, 0, c->stream>>>(c->geo, c->pos4, c->cell_sorted, c->start, c->rows,
-                                                        c->rowcnt, (int)n, c->vl_idx, c->vl_geo, c->vl_cnt,
-                                                        c->vl_ent, maxk, c->vl_disp + 1);
+    c->launches += 1;
+    // fill with the width of the previous list (plus room); if a particle has
+    // more entries, fill again with the width the fill measured
+    int maxk = c->vl_n == n && c->vl_maxk > 0 ? c->vl_maxk + 16 : 0;
+    for (int pass = 0; pass < 2; pass++) {
+      if ((r = vl_cuda(c, cudaMemsetAsync(c->vl_disp + 1, 0, sizeof(unsigned), c->stream), "memset"))) return r;
+      if (maxk == 0) {
+        k_vl_build<true><<<nb, kVlThreads, 0, c->stream>>>(c->geo, c->pos4, c->cell_sorted, c->start, c->rows,
+                                                           c->rowcnt, (int)n, c->vl_idx, c->vl_geo, nullptr, nullptr,
+                                                           0, c->vl_disp + 1);
+      } else {
+        if ((r = vl_grow(c, &c->vl_ent, (int64_t)maxk * n, &c->vl_capent))) return r;
+        k_vl_build<false><<<nb, kVlThreads, 0, c->stream>>>(c->geo, c->pos4, c->cell_sorted, c->start, c->rows,
+                                                            c->rowcnt, (int)n, c->vl_idx, c->vl_geo, c->vl_cnt,
+                                                            c->vl_ent, maxk, c->vl_disp + 1);
+      }
+      c->launches += 1;
+      if ((r = vl_cuda(c, cudaMemcpyAsync(c->h_vl + 1, c->vl_disp + 1, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                          c->stream),
+                       "copy")))
+        return r;
+      if ((r = vl_cuda(c, cudaStreamSynchronize(c->stream), "sync"))) return r;
+      const int need = (int)c->h_vl[1];
+      c->vl_maxk = need;
+      if (maxk > 0 && need <= maxk) break;
+      maxk = need + 16;
+      if (pass == 1) {
+        // the count pass ran first: fill now with its width
+        if ((r = vl_grow(c, &c->vl_ent, (int64_t)maxk * n, &c->vl_capent))) return r;
+        k_vl_build<false><<<nb, kVlThreads, 0, c->stream>>>(c->geo, c->pos4, c->cell_sorted, c->start, c->rows,
+                                                            c->rowcnt, (int)n, c->vl_idx, c->vl_geo, c->vl_cnt,
+                                                            c->vl_ent, maxk, c->vl_disp + 1);
+        c->launches += 1;
+      }
+    }
     k_vl_geo<<<1, 32, 0, c->stream>>>(c->geo, c->vl_geo, rc);
     if ((r = vl_cuda(c, cudaMemsetAsync(c->vl_disp, 0, sizeof(unsigned), c->stream), "memset"))) return r;
     k_vl_pos<<<nb, kVlThreads, 0, c->stream>>>(c->geo, c->vl_geo, c->q_dev, (int)n, c->vl_slot, c->vl_sb, c->vl_idx,
                                                c->vl_pos, c->vl_res, c->vl_disp);
-    c->launches += 5;
-    c->vl_maxk = maxk;
+    c->launches += 2;
     c->vl_n = n;
     c->vl_tb = t;
     c->vl_period = period;
