@@ -136,6 +136,28 @@ struct Acc {
     wyz = fmaf(gy, dz, wyz);
     npair++;
   }
+  // The same sums without the potential's constant factors, which the caller
+  // applies once per particle: fr = (1/r^2) s6 (2 s6 - 1) for the force and
+  // virial (times 24 eps) and s6 (s6 - 1) for the energy (times 4 eps, less
+  // the shift per pair), s6 = (sigma^2 / r^2)^3.
+  __device__ __forceinline__ void add_unscaled(float sig2, float dx, float dy, float dz, float r2) {
+    const float inv = __fdividef(1.0f, r2);
+    const float s2 = sig2 * inv;
+    const float s6 = s2 * s2 * s2;
+    const float fr = inv * s6 * fmaf(2.0f, s6, -1.0f);
+    u = fmaf(s6, s6 - 1.0f, u);
+    const float gx = fr * dx, gy = fr * dy, gz = fr * dz;
+    fx -= gx;
+    fy -= gy;
+    fz -= gz;
+    wxx = fmaf(gx, dx, wxx);
+    wyy = fmaf(gy, dy, wyy);
+    wzz = fmaf(gz, dz, wzz);
+    wxy = fmaf(gx, dy, wxy);
+    wxz = fmaf(gx, dz, wxz);
+    wyz = fmaf(gy, dz, wyz);
+    npair++;
+  }
 };
 
 // t = x_i - (shift + n * step), exact for quantised operands (the fused

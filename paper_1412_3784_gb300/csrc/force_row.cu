@@ -19,12 +19,14 @@
 // shared memory).  Its threshold rc2_hi + e_i bounds every rounding of the
 // half-precision values for any candidate whose quantised distance is within
 // the coarse band, so no partner is lost; a candidate accepted only through
-// e_i fails the exact test of the flush.  Accepted slots are queued per lane
-// and their forces computed in flushes, run only when the next row would not
-// fit in the stage (or a queue could overflow).  Rows are visited in opposite
-// pairs (a lane with many partners in one row has few in the opposite one), so
-// the lanes' queues are about equally long when they are flushed.  Each lane
-// accumulates its particle's force in queue order: results are deterministic.
+// e_i fails the exact test of the flush.  The results of 32 candidates form one
+// accept mask per lane (no dependence between the tests, one store per mask),
+// and the accepted slots' forces are computed in flushes, run only when the
+// next row would not fit in the stage (or the masks could overflow).  Rows are
+// visited in opposite pairs (a lane with many partners in one row has few in
+// the opposite one), so the lanes have about equally many accepted slots when
+// they are flushed.  Each lane accumulates its particle's force in a fixed
+// order: results are deterministic.
 #include <cuda_fp16.h>
 #include <math.h>
 #include <string.h>
@@ -41,32 +43,56 @@ namespace nemd {
 #ifndef NEMD_ROW_STAGE
 #define NEMD_ROW_STAGE 240
 #endif
-#ifndef NEMD_ROW_QUEUE
-#define NEMD_ROW_QUEUE 64
+#ifndef NEMD_ROW_WORDS
+#define NEMD_ROW_WORDS 12
 #endif
 constexpr int kRowThreads = 128;
 constexpr int kRowMinBlocks = NEMD_ROW_MINBLOCKS;
 constexpr int kRowStage = NEMD_ROW_STAGE;  // even
-constexpr int kRowQueue = NEMD_ROW_QUEUE;
-constexpr int kRowCheck = 16;        // slot pairs (32 candidates) between two queue checks
+constexpr int kRowWords = NEMD_ROW_WORDS;  // accept masks per lane between two flushes
 constexpr int kRowRowsStaged = 32;   // rows per class the kernel stages (cell factor <= 2)
 constexpr int kRowABias = 64;        // SA[slot] = row | (A + kRowABias) << 5
+constexpr int kRowPad = 32;          // half slots past the stage that a lane's last mask may read
 static_assert(kRowStage % 2 == 0, "slots are tested in pairs");
-static_assert(kRowQueue >= 2 * 2 * kRowCheck, "a queue check must leave room for a test block");
-static_assert(kRowStage + 2 <= 256, "queue entries are one byte");
+static_assert(kRowStage <= 256, "mask bases are one byte");
 
-// Shared memory of one warp.  Slots [kRowStage, kRowStage + 2) of the half
-// arrays hold a sentinel pair (never within any cut-off).
+// Shared memory of one warp.  The half arrays extend kRowPad slots past the
+// stage: the tests of a mask read whole slot pairs, and every candidate outside
+// the lane's window (stale or never written) is cleared from the mask.
 struct RowStage {
   float4 X[kRowStage];   // chunk frame, exact quantised part; .w: kappa
   float4 R[kRowStage];   // residual part; .w: sorted index of j (bits)
-  __half hx[kRowStage + 2], hy[kRowStage + 2], hz[kRowStage + 2];
+  __half hx[kRowStage + kRowPad], hy[kRowStage + kRowPad], hz[kRowStage + kRowPad];
   unsigned short SA[kRowStage];  // row of the slot and its cell offset A from the chunk's first cell
-  unsigned char q[kRowQueue][32];
+  unsigned mq[kRowWords][32];       // accepted candidates of a lane: bit b is slot mb + b
+  unsigned char mb[kRowWords][32];  // first slot of each mask
   float4 rows[kRowRowsStaged][3];
 };
 
 constexpr float kHalfSentinel = 65504.0f;  // largest finite half: its square overflows
+
+// Bits k and 16 + k (the low and high candidate of slot pair k) to bits 2k and
+// 2k + 1: the outer perfect shuffle of a 32-bit word, four swap steps
+// (Warren, Hacker's Delight, Sec. 7-2).
+__device__ __forceinline__ unsigned row_shuffle(unsigned x) {
+  unsigned t;
+  t = (x ^ (x >> 8)) & 0x0000FF00u;
+  x ^= t ^ (t << 8);
+  t = (x ^ (x >> 4)) & 0x00F000F0u;
+  x ^= t ^ (t << 4);
+  t = (x ^ (x >> 2)) & 0x0C0C0C0Cu;
+  x ^= t ^ (t << 2);
+  t = (x ^ (x >> 1)) & 0x22222222u;
+  x ^= t ^ (t << 1);
+  return x;
+}
+
+// Bits [a, e) of a 32-bit word, the bounds clamped to [0, 32].
+__device__ __forceinline__ unsigned row_range_bits(int a, int e) {
+  a = min(max(a, 0), 32);
+  e = min(max(e, 0), 32);
+  return (unsigned)(((1ull << e) - 1ull) & ~((1ull << a) - 1ull));
+}
 
 // Stencil image (kx, ky, kz) of a staged slot: its row gives (ky, kz) and the
 // row's x-shift sxi; its unwrapped x-cell is ixlo + A - sxi.
@@ -198,24 +224,41 @@ __device__ __forceinline__ float3 pair_ff(const PotFF &pf, float hx, float lx, f
   return make_float3(__fadd_rn(gx.hi, gx.lo), __fadd_rn(gy.hi, gy.lo), __fadd_rn(gz.hi, gz.lo));
 }
 
-// Forces of the queued pairs of every lane (Sec. 5 potential): each entry is
+// The next accepted slot of a lane: the highest set bit of its current mask,
+// the next stored mask once that one is used up (qn counts what is left).
+__device__ __forceinline__ int row_next_slot(const RowStage &S, int lane, unsigned &cur, int &base, int &wi) {
+  if (cur == 0) {
+    cur = S.mq[wi][lane];
+    base = S.mb[wi][lane];
+    wi++;
+  }
+  const int b = 31 - __clz(cur);
+  cur ^= 1u << b;
+  return base + b;
+}
+
+// Forces of the accepted slots of every lane (Sec. 5 potential): each is
 // decided with the residuals added back; the few within float32 rounding of
-// rc go to the float64 fix-up pass (RECORD: decided here in float64).
+// rc go to the float64 fix-up pass (RECORD: decided here in float64) and are
+// counted in nre.  Fast mode sums the pair terms without the potential's
+// constant factors (Acc::add_unscaled).
 template <bool RECORD, bool PRECISE>
-__device__ __forceinline__ void row_flush(RowStage &S, int &qn, int &nre, int lane, int ki, const float4 &pi,
-                                          const float3 &Xi, const float3 &Ri, int ixlo, const Geo *g,
-                                          const float4 *__restrict__ pos, const Pot &pp, const PotFF &pf,
-                                          Acc &acc, AccFF &accp, const double *q,
+__device__ __forceinline__ void row_flush(RowStage &S, int &qn, int &nw, int &nre, int lane, int ki,
+                                          const float4 &pi, const float3 &Xi, const float3 &Ri, int ixlo,
+                                          const Geo *g, const float4 *__restrict__ pos, const Pot &pp,
+                                          const PotFF &pf, Acc &acc, AccFF &accp, const double *q,
                                           int32_t *pair_buf, unsigned long long *pair_count, long long pair_cap,
                                           int4 *rlist, int *rcount, int *err) {
   const int m = __reduce_max_sync(0xffffffffu, qn);
-  const float lo = g->rc2_lo, hi = g->rc2_hi, lo2 = g->rc2_lo2, hi2 = g->rc2_hi2;
+  const float lo2 = g->rc2_lo2, hi2 = g->rc2_hi2;
+  unsigned cur = 0;
+  int base = 0, wi = 0;
   // two entries per pass, both loaded before either is used (independent
   // chains for the scheduler); each is decided and added on its own
   for (int s = 0; s < m; s += 2) {
     const bool v0 = s < qn, v1 = s + 1 < qn;
-    const int sl0 = v0 ? S.q[s][lane] : 0;
-    const int sl1 = v1 ? S.q[s + 1][lane] : 0;
+    const int sl0 = v0 ? row_next_slot(S, lane, cur, base, wi) : 0;
+    const int sl1 = v1 ? row_next_slot(S, lane, cur, base, wi) : 0;
     const float4 X0 = S.X[sl0], R0 = S.R[sl0], X1 = S.X[sl1], R1 = S.R[sl1];
 #pragma unroll
     for (int h = 0; h < 2; h++) {
@@ -228,10 +271,10 @@ __device__ __forceinline__ void row_flush(RowStage &S, int &qn, int &nre, int la
       const float cz = (X.z - Xi.z) + (R.z - Ri.z);
       const float r2c = fmaf(cz, cz, fmaf(cy, cy, cx * cx));
       bool accept = r2c < lo2;
-      if (!(r2c < lo) && r2c < hi) nre++;
       if (!accept && r2c < hi2) {
         int kx, ky, kz;
         row_slot_image(S, slot, ixlo, g->nc[0], kx, ky, kz);
+        nre++;
         if (RECORD)
           accept = guard_band_accept(g, q, __float_as_int(pi.w), __float_as_int(pos[j].w), kx, ky, kz);
         else
@@ -246,7 +289,7 @@ __device__ __forceinline__ void row_flush(RowStage &S, int &qn, int &nre, int la
           acc.fz -= gj.z;
           acc.npair++;
         } else {
-          acc.add_r2(pp, cx, cy, cz, r2c);
+          acc.add_unscaled(pp.sig2, cx, cy, cz, r2c);
         }
         if (RECORD) {
           int kx, ky, kz;
@@ -258,6 +301,7 @@ __device__ __forceinline__ void row_flush(RowStage &S, int &qn, int &nre, int la
     }
   }
   qn = 0;
+  nw = 0;
 }
 
 // Everything one warp does for one chunk cd (x: first sorted particle, y:
@@ -311,15 +355,10 @@ __device__ __forceinline__ void row_chunk(const int4 cd, const Row *__restrict__
     const float4 *src = reinterpret_cast<const float4 *>(crow);
     __syncwarp();
     for (int e = lane; e < 3 * nr; e += 32) S.rows[e / 3][e % 3] = src[e];
-    if (lane < 2) {
-      S.hx[kRowStage + lane] = __float2half_rn(kHalfSentinel);
-      S.hy[kRowStage + lane] = __float2half_rn(kHalfSentinel);
-      S.hz[kRowStage + lane] = __float2half_rn(kHalfSentinel);
-    }
     __syncwarp();
   }
   acc.fx = acc.fy = acc.fz = 0.f;
-  int qn = 0, fill = 0;
+  int qn = 0, nw = 0, fill = 0;  // accepted slots and stored masks of the lane; staged slots
   // extent of the lanes along the row (cells from the chunk's first cell)
   float pmin = act ? kapi : 1e30f, pmax = act ? kapi : -1e30f;
 #pragma unroll
@@ -343,47 +382,56 @@ __device__ __forceinline__ void row_chunk(const int4 cd, const Row *__restrict__
         rb1 = start[cbase];
         re1 = start[cbase + min(rest, l1)];
       }
-      // staged slots of the row (padded to even); a row of more than two runs
-      // counts as the whole stage
-      rcnt = rest > l1 ? kRowStage : (re0 - rb0) + (re1 - rb1) + 1;
+      // staged slots of the row; a row of more than two runs counts as the
+      // whole stage
+      rcnt = rest > l1 ? kRowStage : (re0 - rb0) + (re1 - rb1);
     }
   }
 
   // Per-lane window test of the staged slots [sb, se) of one row: binary
-  // searches for the lane's kappa window, then slot pairs in half precision; a
-  // lane writes the slot of every tested candidate to its queue and advances
-  // only when the test passes (no branch).
+  // searches for the lane's kappa window [lo, hi), then slot pairs in half
+  // precision from an even start m0, 32 candidates per accept mask.  Every lane
+  // reads np pairs (the warp's longest window), from its own window or, where
+  // that would run past the row, from the row's last np pairs: the reads stay
+  // within the stage and its padding, and the mask keeps [lo, hi) only.
   auto test_range = [&](int sb, int se) {
     if (se <= sb) return;
     __syncwarp();
     int lo, hi;
     row_bounds(S, sb, se, kapi - rho, kapi + rho, lo, hi);
-    const int m0 = lo & ~1;
-    const int np = (act && hi > lo) ? ((((hi + 1) & ~1) - m0) >> 1) : 0;
-    if (act && hi > lo) ncand += hi - lo;
-    const int maxnp = __reduce_max_sync(FULL, np);
-    for (int p0 = 0; p0 < maxnp; p0 += kRowCheck) {
-      if (__any_sync(FULL, qn > kRowQueue - 2 * kRowCheck))
-        row_flush<RECORD, PRECISE>(S, qn, nre, lane, ki, pi, Xi, Ri, ixlo, g, pos, pp, pf, acc, accp, q, pair_buf, pair_count,
-                          pair_cap, rlist, rcount, err);
-      const int pend = min(maxnp, p0 + kRowCheck);
-#pragma unroll 4
-      for (int p = p0; p < pend; p++) {
-        const int s = p < np ? m0 + 2 * p : kRowStage;  // past its window: the sentinel pair
-        const __half2 hxv = *reinterpret_cast<const __half2 *>(&S.hx[s]);
-        const __half2 hyv = *reinterpret_cast<const __half2 *>(&S.hy[s]);
-        const __half2 hzv = *reinterpret_cast<const __half2 *>(&S.hz[s]);
-        const __half2 dx = __hsub2(hxv, xi2), dy = __hsub2(hyv, yi2), dz = __hsub2(hzv, zi2);
-        const __half2 r2 = __hfma2(dx, dx, __hfma2(dy, dy, __hmul2(dz, dz)));
-        // r2 < thr exactly when r2 - thr is negative (the sign of a difference
-        // is exact; equal values give +0, infinities a positive result)
-        const __half2 dd = __hsub2(r2, thr2);
-        unsigned bits;
-        memcpy(&bits, &dd, sizeof bits);
-        S.q[qn][lane] = (unsigned char)s;
-        qn += (bits >> 15) & 1u;
-        S.q[qn][lane] = (unsigned char)(s + 1);
-        qn += bits >> 31;
+    if (!act || hi < lo) hi = lo;
+    ncand += hi - lo;
+    const int m0e = lo & ~1;
+    const int np = (__reduce_max_sync(FULL, hi > lo ? hi - m0e : 0) + 1) >> 1;
+    const int m0 = min(m0e, ((se + 1) & ~1) - 2 * np);
+    const __half2 *hx2 = reinterpret_cast<const __half2 *>(S.hx + m0);
+    const __half2 *hy2 = reinterpret_cast<const __half2 *>(S.hy + m0);
+    const __half2 *hz2 = reinterpret_cast<const __half2 *>(S.hz + m0);
+    for (int w0 = 0; w0 < np; w0 += 16) {
+      if (__any_sync(FULL, nw == kRowWords))
+        row_flush<RECORD, PRECISE>(S, qn, nw, nre, lane, ki, pi, Xi, Ri, ixlo, g, pos, pp, pf, acc, accp, q,
+                                   pair_buf, pair_count, pair_cap, rlist, rcount, err);
+      const int pend = min(16, np - w0);
+      unsigned msk = 0;
+      for (int k0 = 0; k0 < pend; k0 += 4) {
+        unsigned m4 = 0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          const int p = w0 + k0 + k;
+          const __half2 dx = __hsub2(hx2[p], xi2), dy = __hsub2(hy2[p], yi2), dz = __hsub2(hz2[p], zi2);
+          const __half2 r2 = __hfma2(dx, dx, __hfma2(dy, dy, __hmul2(dz, dz)));
+          // 0xffff in each half whose r2 is below the threshold (false for NaN)
+          m4 |= __hlt2_mask(r2, thr2) & (0x00010001u << k);
+        }
+        msk |= m4 << k0;
+      }
+      const int base = m0 + 2 * w0;
+      msk = row_shuffle(msk) & row_range_bits(lo - base, hi - base);
+      if (msk) {
+        S.mq[nw][lane] = msk;
+        S.mb[nw][lane] = (unsigned char)base;
+        nw++;
+        qn += __popc(msk);
       }
     }
   };
@@ -396,8 +444,8 @@ __device__ __forceinline__ void row_chunk(const int4 cd, const Row *__restrict__
     if (fill > 0 && fill + __shfl_sync(FULL, rcnt, r) > kRowStage) {
       // the row does not fit behind the rows staged so far: their queued pairs
       // first (flushes cover as many rows as the stage holds)
-      row_flush<RECORD, PRECISE>(S, qn, nre, lane, ki, pi, Xi, Ri, ixlo, g, pos, pp, pf, acc, accp, q, pair_buf,
-                                 pair_count, pair_cap, rlist, rcount, err);
+      row_flush<RECORD, PRECISE>(S, qn, nw, nre, lane, ki, pi, Xi, Ri, ixlo, g, pos, pp, pf, acc, accp, q,
+                                 pair_buf, pair_count, pair_cap, rlist, rcount, err);
       fill = 0;
     }
     const int cbase = __float_as_int(s0.w), dxlo = __float_as_int(s1.w);
@@ -416,8 +464,8 @@ __device__ __forceinline__ void row_chunk(const int4 cd, const Row *__restrict__
         if (fill == kRowStage) {
           // the stage is full: test what this row has in it, then start over
           test_range(sb, fill);
-          row_flush<RECORD, PRECISE>(S, qn, nre, lane, ki, pi, Xi, Ri, ixlo, g, pos, pp, pf, acc, accp, q, pair_buf, pair_count,
-                            pair_cap, rlist, rcount, err);
+          row_flush<RECORD, PRECISE>(S, qn, nw, nre, lane, ki, pi, Xi, Ri, ixlo, g, pos, pp, pf, acc, accp, q,
+                                     pair_buf, pair_count, pair_cap, rlist, rcount, err);
           fill = 0;
           sb = 0;
         }
@@ -457,28 +505,22 @@ __device__ __forceinline__ void row_chunk(const int4 cd, const Row *__restrict__
       jx += len;
       if (jx == l1) jx = 0;
     }
-    if (fill & 1) {
-      // an odd end: the slot after it closes the last pair with a sentinel
-      if (lane == 0) {
-        S.hx[fill] = __float2half_rn(kHalfSentinel);
-        S.hy[fill] = __float2half_rn(kHalfSentinel);
-        S.hz[fill] = __float2half_rn(kHalfSentinel);
-      }
-    }
     test_range(sb, fill);
-    fill += fill & 1;
   }
-  row_flush<RECORD, PRECISE>(S, qn, nre, lane, ki, pi, Xi, Ri, ixlo, g, pos, pp, pf, acc, accp, q, pair_buf,
+  row_flush<RECORD, PRECISE>(S, qn, nw, nre, lane, ki, pi, Xi, Ri, ixlo, g, pos, pp, pf, acc, accp, q, pair_buf,
                              pair_count, pair_cap, rlist, rcount, err);
 }
 
-// F (Cartesian) of a lane's particle from its frame force: F = Q F_frame.
-__device__ __forceinline__ void row_store_force(float *F, const Geo *g, const float4 &pi, const Acc &acc) {
+// F (Cartesian) of a lane's particle from its frame force: F = Q (fs F_frame),
+// fs = 24 eps for the unscaled sums of fast mode, 1 in precise mode.
+__device__ __forceinline__ void row_store_force(float *F, const Geo *g, const float4 &pi, const Acc &acc,
+                                                float fs) {
   const float *Qm = g->Qf;
   const int oi = __float_as_int(pi.w);
-  F[3 * (size_t)oi] = Qm[0] * acc.fx + Qm[1] * acc.fy + Qm[2] * acc.fz;
-  F[3 * (size_t)oi + 1] = Qm[3] * acc.fx + Qm[4] * acc.fy + Qm[5] * acc.fz;
-  F[3 * (size_t)oi + 2] = Qm[6] * acc.fx + Qm[7] * acc.fy + Qm[8] * acc.fz;
+  const float fx = fs * acc.fx, fy = fs * acc.fy, fz = fs * acc.fz;
+  F[3 * (size_t)oi] = Qm[0] * fx + Qm[1] * fy + Qm[2] * fz;
+  F[3 * (size_t)oi + 1] = Qm[3] * fx + Qm[4] * fy + Qm[5] * fz;
+  F[3 * (size_t)oi + 2] = Qm[6] * fx + Qm[7] * fy + Qm[8] * fz;
 }
 
 template <bool RECORD, bool PRECISE>
@@ -509,9 +551,12 @@ __global__ void __launch_bounds__(kRowThreads, kRowMinBlocks) k_force_row(
     row_chunk<RECORD, PRECISE>(cd, rows + (size_t)cd.z * maxrows, rowcnt[cd.z], 0, g, pos, posr, cell_sorted,
                                start, stage[warp], pp, pf, q, acc, accp, ncand, nre, act, pi, ki, pair_buf,
                                pair_count, pair_cap, rlist, rcount, err);
-    if (act && F) row_store_force(F, g, pi, acc);
+    if (act && F) row_store_force(F, g, pi, acc, PRECISE ? 1.0f : pp.eps24);
   }
-  double v[kPartials] = {acc.u, acc.wxx, acc.wyy, acc.wzz, acc.wxy, acc.wxz, acc.wyz,
+  // fast mode: U = 4 eps sum s6 (s6 - 1) - (pairs) shift, W = 24 eps sum fr d d
+  const double e4 = pp.eps4d, e24 = pp.eps24d;
+  double v[kPartials] = {e4 * acc.u - pp.ushiftd * (double)acc.npair,
+                         e24 * acc.wxx, e24 * acc.wyy, e24 * acc.wzz, e24 * acc.wxy, e24 * acc.wxz, e24 * acc.wyz,
                          (double)acc.npair, (double)ncand, (double)nre};
   if (PRECISE) {
     const ff *w[7] = {&accp.u, &accp.wxx, &accp.wyy, &accp.wzz, &accp.wxy, &accp.wxz, &accp.wyz};
@@ -596,9 +641,12 @@ __global__ void __launch_bounds__(kRowThreads, kRowMinBlocks) k_b_force_row(Batc
                             v.cell_sorted, v.start, stage[warp], pp, pf, v.q, acc, accp, ncand, nre, act, pi, ki,
                             nullptr, nullptr, 0, v.recheck, v.nrecheck, &g->error);
     if (act) {
-      if (v.F) row_store_force(v.F, g, pi, acc);
-      v.ppart[2 * (size_t)ki] = make_float4(acc.u, acc.wxx, acc.wyy, acc.wzz);
-      v.ppart[2 * (size_t)ki + 1] = make_float4(acc.wxy, acc.wxz, acc.wyz, __int_as_float(acc.npair));
+      if (v.F) row_store_force(v.F, g, pi, acc, pp.eps24);
+      // the particle's own sums with the potential's constant factors applied
+      const float u = fmaf(pp.eps4, acc.u, -pp.ushift * (float)acc.npair);
+      v.ppart[2 * (size_t)ki] = make_float4(u, pp.eps24 * acc.wxx, pp.eps24 * acc.wyy, pp.eps24 * acc.wzz);
+      v.ppart[2 * (size_t)ki + 1] =
+          make_float4(pp.eps24 * acc.wxy, pp.eps24 * acc.wxz, pp.eps24 * acc.wyz, __int_as_float(acc.npair));
     }
     const unsigned c = __reduce_add_sync(FULL, (unsigned)ncand), r = __reduce_add_sync(FULL, (unsigned)nre);
     if (lane == 0) {
