@@ -274,6 +274,7 @@ int nemd_batch_finalize(nemd_batch *b) {
       L.centered = y.remap;
       GridIn &G = gin[(size_t)s * (K + 1) + k];
       G.rc = y.rc;
+      G.n = (int)y.n;
       G.kfac = nemd::kBatchMaxFactor;
       G.max_cells = 0x7fffffff;
       G.row_stride = 1 << 20;
@@ -342,6 +343,7 @@ int nemd_batch_finalize(nemd_batch *b) {
     lat[s].validate = 0;
     lat[s].centered = y.remap;
     gin[s].rc = y.rc;
+    gin[s].n = (int)y.n;
     gin[s].variant = y.variant;
     gin[s].kfac = b->kfac;
     gin[s].max_cells = si[s].ccap;
@@ -354,6 +356,7 @@ int nemd_batch_finalize(nemd_batch *b) {
   v.ncells = (int)ncells;
   v.nclasses = (int)nclasses;
   v.gs = b->gs;
+  v.wide = b->force_kernel == 4;
   const int64_t np = ntot > 0 ? ntot : 1;
   const int64_t cell_tiles = ncells / nemd::kFixedScanTile + 2, cls_tiles = nclasses / nemd::kFixedScanTile + 2;
   // clang-format off
@@ -467,6 +470,7 @@ int nemd_batch_compute(nemd_batch *b, float *F, double *UW) {
   v.F = Fd;
   v.UW = UWd;
   v.gs = b->gs;
+  v.wide = b->force_kernel == 4;
   if (b->use_graph) {
     const bool same = b->exec && b->key[0] == (const void *)v.q && b->key[1] == (const void *)Fd &&
                       b->key[2] == (const void *)UWd && b->key_cfg[0] == b->kfac && b->key_cfg[1] == b->gs &&

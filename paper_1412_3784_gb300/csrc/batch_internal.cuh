@@ -34,6 +34,7 @@ struct SysInfo {
 struct BatchView {
   int nsys, ntot, ncells, nclasses;  // systems; totals of particles, cell and class slots
   int gs;                            // particles per chunk (16 or 32)
+  int wide;                          // chunks span up to Geo::span cells (row kernel), else kMaxSpan
   Geo *geo;
   const SysInfo *sys;
   const Pot *pot;

@@ -367,7 +367,7 @@ cudaError_t launch_forces(nemd_ctx *c, float *F_dev, double *UW_dev) {
     if (e != cudaSuccess) return e;
   }
   if (grouped || warped || rowk) {
-    cudaError_t e = launch_chunk_build(c, (warped || rowk) ? 32 : c->group);
+    cudaError_t e = launch_chunk_build(c, (warped || rowk) ? 32 : c->group, rowk);
     if (e != cudaSuccess) return e;
   }
   const bool timed = c->timing && c->ev && c->ev_n < c->ev_cap;

@@ -29,16 +29,17 @@ constexpr int kQueue = 64;  // queue entries per lane
 constexpr int kChunkThreads = 128;
 
 // Walk one x-row of cells (cells c0 .. c0 + l1 - 1) in order, cutting its
-// particles into chunks of at most gs particles spanning at most kMaxSpan
-// cells; emit(first, count, ixlo, ixhi) for each chunk, in order.
+// particles into chunks of at most gs particles spanning at most span cells
+// (Geo::span); emit(first, count, ixlo, ixhi) for each chunk, in order.
 template <class Emit>
-__device__ __forceinline__ void chunk_walk(const int *__restrict__ start, int c0, int l1, int gs, Emit &&emit) {
+__device__ __forceinline__ void chunk_walk(const int *__restrict__ start, int c0, int l1, int gs, int span,
+                                           Emit &&emit) {
   int first = 0, count = 0, ixlo = 0, ixhi = 0;
   for (int ix = 0; ix < l1; ix++) {
     const int b = start[c0 + ix], nc = start[c0 + ix + 1] - b;
     int off = 0;
     while (off < nc) {
-      if (count > 0 && ix - ixlo >= kMaxSpan) {
+      if (count > 0 && ix - ixlo >= span) {
         emit(first, count, ixlo, ixhi);
         count = 0;
       }
@@ -69,8 +70,8 @@ constexpr int kWalkCells = 512;  // row lengths staged in shared memory (longer 
 constexpr int kWalkWarps = 4;
 
 template <class Emit>
-__device__ __forceinline__ void chunk_walk_warp(const int *__restrict__ start, int c0, int l1, int gs, int *sm,
-                                                int lane, Emit &&emit) {
+__device__ __forceinline__ void chunk_walk_warp(const int *__restrict__ start, int c0, int l1, int gs, int span,
+                                                int *sm, int lane, Emit &&emit) {
   const bool staged = l1 < kWalkCells;
   __syncwarp();
   if (staged)
@@ -78,15 +79,15 @@ __device__ __forceinline__ void chunk_walk_warp(const int *__restrict__ start, i
   __syncwarp();
   if (lane == 0) {
     if (staged)
-      chunk_walk(sm, 0, l1, gs, emit);
+      chunk_walk(sm, 0, l1, gs, span, emit);
     else
-      chunk_walk(start, c0, l1, gs, emit);
+      chunk_walk(start, c0, l1, gs, span, emit);
   }
 }
 
 __global__ void __launch_bounds__(32 * kWalkWarps) k_chunk_count(const Geo *__restrict__ g,
                                                                  const int *__restrict__ start,
-                                                                 int *__restrict__ cnt, int gs) {
+                                                                 int *__restrict__ cnt, int gs, int wide) {
   __shared__ int sm[kWalkWarps][kWalkCells + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool ok = !(g->error & (ERRB_BOX | ERRB_CAPACITY));
@@ -94,7 +95,8 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_chunk_count(const Geo *__re
   const int nw = gridDim.x * kWalkWarps;
   for (int cls = blockIdx.x * kWalkWarps + warp; cls < ncls; cls += nw) {
     int n = 0;
-    chunk_walk_warp(start, cls * l1, l1, gs, sm[warp], lane, [&](int, int, int, int) { n++; });
+    chunk_walk_warp(start, cls * l1, l1, gs, wide ? g->span : kMaxSpan, sm[warp], lane,
+                    [&](int, int, int, int) { n++; });
     if (lane == 0) cnt[cls] = n;
   }
 }
@@ -102,7 +104,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_chunk_count(const Geo *__re
 __global__ void __launch_bounds__(32 * kWalkWarps) k_chunk_write(const Geo *__restrict__ g,
                                                                  const int *__restrict__ start,
                                                                  const int *__restrict__ off,
-                                                                 int4 *__restrict__ chunks, int gs) {
+                                                                 int4 *__restrict__ chunks, int gs, int wide) {
   __shared__ int sm[kWalkWarps][kWalkCells + 1];
   if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -110,7 +112,8 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_chunk_write(const Geo *__re
   const int nw = gridDim.x * kWalkWarps;
   for (int cls = blockIdx.x * kWalkWarps + warp; cls < ncls; cls += nw) {
     int k = off[cls];
-    chunk_walk_warp(start, cls * l1, l1, gs, sm[warp], lane, [&](int first, int count, int ixlo, int ixhi) {
+    chunk_walk_warp(start, cls * l1, l1, gs, wide ? g->span : kMaxSpan, sm[warp], lane,
+                    [&](int first, int count, int ixlo, int ixhi) {
       chunks[k++] = make_int4(first, count, cls, ixlo | (ixhi << 16));
     });
   }
@@ -273,15 +276,18 @@ __global__ void __launch_bounds__(kChunkThreads, 4) k_force_chunk(
   block_reduce_store<kChunkThreads>(v, partials);
 }
 
-cudaError_t launch_chunk_build(nemd_ctx *c, int gs) {
+// wide: chunks span up to Geo::span cells (the row kernel), else kMaxSpan (the
+// grouped and warp kernels, whose queue entries hold the cell offset in 5 bits).
+cudaError_t launch_chunk_build(nemd_ctx *c, int gs, bool wide) {
   const int cap = (int)c->cap_cells;
   int64_t blocks = (c->cap_cells + kWalkWarps - 1) / kWalkWarps;
   if (blocks > 16 * (int64_t)c->sms) blocks = 16 * (int64_t)c->sms;
   if (blocks < 1) blocks = 1;
-  k_chunk_count<<<(int)blocks, 32 * kWalkWarps, 0, c->stream>>>(c->geo, c->start, c->chunk_cnt, gs);
+  k_chunk_count<<<(int)blocks, 32 * kWalkWarps, 0, c->stream>>>(c->geo, c->start, c->chunk_cnt, gs, wide);
   cudaError_t e = launch_class_scan(c, c->chunk_cnt, c->chunk_off, cap);
   if (e != cudaSuccess) return e;
-  k_chunk_write<<<(int)blocks, 32 * kWalkWarps, 0, c->stream>>>(c->geo, c->start, c->chunk_off, c->chunks, gs);
+  k_chunk_write<<<(int)blocks, 32 * kWalkWarps, 0, c->stream>>>(c->geo, c->start, c->chunk_off, c->chunks, gs,
+                                                                 wide);
   c->launches += 2;
   return cudaGetLastError();
 }
@@ -362,7 +368,8 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_b_chunk_count(BatchView v) 
     const Geo *g;
     int c0, l1, n = 0;
     if (batch_class(v, slot, g, c0, l1))
-      chunk_walk_warp(v.start, c0, l1, v.gs, sm[warp], lane, [&](int, int, int, int) { n++; });
+      chunk_walk_warp(v.start, c0, l1, v.gs, v.wide ? g->span : kMaxSpan, sm[warp], lane,
+                      [&](int, int, int, int) { n++; });
     if (lane == 0) v.chunk_cnt[slot] = n;
   }
 }
@@ -376,7 +383,8 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_b_chunk_write(BatchView v) 
     int c0, l1;
     if (!batch_class(v, slot, g, c0, l1)) continue;
     int k = v.chunk_off[slot];
-    chunk_walk_warp(v.start, c0, l1, v.gs, sm[warp], lane, [&](int first, int count, int ixlo, int ixhi) {
+    chunk_walk_warp(v.start, c0, l1, v.gs, v.wide ? g->span : kMaxSpan, sm[warp], lane,
+                    [&](int first, int count, int ixlo, int ixhi) {
       v.chunks[k++] = make_int4(first, count, slot, ixlo | (ixhi << 16));
     });
   }

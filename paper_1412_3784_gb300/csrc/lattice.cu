@@ -313,6 +313,12 @@ __device__ void grid_body(Geo *g, const GridIn &in) {
   }
   g->ncells = err ? 0 : (int)ncells;
   g->maxrows = maxrows;
+  // chunks of up to 32 particles of one x-row span at most kMaxSpan cells, or
+  // more (up to kMaxSpanCap) where the cells hold on average fewer than 6
+  // particles, so that a chunk still fills most of a warp
+  int span = kMaxSpan;
+  if (ncells > 0 && in.n > 0) span = min(kMaxSpanCap, max(kMaxSpan, (int)ceil(48.0 * (double)ncells / in.n)));
+  g->span = span;
   for (int k = 0; k < 9; k++) {
     g->G[k] = Gd[k];
     g->Gf[k] = (float)Gd[k];
@@ -329,7 +335,7 @@ __device__ void grid_body(Geo *g, const GridIn &in) {
   // offsets reach (rmax + 2 + span) cells and the warp kernel's staged
   // positions (Sec. 3 union windows) up to (span + 2 rmax + 3) cells from a
   // chunk's first cell; positions half a cell, distances rc
-  const double M = (double)(3 * rmax + 6 + kMaxSpan) * gmax + 2.0 * rc;
+  const double M = (double)(3 * rmax + 6 + span) * gmax + 2.0 * rc;
   int e2;
   frexp(M, &e2);             // M < 2^e2
   const double q = ldexp(1.0, e2 - 23);
@@ -349,7 +355,7 @@ __device__ void grid_body(Geo *g, const GridIn &in) {
   // plus the rounding of r^2.  Fine band (test with residuals added back): one
   // rounding of each corrected component and of r^2.
   const double u = 5.9604644775390625e-08;  // 2^-24
-  const double E = (double)(rmax + 6 + kMaxSpan) * 0.5 * q;
+  const double E = (double)(rmax + 6 + span) * 0.5 * q;
   const double s3 = 1.7320508075688772;
   // Both bands also cover the wrap's float-float error: each position within
   // dw of its float64 value (wrap_tol, plus a rounding of the residual), so
@@ -510,6 +516,7 @@ cudaError_t launch_grid(nemd_ctx *c) {
   in.rc = c->rc;
   in.variant = c->variant_req;
   in.kfac = c->kfac;
+  in.n = (int)c->n;
   in.max_cells = (int)c->cap_cells;
   const int ka = c->kfac_alloc > c->kfac ? c->kfac_alloc : c->kfac;
   in.row_stride = (2 * ka + 1) * (2 * ka + 2);

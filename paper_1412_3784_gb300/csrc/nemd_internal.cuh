@@ -17,7 +17,8 @@ namespace nemd {
 // rounding of positions can never drop a pair.
 constexpr double kMargin = 1e-12;
 constexpr int kMaxFactor = 3;          // largest cell-size factor k
-constexpr int kMaxSpan = 8;            // largest x-span (cells) of a chunk of the grouped kernel
+constexpr int kMaxSpan = 8;            // x-span (cells) of a chunk of the grouped and row kernels ...
+constexpr int kMaxSpanCap = 32;        // ... widened up to this where cells hold few particles
 constexpr int kRecheckCap = 1 << 14;   // fine-band candidates per evaluation (~1e-7 of candidates)
 constexpr int kFixupBlocks = 16;       // blocks of the float64 fix-up pass (when partial slots allow)
 constexpr int kMaxRowsPerClass = 64;   // (2k+2)^2 for k = 3
@@ -48,6 +49,7 @@ struct Geo {
   int nc[3];
   int ncells;
   int maxrows;        // row stride per (iy, iz) class
+  int span;           // largest x-span (cells) of a chunk this step
   int reach[3];       // stencil reach in cells per axis
   double G[9];        // frame position of cell corner = G * (ix, iy, iz)
   double Ginv_scale[3];  // DS: c_i ; DO: 1 / w_i
@@ -94,6 +96,7 @@ struct LatIn {
 struct GridIn {
   double rc;
   int variant, kfac, max_cells, row_stride;
+  int n;  // particles of the system (0: unknown, Geo::span = kMaxSpan)
 };
 
 // One neighbour row of a home (iy, iz) class: the x-cells ix+dxlo ... ix+dxlo+cnt-1
@@ -294,7 +297,7 @@ int verlet_forces(nemd_ctx *c, float *F, int variant, double rc, double t);
 // blocks whose partials it wrote)
 bool chunk_kernel_applies(const nemd_ctx *c);
 bool warp_kernel_applies(const nemd_ctx *c);
-cudaError_t launch_chunk_build(nemd_ctx *c, int gs);
+cudaError_t launch_chunk_build(nemd_ctx *c, int gs, bool wide);
 cudaError_t launch_force_warp(nemd_ctx *c, float *F_dev, int *nblocks, bool half);
 // row kernel (per-lane kappa windows, half-precision coarse test)
 bool row_kernel_applies(const nemd_ctx *c);
