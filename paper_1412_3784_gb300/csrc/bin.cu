@@ -240,50 +240,66 @@ __device__ __forceinline__ bool sort_before(float ka, int ia, float kb, int ib) 
 
 // One thread per cell: the cell's slots sorted by (kappa, input index) --
 // keys in the slots of cell_sorted, indices in perm, both contiguous per cell.
-// A cell of up to 32 particles is sorted in registers by a bitonic network
-// (padded with keys that sort last); a longer one in place by insertion.
+// A cell of up to 32 particles is sorted in registers by a bitonic network of
+// the smallest power-of-two width that holds it (padded with keys that sort
+// last); a longer one in place by insertion.
 constexpr int kNet = 32;
+
+template <int K>
+__device__ __forceinline__ void cellsort_net(int *__restrict__ perm, int *__restrict__ key_slot, int b, int n) {
+  float key[K];
+  int idx[K];
+#pragma unroll
+  for (int t = 0; t < K; t++) {
+    key[t] = t < n ? __int_as_float(key_slot[b + t]) : INFINITY;
+    idx[t] = t < n ? perm[b + t] : 0x7fffffff;
+  }
+#pragma unroll
+  for (int k = 2; k <= K; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+      for (int i = 0; i < K; i++) {
+        const int l = i ^ j;
+        if (l > i) {
+          const bool up = (i & k) == 0;
+          const bool swap = up ? sort_before(key[l], idx[l], key[i], idx[i]) : sort_before(key[i], idx[i], key[l], idx[l]);
+          const float ka = key[i], kb = key[l];
+          const int ia = idx[i], ib = idx[l];
+          key[i] = swap ? kb : ka;
+          key[l] = swap ? ka : kb;
+          idx[i] = swap ? ib : ia;
+          idx[l] = swap ? ia : ib;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < K; t++)
+    if (t < n) {
+      key_slot[b + t] = __float_as_int(key[t]);
+      perm[b + t] = idx[t];
+    }
+}
 
 __device__ __forceinline__ void cellsort_body(const int *__restrict__ start, int *__restrict__ perm,
                                               int *__restrict__ key_slot, int c) {
   const int b = start[c], e = start[c + 1], n = e - b;
   if (n <= 1) return;
-  if (n <= kNet) {
-    float key[kNet];
-    int idx[kNet];
-#pragma unroll
-    for (int t = 0; t < kNet; t++) {
-      key[t] = t < n ? __int_as_float(key_slot[b + t]) : INFINITY;
-      idx[t] = t < n ? perm[b + t] : 0x7fffffff;
+  if (n == 2) {
+    const int k0 = key_slot[b], k1 = key_slot[b + 1], i0 = perm[b], i1 = perm[b + 1];
+    if (sort_before(__int_as_float(k1), i1, __int_as_float(k0), i0)) {
+      key_slot[b] = k1;
+      key_slot[b + 1] = k0;
+      perm[b] = i1;
+      perm[b + 1] = i0;
     }
-#pragma unroll
-    for (int k = 2; k <= kNet; k <<= 1) {
-#pragma unroll
-      for (int j = k >> 1; j > 0; j >>= 1) {
-#pragma unroll
-        for (int i = 0; i < kNet; i++) {
-          const int l = i ^ j;
-          if (l > i) {
-            const bool up = (i & k) == 0;
-            const bool swap = up ? sort_before(key[l], idx[l], key[i], idx[i]) : sort_before(key[i], idx[i], key[l], idx[l]);
-            const float ka = key[i], kb = key[l];
-            const int ia = idx[i], ib = idx[l];
-            key[i] = swap ? kb : ka;
-            key[l] = swap ? ka : kb;
-            idx[i] = swap ? ib : ia;
-            idx[l] = swap ? ia : ib;
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int t = 0; t < kNet; t++)
-      if (t < n) {
-        key_slot[b + t] = __float_as_int(key[t]);
-        perm[b + t] = idx[t];
-      }
     return;
   }
+  if (n <= 4) return cellsort_net<4>(perm, key_slot, b, n);
+  if (n <= 8) return cellsort_net<8>(perm, key_slot, b, n);
+  if (n <= 16) return cellsort_net<16>(perm, key_slot, b, n);
+  if (n <= kNet) return cellsort_net<kNet>(perm, key_slot, b, n);
   for (int k = b + 1; k < e; k++) {
     const int kbits = key_slot[k];
     const float kv = __int_as_float(kbits);

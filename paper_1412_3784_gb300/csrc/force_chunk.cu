@@ -360,44 +360,41 @@ __device__ __forceinline__ bool batch_class(const BatchView &v, int slot, const 
   return true;
 }
 
-__global__ void __launch_bounds__(32 * kWalkWarps) k_b_chunk_count(BatchView v) {
-  __shared__ int sm[kWalkWarps][kWalkCells + 1];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nw = gridDim.x * kWalkWarps;
-  for (int slot = blockIdx.x * kWalkWarps + warp; slot < v.nclasses; slot += nw) {
+// One thread per class slot: the rows of batched systems are short (a few
+// dozen cells) and there are many of them, so each thread walks its own row
+// in global memory.
+constexpr int kBatchWalkThreads = 128;
+
+__global__ void __launch_bounds__(kBatchWalkThreads) k_b_chunk_count(BatchView v) {
+  for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < v.nclasses; slot += gridDim.x * blockDim.x) {
     const Geo *g;
     int c0, l1, n = 0;
     if (batch_class(v, slot, g, c0, l1))
-      chunk_walk_warp(v.start, c0, l1, v.gs, v.wide ? g->span : kMaxSpan, sm[warp], lane,
-                      [&](int, int, int, int) { n++; });
-    if (lane == 0) v.chunk_cnt[slot] = n;
+      chunk_walk(v.start, c0, l1, v.gs, v.wide ? g->span : kMaxSpan, [&](int, int, int, int) { n++; });
+    v.chunk_cnt[slot] = n;
   }
 }
 
-__global__ void __launch_bounds__(32 * kWalkWarps) k_b_chunk_write(BatchView v) {
-  __shared__ int sm[kWalkWarps][kWalkCells + 1];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nw = gridDim.x * kWalkWarps;
-  for (int slot = blockIdx.x * kWalkWarps + warp; slot < v.nclasses; slot += nw) {
+__global__ void __launch_bounds__(kBatchWalkThreads) k_b_chunk_write(BatchView v) {
+  for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < v.nclasses; slot += gridDim.x * blockDim.x) {
     const Geo *g;
     int c0, l1;
     if (!batch_class(v, slot, g, c0, l1)) continue;
     int k = v.chunk_off[slot];
-    chunk_walk_warp(v.start, c0, l1, v.gs, v.wide ? g->span : kMaxSpan, sm[warp], lane,
-                    [&](int first, int count, int ixlo, int ixhi) {
+    chunk_walk(v.start, c0, l1, v.gs, v.wide ? g->span : kMaxSpan, [&](int first, int count, int ixlo, int ixhi) {
       v.chunks[k++] = make_int4(first, count, slot, ixlo | (ixhi << 16));
     });
   }
 }
 
 cudaError_t launch_batch_chunks(cudaStream_t st, const BatchView &v, int sms) {
-  int blocks = (v.nclasses + kWalkWarps - 1) / kWalkWarps;
+  int blocks = (v.nclasses + kBatchWalkThreads - 1) / kBatchWalkThreads;
   if (blocks > 16 * sms) blocks = 16 * sms;
   if (blocks < 1) blocks = 1;
-  k_b_chunk_count<<<blocks, 32 * kWalkWarps, 0, st>>>(v);
+  k_b_chunk_count<<<blocks, kBatchWalkThreads, 0, st>>>(v);
   cudaError_t e = launch_fixed_scan(st, v.chunk_cnt, v.chunk_off, v.chunk_tiles, v.nclasses);
   if (e != cudaSuccess) return e;
-  k_b_chunk_write<<<blocks, 32 * kWalkWarps, 0, st>>>(v);
+  k_b_chunk_write<<<blocks, kBatchWalkThreads, 0, st>>>(v);
   return cudaGetLastError();
 }
 

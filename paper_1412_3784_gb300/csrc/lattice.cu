@@ -426,11 +426,12 @@ __device__ int stencil_class_warp(Geo *g, int cls, int cell_base, Row *out, int 
       out[e] = r;
     }
   } else {
-    // window bounds by reciprocals of the cell sides: a bound that moves by a
-    // rounding only adds or drops a cell lying at distance rc (1 + 1e-12) or
-    // more, which holds no partner
+    // window bounds by reciprocals of the cell sides (those of the grid, the
+    // same rounded quotients): a bound that moves by a rounding only adds or
+    // drops a cell lying at distance rc (1 + 1e-12) or more, which holds no
+    // partner
     const double w1 = g->w[0], w2 = g->w[1], w3 = g->w[2];
-    const double iw1 = 1.0 / w1, iw2 = 1.0 / w2, iw3 = 1.0 / w3;
+    const double iw1 = g->Ginv_scale[0], iw2 = g->Ginv_scale[1], iw3 = g->Ginv_scale[2];
     const double r12 = g->R[1], r13 = g->R[2], r23 = g->R[5];
     const int zlo = (int)floor(((double)iz * w3 - rce) * iw3);
     int zhi = (int)ceil(((double)(iz + 1) * w3 + rce) * iw3) - 1;
@@ -438,20 +439,28 @@ __device__ int stencil_class_warp(Geo *g, int cls, int cell_base, Row *out, int 
       if (lane == 0) atomicOr(&g->error, ERRB_CAPACITY);
       zhi = zlo + kMaxZ - 1;
     }
-    int ylo[kMaxZ], ycnt[kMaxZ];
-    nr = 0;
-    for (int jzu = zlo; jzu <= zhi; jzu++) {
+    // lane z: the y-window of z-row zlo + z; rows numbered z-row by z-row
+    const int nz = zhi - zlo + 1;
+    int ycnt_l = 0, ylo_l = 0;
+    if (lane < nz) {
+      const int jzu = zlo + lane;
       const int kz = floordiv_i(jzu, l3);
       const double yshift = (double)kz * r23;
-      const int lo = (int)floor(((double)iy * w2 - rce - yshift) * iw2);
+      ylo_l = (int)floor(((double)iy * w2 - rce - yshift) * iw2);
       const int hi = (int)ceil(((double)(iy + 1) * w2 + rce - yshift) * iw2) - 1;
-      ylo[jzu - zlo] = lo;
-      ycnt[jzu - zlo] = hi - lo + 1;
-      nr += hi - lo + 1;
+      ycnt_l = hi - ylo_l + 1;
+    }
+    int ylo[kMaxZ], ycnt[kMaxZ];
+    nr = 0;
+#pragma unroll
+    for (int z = 0; z < kMaxZ; z++) {
+      ylo[z] = __shfl_sync(0xffffffffu, ylo_l, z);
+      ycnt[z] = z < nz ? __shfl_sync(0xffffffffu, ycnt_l, z) : 0;
+      nr += ycnt[z];
     }
     for (int e = lane; e < nr && e < maxrows; e += 32) {
       int z = 0, base = 0;
-      while (e >= base + ycnt[z]) base += ycnt[z++];
+      while (z < kMaxZ - 1 && e >= base + ycnt[z]) base += ycnt[z++];
       const int jzu = zlo + z, jyu = ylo[z] + (e - base);
       const int kz = floordiv_i(jzu, l3), jz = jzu - kz * l3;
       const int ky = floordiv_i(jyu, l2), jy = jyu - ky * l2;
@@ -545,9 +554,11 @@ __global__ void k_b_lattice(Geo *geo, const LatIn *__restrict__ lat, const doubl
   lattice_body(geo + blockIdx.x, in);
 }
 
+// One system per block (its first thread): the float64 work of the systems
+// is spread over the SMs.
 __global__ void k_b_grid(Geo *geo, const GridIn *__restrict__ grid, const SysInfo *__restrict__ sys, int count) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= count) return;
+  const int e = blockIdx.x;
+  if (e >= count || threadIdx.x != 0) return;
   Geo *g = geo + e;
   grid_body(g, grid[e]);
   // the batch sizes a system's row classes from its states over one period
@@ -581,7 +592,7 @@ cudaError_t launch_batch_lattice(cudaStream_t st, Geo *geo, const LatIn *lat, co
 
 cudaError_t launch_batch_grid(cudaStream_t st, Geo *geo, const GridIn *grid, const SysInfo *sys, int count) {
   if (count <= 0) return cudaSuccess;
-  k_b_grid<<<(count + 63) / 64, 64, 0, st>>>(geo, grid, sys, count);
+  k_b_grid<<<count, 32, 0, st>>>(geo, grid, sys, count);
   return cudaGetLastError();
 }
 
