@@ -59,14 +59,21 @@ __device__ __forceinline__ void set_shift(Row &r, double ox, double oy, double o
 
 }  // namespace
 
-// One warp (the whole block).  validate != 0: compute exp(tau_in A) L0 only
-// (for the KR check).
-__device__ __forceinline__ void lattice_body(Geo *g, const LatIn &in) {
+// Shared scratch of one warp's lattice.
+struct LatScratch {
+  double B[9], P[9], E[9], Ls[9], Gm[9], Rm[9], Ri[9], Lt[9], cof[9];
+  double det;
+  int s;
+};
+
+// One warp (sc its shared scratch).  validate != 0: compute exp(tau_in A) L0
+// only (for the KR check).
+__device__ __forceinline__ void lattice_body(Geo *g, const LatIn &in, LatScratch &sc) {
   const int validate = in.validate;
   const double tau_in = in.tau;
-  __shared__ double B[9], P[9], E[9], Ls[9], Gm[9], Rm[9], Ri[9], Lt[9];
-  __shared__ int sh_s;
-  const int lane = threadIdx.x;
+  double *B = sc.B, *P = sc.P, *E = sc.E, *Ls = sc.Ls, *Gm = sc.Gm, *Rm = sc.Rm, *Ri = sc.Ri, *Lt = sc.Lt;
+  int &sh_s = sc.s;
+  const int lane = threadIdx.x & 31;
 
   double tau;
   if (validate) {
@@ -138,8 +145,8 @@ __device__ __forceinline__ void lattice_body(Geo *g, const LatIn &in) {
   }
 
   // inverse by the adjugate
-  __shared__ double cof[9];
-  __shared__ double det_s;
+  double *cof = sc.cof;
+  double &det_s = sc.det;
   if (lane < 9) {
     const double *a = Ls;
     double c;
@@ -209,7 +216,10 @@ __device__ __forceinline__ void lattice_body(Geo *g, const LatIn &in) {
   __syncwarp();
 }
 
-__global__ void k_lattice(Geo *g, LatIn in) { lattice_body(g, in); }
+__global__ void k_lattice(Geo *g, LatIn in) {
+  __shared__ LatScratch sc;
+  lattice_body(g, in, sc);
+}
 
 // Single thread: cell counts of both variants at k = 1, their neighbourhood
 // volumes (Sec. 5.1: V_DS = 27 V / (c1 c2 c3); Sec. 5.2: V_DO = avg r11 r22 r33 /
@@ -548,17 +558,19 @@ cudaError_t launch_stencil(nemd_ctx *c) {
 
 // ---- batches: one launch over every system (or every sampled state) ----
 
+// One system per block (one warp).
 __global__ void k_b_lattice(Geo *geo, const LatIn *__restrict__ lat, const double *__restrict__ t) {
+  __shared__ LatScratch sc;
   LatIn in = lat[blockIdx.x];
   if (t) in.t = t[blockIdx.x];
-  lattice_body(geo + blockIdx.x, in);
+  lattice_body(geo + blockIdx.x, in, sc);
 }
 
-// One system per block (its first thread): the float64 work of the systems
-// is spread over the SMs.
+// One thread per system, 128 per block: the grid is long straight-line
+// float64 code run once, so few SMs (each fetching it once) do it fastest.
 __global__ void k_b_grid(Geo *geo, const GridIn *__restrict__ grid, const SysInfo *__restrict__ sys, int count) {
-  const int e = blockIdx.x;
-  if (e >= count || threadIdx.x != 0) return;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= count) return;
   Geo *g = geo + e;
   grid_body(g, grid[e]);
   // the batch sizes a system's row classes from its states over one period
@@ -592,7 +604,7 @@ cudaError_t launch_batch_lattice(cudaStream_t st, Geo *geo, const LatIn *lat, co
 
 cudaError_t launch_batch_grid(cudaStream_t st, Geo *geo, const GridIn *grid, const SysInfo *sys, int count) {
   if (count <= 0) return cudaSuccess;
-  k_b_grid<<<count, 32, 0, st>>>(geo, grid, sys, count);
+  k_b_grid<<<(count + 127) / 128, 128, 0, st>>>(geo, grid, sys, count);
   return cudaGetLastError();
 }
 
