@@ -60,21 +60,23 @@ WORKLOADS = {
 C_TEST = 7     # FP32 instructions per candidate test: 3 FADD, 1 FMUL, 2 FFMA, 1 FSETP
 C_PAIR = 24    # FP32 instructions per interacting pair (force, energy, virial, both sides)
 
-# DRAM bytes (read + write) of one k_force_warp launch on the N = 2^20 system,
-# from one ncu capture of that launch (dram__bytes_read.sum + dram__bytes_write.sum); valid
+# DRAM bytes (read + write) of one k_force_row launch on the N = 2^20 general-flow
+# system at t = T/2, from one ncu capture of that launch (dram__bytes_read.sum +
+# dram__bytes_write.sum; bench.py --sections kernel, third of three back-to-back
+# launches, so that no earlier kernel's output is written back during it); valid
 # only while the kernel's sources are the ones captured (sha1 prefixes).
-WARP_TRAFFIC = {"bytes": 39.401472e6 + 0.320768e6,
-                "sha1": {"paper_1412_3784_gb300/csrc/force_warp.cu": "0f4e047dcf2b",
-                         "paper_1412_3784_gb300/csrc/force_common.cuh": "2c912e007080"}}
+ROW_TRAFFIC = {"bytes": 40.331776e6 + 1.501696e6,
+               "sha1": {"paper_1412_3784_gb300/csrc/force_row.cu": "044c831deaa3",
+                        "paper_1412_3784_gb300/csrc/force_common.cuh": "7add2c4a0360"}}
 
 
-def warp_traffic():
+def row_traffic():
     import hashlib
-    for rel, prefix in WARP_TRAFFIC["sha1"].items():
+    for rel, prefix in ROW_TRAFFIC["sha1"].items():
         with open(os.path.join(ROOT, rel), "rb") as f:
             if not hashlib.sha1(f.read()).hexdigest().startswith(prefix):
                 return None
-    return WARP_TRAFFIC["bytes"]
+    return ROW_TRAFFIC["bytes"]
 
 
 def parse():
@@ -94,7 +96,9 @@ def parse():
     p.add_argument("--group", type=int, default=16, help="lanes per group of the grouped kernel")
     p.add_argument("--kfac", type=int, default=1, help="cell-size factor without autotuning")
     p.add_argument("--sections", default="main,batched,learned,shear,equilibrium,integrate",
-                   help="comma list of main, batched, learned, shear, equilibrium")
+                   help="comma list of main, batched, learned, shear, equilibrium, integrate; or "
+                        "'kernel' alone: one strain's forces evaluated three times back to back "
+                        "(the force kernel of the default options, for a counter capture)")
     p.add_argument("--batch-steps", type=int, default=10)
     p.add_argument("--learned-strains", type=int, default=64,
                    help="strains of the N = 2^21 system in the learned section (256 = one per period step)")
@@ -297,22 +301,55 @@ def cpu_baseline_sample(ser, k, ts, reps=3):
             "host": {"nproc": nproc, "model": model}}
 
 
-def timed_loop(torch, dev, world, fn, steps, warmup):
+def timed_loop(torch, dev, world, fn, steps, warmup, nvtx=None):
     """CUDA-event time (ms) of `steps` calls of fn after `warmup` untimed ones,
-    bracketed by a barrier and a device synchronise on both sides."""
+    bracketed by a barrier and a device synchronise on both sides (inside an
+    NVTX range named nvtx, when given, for profilers)."""
     for _ in range(warmup):
         fn()
     barrier(world)
     torch.cuda.synchronize(dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    if nvtx:
+        torch.cuda.nvtx.range_push(nvtx)
     e0.record()
     for _ in range(steps):
         fn()
     e1.record()
+    if nvtx:
+        torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize(dev)
     barrier(world)
     return e0.elapsed_time(e1)
+
+
+def section_kernel(args, dev, torch, nemd, W):
+    """The workload's strain at t = T/2: cell list once, then the forces three
+    times back to back with the default kernel options (no autotuning), so that
+    a counter capture of the third force launch sees only that kernel's own
+    memory traffic (no binning output waiting in L2).  Prints one JSON line."""
+    k, _ = WORKLOADS[args.workload]
+    ser = series_for(W, k)
+    t = 0.5 * ser.period
+    q = torch.from_numpy(ser.positions(t)).to(dev)
+    F = torch.empty((ser.n, 3), dtype=torch.float32, device=dev)
+    U = torch.zeros(1, dtype=torch.float64, device=dev)
+    Wv = torch.zeros(9, dtype=torch.float64, device=dev)
+    ctx = nemd.Context(dev.index)
+    ctx.set_flow(ser.A, ser.L0, ser.M, ser.period)
+    ctx.set_potential(nemd.NEMD_LJ, 1.0, 1.0, 1)
+    ctx.set_option(nemd.NEMD_OPT_KERNEL, args.kernel)
+    ctx.set_option(nemd.NEMD_OPT_CELL_FACTOR, args.kfac)
+    ctx.set_state(q, t)
+    ctx.build_cells(nemd.NEMD_AUTO_HEURISTIC, ser.rc)
+    for _ in range(3):
+        ctx.compute_forces(F, U, Wv)
+    ctx.sync()
+    st = ctx.stats()
+    print(json.dumps({"section": "kernel", "workload": args.workload, "t": t, "kernel": args.kernel,
+                      "pairs": st["pairs"], "candidates": st["candidates"], "variant": st["variant"]}))
+    ctx.close()
 
 
 def section_main(args, rank, world, dev, torch, nemd, W):
@@ -442,7 +479,7 @@ def section_main(args, rank, world, dev, torch, nemd, W):
                 "unit": "T FP32 lane-instructions/s",
                 "peak_measured": peak_measured,
                 "peak_measured_basis": "the library's FFMA loop (nemd_measure_peaks), T lane-ops/s",
-                "frac": achieved / peak, "traffic": warp_traffic() if tuned_kernel == 2 else None,
+                "frac": achieved / peak, "traffic": row_traffic() if tuned_kernel == 4 else None,
                 "kernel": kernel_name.get(tuned_kernel, "?"), "ops_per_launch": ops_per_launch,
                 "avg_launch_ms": avg_launch_s * 1e3,
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x {peak_mhz:.0f} MHz (FP32 instruction "
@@ -588,21 +625,27 @@ def section_batched(args, world, dev, torch, nemd, W):
     F = torch.zeros((b.ntot, 3), dtype=torch.float32, device=dev)
     UW = torch.zeros((b.nsys, 10), dtype=torch.float64, device=dev)
     b.set_state(q, ts)
-    times = b.autotune(reps=3)
+    if args.no_autotune:  # the default options: cell factor 1, 32-particle chunks
+        times = [({"cell_factor": 1, "tile": 32}, float("nan"))]
+    else:
+        times = b.autotune(reps=3)
     b.compute(F, UW)
     b.sync()
     st, launches = b.stats()
     pairs = sum(x["pairs"] for x in st)
-    ms = timed_loop(torch, dev, world, lambda: b.compute(F, UW), args.batch_steps, 3) / args.batch_steps
+    ms = timed_loop(torch, dev, world, lambda: b.compute(F, UW), args.batch_steps, 3,
+                    nvtx="timed_batched") / args.batch_steps
     b.sync()
-    best = min(times, key=lambda x: x[1])[0]
+    best = min(times, key=lambda x: x[1] if x[1] == x[1] else 0.0)[0]
     b.close()
-    # the same systems through per-system contexts: plain kernel, fixed dynamic size cell list
+    # the same systems through per-system contexts with the same force kernel
+    # (row kernel, cell list per system by neighbourhood volume), one after another
     ctxs = []
     for w, kd in zip(ws, kinds):
         c = nemd.Context(dev.index)
         c.set_flow(w.A, w.L0, w.M, w.T)
         c.set_potential(kd, 1.0, 1.0, 1)
+        c.set_option(nemd.NEMD_OPT_KERNEL, 4)
         ctxs.append(c)
     qs = [q[b.offsets[s]:b.offsets[s + 1]] for s in range(len(ws))]
     Fs = [F[b.offsets[s]:b.offsets[s + 1]] for s in range(len(ws))]
@@ -610,7 +653,7 @@ def section_batched(args, world, dev, torch, nemd, W):
     def loop():
         for s, c in enumerate(ctxs):
             c.set_state(qs[s], ts[s])
-            c.build_cells(nemd.NEMD_DS, ws[s].rc)
+            c.build_cells(nemd.NEMD_AUTO_HEURISTIC, ws[s].rc)
             c.compute_forces(Fs[s])
     ms_loop = timed_loop(torch, dev, world, loop, 2, 1) / 2
     pairs_loop = sum(c.stats()["pairs"] for c in ctxs)
@@ -622,10 +665,11 @@ def section_batched(args, world, dev, torch, nemd, W):
             "pairs_per_step": pairs, "ms_per_step": ms, "pairs_per_s": pairs / ms * 1e3,
             "kernel_launches_per_step": launches,
             "autotuned": {"cell_factor": best["cell_factor"], "tile": best["tile"],
-                          "candidates_ms": [[c["cell_factor"], c["tile"], round(t, 4)] for c, t in times]},
+                          "candidates_ms": [[c["cell_factor"], c["tile"], round(t, 4)] for c, t in times
+                                            if t == t]},
             "finalize_s": t_final,
             "per_system_loop": {"ms_per_step": ms_loop, "pairs_per_s": pairs / ms_loop * 1e3,
-                                "form": "one context per system, plain kernel, dynamic size cell list"},
+                                "form": "one context per system, row kernel, cell list by neighbourhood volume"},
             "speedup_over_loop": ms_loop / ms}
 
 
@@ -991,6 +1035,10 @@ def main():
     # all work (library contexts, batches, events) on one stream of our own: the
     # legacy default stream adds a per-launch cost (about 4 % of an evaluation)
     stream = torch.cuda.Stream(dev)
+    if sections == {"kernel"}:
+        with torch.cuda.stream(stream):
+            section_kernel(args, dev, torch, nemd, W)
+        return
     with torch.cuda.stream(stream):
         main_part = section_main(args, rank, world, dev, torch, nemd, W)
         batched = section_batched(args, world, dev, torch, nemd, W) if "batched" in sections else None

@@ -282,11 +282,13 @@ __device__ __forceinline__ void cellsort_net(int *__restrict__ perm, int *__rest
     }
 }
 
+// wn: the largest cell of the calling warp (one network width per warp: no
+// divergence between widths).
 __device__ __forceinline__ void cellsort_body(const int *__restrict__ start, int *__restrict__ perm,
-                                              int *__restrict__ key_slot, int c) {
+                                              int *__restrict__ key_slot, int c, int wn) {
   const int b = start[c], e = start[c + 1], n = e - b;
   if (n <= 1) return;
-  if (n == 2) {
+  if (wn <= 2) {
     const int k0 = key_slot[b], k1 = key_slot[b + 1], i0 = perm[b], i1 = perm[b + 1];
     if (sort_before(__int_as_float(k1), i1, __int_as_float(k0), i0)) {
       key_slot[b] = k1;
@@ -296,9 +298,9 @@ __device__ __forceinline__ void cellsort_body(const int *__restrict__ start, int
     }
     return;
   }
-  if (n <= 4) return cellsort_net<4>(perm, key_slot, b, n);
-  if (n <= 8) return cellsort_net<8>(perm, key_slot, b, n);
-  if (n <= 16) return cellsort_net<16>(perm, key_slot, b, n);
+  if (wn <= 4) return cellsort_net<4>(perm, key_slot, b, n);
+  if (wn <= 8) return cellsort_net<8>(perm, key_slot, b, n);
+  if (wn <= 16) return cellsort_net<16>(perm, key_slot, b, n);
   if (n <= kNet) return cellsort_net<kNet>(perm, key_slot, b, n);
   for (int k = b + 1; k < e; k++) {
     const int kbits = key_slot[k];
@@ -318,12 +320,23 @@ __device__ __forceinline__ void cellsort_body(const int *__restrict__ start, int
   }
 }
 
+// Cells [0, ncells) a thread each, in warp-aligned strides (each warp's
+// network width from its largest cell).
+__device__ __forceinline__ void cellsort_cells(const int *__restrict__ start, int *__restrict__ perm,
+                                               int *__restrict__ key_slot, int ncells) {
+  const int lane = threadIdx.x & 31;
+  for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < ncells; base += gridDim.x * blockDim.x) {
+    const int c = base + lane;
+    const int n = c < ncells ? start[c + 1] - start[c] : 0;
+    const int wn = __reduce_max_sync(0xffffffffu, n);
+    if (c < ncells) cellsort_body(start, perm, key_slot, c, wn);
+  }
+}
+
 __global__ void k_cellsort(const Geo *g, const int *__restrict__ start, int *__restrict__ perm,
                            int *__restrict__ key_slot) {
   if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
-  const int ncells = g->ncells;
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x)
-    cellsort_body(start, perm, key_slot, c);
+  cellsort_cells(start, perm, key_slot, g->ncells);
 }
 
 // Sorted slot k: float4 {rel position, input index}, {residual, kappa}, cell id.
@@ -464,8 +477,7 @@ __global__ void k_b_scatter(BatchView v) {
 
 // Every system's cells (the cell slots of all systems are one array).
 __global__ void k_b_cellsort(BatchView v) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < v.ncells; c += gridDim.x * blockDim.x)
-    cellsort_body(v.start, v.perm, v.cell_sorted, c);
+  cellsort_cells(v.start, v.perm, v.cell_sorted, v.ncells);
 }
 
 // Sorted slots [0, start[ncells]): the particles of every system that binned.
