@@ -19,7 +19,8 @@ if not torch.cuda.is_available():
 from paper_1412_3784_gb300 import nemd  # noqa: E402
 
 F_TOL = 1e-5
-UW_TOL_FAST = 3e-6
+UW_TOL_FAST = 3e-6    # warp kernel and the batch's per-particle float32 sums (worst measured 1.4e-6)
+UW_TOL_ROW = 1e-6     # row kernel (worst measured 2.5e-7, the 2^21 system's virial)
 UW_TOL_PRECISE = 1e-9
 WARP = (2, 32)
 ROW = (4, 32)
@@ -53,7 +54,7 @@ def test_general_n1m_bench_configuration(t):
     q = torch.from_numpy(w.q).cuda()
     for kern in (2, 4):
         ctx.set_option(nemd.NEMD_OPT_KERNEL, kern)
-        check(*evaluate(ctx, w, q, nemd.NEMD_AUTO_HEURISTIC), ref)
+        check(*evaluate(ctx, w, q, nemd.NEMD_AUTO_HEURISTIC), ref, UW_TOL_ROW if kern == 4 else UW_TOL_FAST)
     # the row kernel's precise mode (float-float energy and virial): 1e-9
     ctx.set_option(nemd.NEMD_OPT_PRECISE, 1)
     check(*evaluate(ctx, w, q, nemd.NEMD_AUTO_HEURISTIC), ref, UW_TOL_PRECISE)
@@ -79,7 +80,7 @@ def test_general_n2m_cell_factors():
             for variant in (nemd.NEMD_DS, nemd.NEMD_DO):
                 F, U, Wm, st = evaluate(ctx, w, q, variant)
                 assert st["cell_factor"] == kfac
-                check(F, U, Wm, st, ref)
+                check(F, U, Wm, st, ref, UW_TOL_ROW if kern == 4 else UW_TOL_FAST)
     # precise mode on the row kernel, both cell lists: energy and virial to 1e-9
     ctx.set_option(nemd.NEMD_OPT_KERNEL, 4)
     ctx.set_option(nemd.NEMD_OPT_CELL_FACTOR, 1)

@@ -6,13 +6,17 @@ Bars:
   energy, virial       rel <= 1e-9 in precise mode (accepted pairs in float64
                        or float-float, summed in float64 / float-float);
                        fast mode (float32 pair terms summed per particle in
-                       float32, float64 across particles) <= 3e-6: the error
-                       is a few float32 roundings per pair term times the
-                       sum's condition number (sum of |terms| over |sum|), not a
-                       function of N; the worst measured is 1.4e-6 (virial of
-                       the 2^21-particle system compressed at t = 0.61 T; 2.8e-7
-                       on the smaller systems of this file), the bar leaves a
-                       factor 2
+                       float32, float64 across particles): the error is a few
+                       float32 roundings per pair term times the sum's
+                       condition number (sum of |terms| over |sum|), not a
+                       function of N.  Row kernel (the pair sums without the
+                       potential's constant factors, applied once per
+                       particle in float64) <= 1e-6: worst measured 2.5e-7
+                       (virial of the 2^21-particle system at t = 0.61 T),
+                       7.9e-7 for F.  The other kernels (constant factors in
+                       every float32 pair term) <= 3e-6: worst measured 1.4e-6
+                       on the same system, 2.8e-7 on the smaller systems of
+                       this file
   lattice              |L_gpu - L_oracle| <= 1e-13 |L|
 """
 import numpy as np
@@ -32,6 +36,7 @@ DS, DO = 0, 1
 F_TOL = 1e-5
 UW_TOL_PRECISE = 1e-9
 UW_TOL_FAST = 3e-6
+UW_TOL_ROW = 1e-6
 
 
 def keys(p):
@@ -52,8 +57,9 @@ def check_against(w, variant, ref, *, pairs=True, precise=True, kfac=1, kernel=(
     g = run(w, variant, kfac=kfac, kernel=kernel)
     assert g["stats"]["pairs"] == ref.npairs
     assert force_err(g["F"], ref.F) <= F_TOL
-    assert rel(g["U"], ref.U) <= UW_TOL_FAST
-    assert mat_rel(g["W"], ref.W) <= UW_TOL_FAST
+    uw = UW_TOL_ROW if kernel[0] == 4 else UW_TOL_FAST
+    assert rel(g["U"], ref.U) <= uw
+    assert mat_rel(g["W"], ref.W) <= uw
     if precise:
         gp = run(w, variant, precise=True, kfac=kfac, kernel=kernel)
         assert gp["stats"]["pairs"] == ref.npairs
