@@ -137,6 +137,8 @@ struct VlGeo {
   double quantum, quantum_inv;
   float rc2_lo, rc2_hi, rc2_lo2, rc2_hi2;
   double rl;  // rc + skin
+  float2 Gff[9];  // G in float-float (hi, lo)
+  float Lf[9];    // L(t) rounded to float (peculiar displacements)
 };
 
 // Per-block partial sums of the force kernel (float64): U, W (6 symmetric
@@ -265,7 +267,7 @@ struct nemd_ctx {
   int64_t vl_capn;          // particles the per-particle buffers hold
   int64_t vl_capent;        // entries vl_ent holds
   int64_t vl_n;             // particles of the current list
-  int vl_maxk;              // entries per particle (ELL width) of the current list
+  int vl_maxk;              // most entries of one particle in the current list
   int *vl_cnt;              // per sorted particle: its entries
   int2 *vl_ent;             // (sorted j, packed cell offset)
   int *vl_slot;             // per input particle: its sorted slot at the build

@@ -86,8 +86,9 @@ __global__ void k_vl_init(const Geo *__restrict__ g, const double *__restrict__ 
 // candidate whose quantised distance passes the coarse test at rl (a superset
 // of the pairs within rl).  COUNT: entries per particle only.  Otherwise the
 // entries (sorted j, cell offset k = idx_j - idx_i + c n, n the pair's lattice
-// image) in ELL layout, at most maxk per particle; both report the largest
-// count in maxcnt (the host repeats the fill with more room if it exceeded maxk).
+// image) in ELL layout (entry e of particle k at ent[e n + k]), at most maxk
+// per particle; both report the largest count in maxcnt (the host repeats
+// the fill with more room if it exceeded maxk).
 template <bool COUNT>
 __global__ void __launch_bounds__(kVlThreads) k_vl_build(
     Geo *__restrict__ g, const float4 *__restrict__ pos, const int *__restrict__ cell_sorted,
@@ -180,6 +181,9 @@ __global__ void k_vl_geo(Geo *g, VlGeo *vg, double rc) {
     const double sq = rint(vg->G[k] / q) * q;
     vg->Gq[k] = (float)sq;
     vg->Gr[k] = (float)(vg->G[k] - sq);
+    const float hi = __double2float_rn(vg->G[k]);
+    vg->Gff[k] = make_float2(hi, __double2float_rn(vg->G[k] - (double)hi));
+    vg->Lf[k] = __double2float_rn(g->L[k]);
   }
   // coarse band: the omitted residuals (two positions, q / 2 each per
   // component, and G_r k, |k| <= 4: 6 q) and the rounding of r^2; fine band:
@@ -199,13 +203,16 @@ __global__ void k_vl_geo(Geo *g, VlGeo *vg, double rc) {
   for (int k = 0; k < 9; k++) g->Qf[k] = (k % 4 == 0) ? 1.0f : 0.0f;
 }
 
-// Per input particle at a step: its fractional position s (canonical wrap),
-// the image m = round(s_b - s) the wrap has moved it by since the build, its
-// peculiar displacement |L u| (u = s + m - s_b; the largest goes to disp as
-// float bits), and its position relative to the centre of its build cell,
-// p = G (c (s + m) - idx - 1/2), split into an exact multiple of the quantum
-// and a float32 residual, stored at its sorted slot (.w: input index; the
-// residual's .w: m packed).
+// Per input particle at a step: its fractional position s (the canonical
+// wrap, in float-float: frac_wrap_ff takes float64 wherever the float-float
+// floor could differ), the image m = round(s_b - s) the wrap has moved it by
+// since the build, its peculiar displacement |L u| (u = s + m - s_b, in float;
+// the largest goes to disp as float bits), and its position relative to the
+// centre of its build cell, p = G (c (s + m) - idx - 1/2), in float-float,
+// split into an exact multiple of the quantum and a float32 residual, stored
+// at its sorted slot (.w: input index; the residual's .w: m packed).  The
+// float-float p is within ~2^-44 |p| of the float64 value: far below the
+// float32 residual's rounding, which the guard bands already cover.
 __global__ void __launch_bounds__(kVlThreads) k_vl_pos(const Geo *__restrict__ g, const VlGeo *__restrict__ vg,
                                                        const double *__restrict__ q, int n,
                                                        const int *__restrict__ slot, const double *__restrict__ sb,
@@ -215,32 +222,46 @@ __global__ void __launch_bounds__(kVlThreads) k_vl_pos(const Geo *__restrict__ g
   float dmax = 0.0f;
   if (i < n) {
     const int k = slot[i];
-    double s[3];
-    frac_wrap(g->Linv, q[3 * (size_t)i], q[3 * (size_t)i + 1], q[3 * (size_t)i + 2], s);
+    ff s[3];
+    double s64[3];
+    bool exact;
+    float tol[3];
+    frac_wrap_ff(g, q[3 * (size_t)i], q[3 * (size_t)i + 1], q[3 * (size_t)i + 2], s, s64, exact, tol);
     const int4 ii = idx[k];
     int m[3];
-    double hs[3], u[3];
+    ff t3[3];
+    float u[3];
+    const int ic[3] = {ii.x, ii.y, ii.z};
+#pragma unroll
     for (int a = 0; a < 3; a++) {
-      const double b = sb[3 * (size_t)k + a];
-      m[a] = (int)rint(b - s[a]);
-      hs[a] = s[a] + (double)m[a];
-      u[a] = hs[a] - b;
+      const ff b = split_unit(sb[3 * (size_t)k + a]);
+      m[a] = (int)rintf(__fsub_rn(b.hi, s[a].hi));  // |s_b - s - m| is a small displacement
+      const ff hs = ff_add(s[a], ff{(float)m[a], 0.f});
+      const ff du = ff_add(hs, ff_neg(b));
+      u[a] = __fadd_rn(du.hi, du.lo);
+      // c (s + m) - idx - 1/2 (c and idx + 1/2 exact in float)
+      t3[a] = ff_add(ff_mul_f(hs, (float)vg->c[a]), ff{-((float)ic[a] + 0.5f), 0.f});
     }
-    const double *L = g->L;
-    double du2 = 0.0;
+    float du2 = 0.0f;
+#pragma unroll
     for (int a = 0; a < 3; a++) {
-      const double v = (L[3 * a] * u[0] + L[3 * a + 1] * u[1]) + L[3 * a + 2] * u[2];
-      du2 += v * v;
+      const float v = fmaf(vg->Lf[3 * a + 2], u[2], fmaf(vg->Lf[3 * a + 1], u[1], vg->Lf[3 * a] * u[0]));
+      du2 = fmaf(v, v, du2);
     }
-    dmax = (float)sqrt(du2) * (1.0f + 1e-6f);
-    const double t3[3] = {(double)vg->c[0] * hs[0] - (double)ii.x - 0.5, (double)vg->c[1] * hs[1] - (double)ii.y - 0.5,
-                          (double)vg->c[2] * hs[2] - (double)ii.z - 0.5};
+    dmax = sqrtf(du2) * (1.0f + 1e-5f) + 1e-12f;
     float X[3], R[3];
+    const float qf = vg->quantum_f, qi = vg->quantum_inv_f;
+#pragma unroll
     for (int a = 0; a < 3; a++) {
-      const double p = (vg->G[3 * a] * t3[0] + vg->G[3 * a + 1] * t3[1]) + vg->G[3 * a + 2] * t3[2];
-      const double x = rint(p * vg->quantum_inv) * vg->quantum;
-      X[a] = (float)x;
-      R[a] = (float)(p - x);
+      const ff p = ff_add(ff_add(ff_mul(ff_of(vg->Gff[3 * a]), t3[0]), ff_mul(ff_of(vg->Gff[3 * a + 1]), t3[1])),
+                          ff_mul(ff_of(vg->Gff[3 * a + 2]), t3[2]));
+      // the multiple of the quantum nearest to p.hi + p.lo (scaling by powers of two is exact)
+      const float tq = __fmul_rn(p.hi, qi);
+      float r = rintf(tq);
+      const float d = __fadd_rn(__fsub_rn(tq, r), __fmul_rn(p.lo, qi));
+      r = d > 0.5f ? __fadd_rn(r, 1.f) : (d < -0.5f ? __fsub_rn(r, 1.f) : r);
+      X[a] = __fmul_rn(r, qf);
+      R[a] = __fadd_rn(__fsub_rn(p.hi, X[a]), p.lo);
     }
     pos[k] = make_float4(X[0], X[1], X[2], __int_as_float(i));
     res[k] = make_float4(R[0], R[1], R[2], __int_as_float(pack3(m[0], m[1], m[2])));
