@@ -95,6 +95,8 @@ def parse():
                    help="force kernel without autotuning (0 plain, 1 grouped, 2 warp, 3 warp half, 4 row)")
     p.add_argument("--group", type=int, default=16, help="lanes per group of the grouped kernel")
     p.add_argument("--kfac", type=int, default=1, help="cell-size factor without autotuning")
+    p.add_argument("--streams", type=int, default=3,
+                   help="contexts (each on its own CUDA stream) that take the strains of the tuned step in turn")
     p.add_argument("--sections", default="main,batched,learned,shear,equilibrium,integrate",
                    help="comma list of main, batched, learned, shear, equilibrium, integrate; or "
                         "'kernel' alone: one strain's forces evaluated three times back to back "
@@ -429,20 +431,82 @@ def section_main(args, rank, world, dev, torch, nemd, W):
 
     clocks = Clocks(dev.index)
     variant = configure("tuned")
+    # the tuned form as one context on the bench's stream (one evaluation after
+    # another) ...
     for _ in range(args.warmup):
         one_step(variant)
     ctx.sync()
+    # the force kernel's launch durations for the roofline come from this loop:
+    # under concurrency a launch's events also count the time it waits for SMs
+    # that another context's kernels hold
     ctx.set_option(nemd.NEMD_OPT_TIMING, 1)
-    launches0 = ctx.stats()["launches"]
-    clocks.start()
-    torch.cuda.nvtx.range_push("timed_tuned")   # marks the timed region for profilers
-    ms_tuned = timed_loop(torch, dev, world, lambda: one_step(variant), args.steps, 0)
-    torch.cuda.nvtx.range_pop()
-    clk = clocks.stop()
-    launches = ctx.stats()["launches"] - launches0
+    ms_single = timed_loop(torch, dev, world, lambda: one_step(variant), args.steps, 0)
     ctx.sync()
     k_ms, k_n = ctx.kernel_time()
     ctx.set_option(nemd.NEMD_OPT_TIMING, 0)
+    # ... and as K contexts, each on its own CUDA stream, taking the strains in
+    # turn: the strains are independent evaluations, so the lattice, grid and
+    # stencil kernels of one overlap the force kernel of another.  Every
+    # context runs the tuned configuration (the autotuner's choice above).
+    K = max(1, args.streams)
+    choice = tune["choice"] if tune is not None else {"kernel": args.kernel, "group": args.group,
+                                                      "cell_factor": args.kfac}
+    pipe = []
+    for k in range(K):
+        st = torch.cuda.Stream(dev)
+        c = nemd.Context(dev.index, stream=st.cuda_stream)
+        c.set_flow(ser.A, ser.L0, ser.M, ser.period)
+        c.set_potential(nemd.NEMD_LJ, 1.0, 1.0, 1)
+        c.set_option(nemd.NEMD_OPT_KERNEL, choice["kernel"])
+        c.set_option(nemd.NEMD_OPT_GROUP, choice["group"])
+        c.set_option(nemd.NEMD_OPT_CELL_FACTOR, choice["cell_factor"])
+        outs = (torch.empty((n, 3), dtype=torch.float32, device=dev), torch.zeros(1, dtype=torch.float64, device=dev),
+                torch.zeros(9, dtype=torch.float64, device=dev))
+        pipe.append((c, st, outs))
+
+    def pipe_step():
+        for i in range(S):
+            c, _, (Fk, Uk, Wk) = pipe[i % K]
+            c.set_state(q_all[i], ts[i])
+            c.build_cells(nemd.NEMD_AUTO_HEURISTIC, ser.rc)
+            c.compute_forces(Fk, Uk, Wk)
+
+    def pipe_timed(steps, warmup):
+        for _ in range(warmup):
+            pipe_step()
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        home = torch.cuda.current_stream(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("timed_tuned")   # marks the timed region for profilers
+        e0.record(home)
+        for _, st, _ in pipe:
+            st.wait_event(e0)
+        for _ in range(steps):
+            pipe_step()
+        for _, st, _ in pipe:
+            home.wait_stream(st)
+        e1.record(home)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        return e0.elapsed_time(e1)
+
+    for _ in range(args.warmup):
+        pipe_step()
+    torch.cuda.synchronize(dev)
+    launches0 = sum(c.stats()["launches"] for c, _, _ in pipe)
+    clocks.start()
+    ms_tuned = pipe_timed(args.steps, 0)
+    clk = clocks.stop()
+    launches = sum(c.stats()["launches"] for c, _, _ in pipe) - launches0
+    # each context's last strain gave the pairs of the untimed pass
+    for k, (c, _, _) in enumerate(pipe):
+        c.sync()
+        last = max(i for i in range(S) if i % K == k) if k < S else None
+        if last is not None:
+            assert c.stats()["pairs"] == per["tuned"]["pairs"][last], "pipelined pairs differ"
     kernel_name = {0: "k_force_plain", 1: "k_force_chunk", 2: "k_force_warp", 3: "k_force_warp (half)",
                    4: "k_force_row"}
     tuned_kernel = tune["choice"]["kernel"] if tune is not None else args.kernel
@@ -454,6 +518,7 @@ def section_main(args, rank, world, dev, torch, nemd, W):
     ms_tuned_max = max_over_ranks(ms_tuned, world, dev)
     total_pairs = sum_over_ranks(float(pairs_per_step * args.steps), world, dev)
     value = total_pairs / (ms_tuned_max * 1e-3)
+    single_stream = total_pairs / (max_over_ranks(ms_single, world, dev) * 1e-3)
     plain_ds = total_pairs / (max_over_ranks(ms_ds, world, dev) * 1e-3)
     plain_do = total_pairs / (max_over_ranks(ms_do, world, dev) * 1e-3)
 
@@ -518,47 +583,50 @@ def section_main(args, rank, world, dev, torch, nemd, W):
     Se = min(args.e2e_strains, S)
     e2e_idx = [j * S // Se for j in range(Se)]
     qh = [torch.from_numpy(ser.positions(ts[i])).pin_memory() for i in e2e_idx]
-    Fh = torch.empty((n, 3), dtype=torch.float32).pin_memory()
-    Uh = torch.zeros(1, dtype=torch.float64).pin_memory()
-    Wh = torch.zeros(9, dtype=torch.float64).pin_memory()
-    variant = configure("tuned")
+    # the tuned form as timed above: the K contexts take the strains in turn,
+    # each with its own pinned result buffers
+    outh = [(torch.empty((n, 3), dtype=torch.float32).pin_memory(), torch.zeros(1, dtype=torch.float64).pin_memory(),
+             torch.zeros(9, dtype=torch.float64).pin_memory()) for _ in range(K)]
     # asynchronous host I/O: the copy of the next state's positions (and of the
     # previous result) overlaps the current evaluation; results valid after sync
-    ctx.set_option(nemd.NEMD_OPT_ASYNC_HOST, 1)
+    for c, _, _ in pipe:
+        c.set_option(nemd.NEMD_OPT_ASYNC_HOST, 1)
+
+    def e2e_pass(host):
+        for j in range(Se):
+            c, _, outd = pipe[j % K]
+            c.set_state(qh[j] if host else q_all[e2e_idx[j]], ts[e2e_idx[j]])
+            c.build_cells(nemd.NEMD_AUTO_HEURISTIC, ser.rc)
+            c.compute_forces(*(outh[j % K] if host else outd))
+        for c, _, _ in pipe:
+            c.sync()                         # every copy back has landed
+
     # untimed passes over every host buffer first: the first device accesses of
     # freshly pinned pages are measurably slower than later ones
     for _ in range(2):
-        for j in range(Se):
-            ctx.set_state(qh[j], ts[e2e_idx[j]])
-            ctx.build_cells(variant, ser.rc)
-            ctx.compute_forces(Fh, Uh, Wh)
-    ctx.sync()
+        e2e_pass(True)
     # three timed passes over the Se strains; the median pass is reported
     e2e_reps = []
     for _ in range(3):
         barrier(world)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        for j in range(Se):
-            ctx.set_state(qh[j], ts[e2e_idx[j]])
-            ctx.build_cells(variant, ser.rc)
-            ctx.compute_forces(Fh, Uh, Wh)
-        ctx.sync()                           # every copy back has landed
+        e2e_pass(True)
         torch.cuda.synchronize(dev)
         e2e_reps.append(max_over_ranks(time.perf_counter() - t0, world, dev))
     e2e_s = sorted(e2e_reps)[1]
-    ctx.set_option(nemd.NEMD_OPT_ASYNC_HOST, 0)
+    for c, _, _ in pipe:
+        c.set_option(nemd.NEMD_OPT_ASYNC_HOST, 0)
     e2e_pairs = sum_over_ranks(float(sum(per["tuned"]["pairs"][i] for i in e2e_idx)), world, dev)
     # the same strains from device-resident positions, timed the same way
+    e2e_pass(False)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    for j in range(Se):
-        ctx.set_state(q_all[e2e_idx[j]], ts[e2e_idx[j]])
-        ctx.build_cells(variant, ser.rc)
-        ctx.compute_forces(F, U, Wv)
-    ctx.sync()
+    e2e_pass(False)
     torch.cuda.synchronize(dev)
     dev_same_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    for c, _, _ in pipe:
+        c.close()
     # the box's pinned host <-> device copy rate, measured beside the e2e loop
     probe_h = torch.empty(6 << 20, dtype=torch.float32).pin_memory()
     probe_d = torch.empty(6 << 20, dtype=torch.float32, device=dev)
@@ -577,8 +645,10 @@ def section_main(args, rank, world, dev, torch, nemd, W):
            "pass_ms": [round(x * 1e3, 3) for x in e2e_reps],
            "h2d_bytes_per_step": int(S * n * 3 * 8), "d2h_bytes_per_step": int(S * (n * 3 * 4 + 80)),
            "strains_timed": Se, "strains_timed_are": "evenly spaced over the period",
-           "mode": "host positions in and host F, U, W out every strain through the C ABI with "
-                   "NEMD_OPT_ASYNC_HOST (copies on a second stream overlap the evaluations), one sync at the end; median of three passes"}
+           "mode": f"host positions in and host F, U, W out every strain through the C ABI with "
+                   f"NEMD_OPT_ASYNC_HOST (copies on a second stream of each context overlap the evaluations), "
+                   f"the {K} contexts of the tuned step taking the strains in turn, one sync per context at the "
+                   f"end; median of three passes"}
     ctx.close()
     del q_all
 
@@ -601,9 +671,17 @@ def section_main(args, rank, world, dev, torch, nemd, W):
                             f"; cell list per strain by neighbourhood volume (dynamic offset at {ndo} of {S})",
                    "coarse_band_candidates_per_step": int(sum(per["tuned"]["rechecks"])),
                    "l2": "inputs larger than L2: a distinct 24 MB position array per strain",
+                   "streams": K,
+                   "concurrency": f"{K} contexts, each on its own CUDA stream, take the strains in turn "
+                                  "(independent evaluations; one context's setup kernels overlap "
+                                  "another's force kernel)",
                    "parallelism": f"replicas x{world}"},
+        "single_stream": {"pairs_per_s": single_stream, "ms_per_step": max_over_ranks(ms_single, world, dev) /
+                          args.steps, "streams_over_single": value / single_stream,
+                          "form": "the same tuned evaluations, one context on one stream"},
         "plain": {"dynamic_size_pairs_per_s": plain_ds, "dynamic_offset_pairs_per_s": plain_do,
-                  "tuned_over_best_plain": value / max(plain_ds, plain_do),
+                  "tuned_over_best_plain": single_stream / max(plain_ds, plain_do),
+                  "basis": "single-stream tuned form against the plain kernels, also one stream",
                   "search_efficiency_ds": eta_ds, "search_efficiency_do": eta_do},
         "autotune": tune,
         "roofline": roofline, "precise": precise, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
@@ -1054,7 +1132,8 @@ def main():
             "vs_baseline": None, "dtype": "f32 pair math, f64 lattice/guard band/reductions, float-float wrap",
             "data": "synthetic",
         }
-        for key in ("config", "plain", "autotune", "roofline", "precise", "cpu_baseline", "e2e", "gpu_launches",
+        for key in ("config", "single_stream", "plain", "autotune", "roofline", "precise", "cpu_baseline", "e2e",
+                    "gpu_launches",
                     "clocks"):
             line[key] = main_part[key]
         line["batched"] = batched
