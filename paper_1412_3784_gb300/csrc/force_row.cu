@@ -46,10 +46,14 @@ namespace nemd {
 #ifndef NEMD_ROW_WORDS
 #define NEMD_ROW_WORDS 12
 #endif
+#ifndef NEMD_ROW_PASS
+#define NEMD_ROW_PASS 2
+#endif
 constexpr int kRowThreads = 128;
 constexpr int kRowMinBlocks = NEMD_ROW_MINBLOCKS;
 constexpr int kRowStage = NEMD_ROW_STAGE;  // even
 constexpr int kRowWords = NEMD_ROW_WORDS;  // accept masks per lane between two flushes
+constexpr int kRowPass = NEMD_ROW_PASS;    // accepted slots a lane loads together in a flush pass
 constexpr int kRowRowsStaged = 32;   // rows per class the kernel stages (cell factor <= 2)
 constexpr int kRowABias = 64;        // SA[slot] = row | (A + kRowABias) << 5
 constexpr int kRowPad = 32;          // half slots past the stage that a lane's last mask may read
@@ -253,18 +257,27 @@ __device__ __forceinline__ void row_flush(RowStage &S, int &qn, int &nw, int &nr
   const float lo2 = g->rc2_lo2, hi2 = g->rc2_hi2;
   unsigned cur = 0;
   int base = 0, wi = 0;
-  // two entries per pass, both loaded before either is used (independent
+  // kRowPass entries per pass, all loaded before any is used (independent
   // chains for the scheduler); each is decided and added on its own
-  for (int s = 0; s < m; s += 2) {
-    const bool v0 = s < qn, v1 = s + 1 < qn;
-    const int sl0 = v0 ? row_next_slot(S, lane, cur, base, wi) : 0;
-    const int sl1 = v1 ? row_next_slot(S, lane, cur, base, wi) : 0;
-    const float4 X0 = S.X[sl0], R0 = S.R[sl0], X1 = S.X[sl1], R1 = S.R[sl1];
+  for (int s = 0; s < m; s += kRowPass) {
+    bool vv[kRowPass];
+    int sl[kRowPass];
+    float4 XX[kRowPass], RR[kRowPass];
 #pragma unroll
-    for (int h = 0; h < 2; h++) {
-      if (!(h ? v1 : v0)) continue;
-      const int slot = h ? sl1 : sl0;
-      const float4 X = h ? X1 : X0, R = h ? R1 : R0;
+    for (int h = 0; h < kRowPass; h++) {
+      vv[h] = s + h < qn;
+      sl[h] = vv[h] ? row_next_slot(S, lane, cur, base, wi) : 0;
+    }
+#pragma unroll
+    for (int h = 0; h < kRowPass; h++) {
+      XX[h] = S.X[sl[h]];
+      RR[h] = S.R[sl[h]];
+    }
+#pragma unroll
+    for (int h = 0; h < kRowPass; h++) {
+      if (!vv[h]) continue;
+      const int slot = sl[h];
+      const float4 X = XX[h], R = RR[h];
       const int j = __float_as_int(R.w);
       const float cx = (X.x - Xi.x) + (R.x - Ri.x);
       const float cy = (X.y - Xi.y) + (R.y - Ri.y);
@@ -587,6 +600,11 @@ cudaError_t launch_force_row(nemd_ctx *c, float *F, int *nblocks) {
   const bool rec = c->record_cap > 0, pre = c->precise != 0;
   int blocks = rec ? (pre ? row_resident_blocks<true, true>(c->sms) : row_resident_blocks<true, false>(c->sms))
                    : (pre ? row_resident_blocks<false, true>(c->sms) : row_resident_blocks<false, false>(c->sms));
+  // a small system needs fewer blocks than the resident limit (one per 64
+  // particles; the warps stride over the chunks either way), and the fix-up
+  // then sums fewer partial rows
+  const int64_t by_n = (c->n + 63) / 64;
+  if ((int64_t)blocks > by_n) blocks = (int)std::max<int64_t>(by_n, 1);
   if (blocks > (int)(c->cap_partials - 1)) blocks = (int)(c->cap_partials - 1);
   *nblocks = blocks;
 #define NEMD_ARGS                                                                                            \

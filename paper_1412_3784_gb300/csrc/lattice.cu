@@ -180,18 +180,24 @@ __device__ __forceinline__ void lattice_body(Geo *g, const LatIn &in, LatScratch
   if (lane == 0) {
     g->tau = tau;
     g->V = fabs(det);
+    // heights 1 / |row_i(L^-1)| = |det| / |row_i(cof)|, by the reciprocal square
+    // root (float64 division and square root are each ~0.3 us of latency here)
+    const double adet = fabs(det);
     for (int i = 0; i < 3; i++) {
-      double r0 = cof[3 * i] / det, r1 = cof[3 * i + 1] / det, r2 = cof[3 * i + 2] / det;
-      g->h[i] = 1.0 / sqrt(r0 * r0 + r1 * r1 + r2 * r2);
+      const double r0 = cof[3 * i], r1 = cof[3 * i + 1], r2 = cof[3 * i + 2];
+      g->h[i] = adet * rsqrt(r0 * r0 + r1 * r1 + r2 * r2);
     }
+    // Cholesky of the Gram matrix, each pivot's reciprocal formed once
     double r11 = sqrt(Gm[0]);
-    double r12 = Gm[1] / r11, r13 = Gm[2] / r11;
+    const double i11 = 1.0 / r11;
+    double r12 = Gm[1] * i11, r13 = Gm[2] * i11;
     double r22 = sqrt(Gm[4] - r12 * r12);
-    double r23 = (Gm[5] - r12 * r13) / r22;
+    const double i22 = 1.0 / r22;
+    double r23 = (Gm[5] - r12 * r13) * i22;
     double r33 = sqrt(Gm[8] - r13 * r13 - r23 * r23);
+    const double i33 = 1.0 / r33;
     double R[9] = {r11, r12, r13, 0.0, r22, r23, 0.0, 0.0, r33};
     for (int k = 0; k < 9; k++) Rm[k] = R[k];
-    double i11 = 1.0 / r11, i22 = 1.0 / r22, i33 = 1.0 / r33;
     Ri[0] = i11;
     Ri[1] = -r12 * i11 * i22;
     Ri[2] = (r12 * r23 - r13 * r22) * i11 * i22 * i33;
@@ -208,8 +214,9 @@ __device__ __forceinline__ void lattice_body(Geo *g, const LatIn &in, LatScratch
     g->Rff[lane] = to_ff2(Rm[lane]);
   }
   if (lane < 3) {
-    g->rinv[lane] = 1.0 / Rm[4 * lane];
-    g->rinvff[lane] = to_ff2(1.0 / Rm[4 * lane]);
+    const double ri = Ri[4 * lane];  // 1 / r_ii, from the Cholesky above
+    g->rinv[lane] = ri;
+    g->rinvff[lane] = to_ff2(ri);
   }
   mm3(Ls, Ri, Ri, lane);  // Q = L R^-1
   if (lane < 9) g->Q[lane] = Ri[lane];
@@ -239,10 +246,15 @@ __device__ void grid_body(Geo *g, const GridIn &in) {
   const double rc = g->rc;
   const double V = g->V;
   const double fac = (1.0 - kMargin);
+  // one reciprocal instead of a division per count (a float64 division is
+  // ~0.3 us of latency on this part, and this thread's work is serial): the
+  // product differs from the quotient by a rounding, which moves a count only
+  // within 2^-52 of an integer, inside the 1e-12 margin of fac
+  const double irc = 1.0 / rc;
   int cds1[3], cdo1[3];
   for (int a = 0; a < 3; a++) {
-    cds1[a] = (int)floor(fac * g->h[a] / rc);
-    cdo1[a] = (int)floor(fac * Rm[4 * a] / rc);
+    cds1[a] = (int)floor(fac * g->h[a] * irc);
+    cdo1[a] = (int)floor(fac * Rm[4 * a] * irc);
   }
   // neighbourhood volumes at k = 1 (Sec. 5.1, 5.2)
   double vds = 1e300, vdo = 1e300;
@@ -287,9 +299,11 @@ __device__ void grid_body(Geo *g, const GridIn &in) {
   g->wrap_tol = wtol;
   const double rce = rc * (1.0 + kMargin) + (variant == NEMD_DS ? 0.0 : 2.0 * wtol);
   if (variant == NEMD_DS) {
-    for (int a = 0; a < 3; a++) nc[a] = (int)floor(fac * (double)kf * g->h[a] / rc);
+    for (int a = 0; a < 3; a++) nc[a] = (int)floor(fac * (double)kf * g->h[a] * irc);
+    double inc[3];
+    for (int b = 0; b < 3; b++) inc[b] = nc[b] > 0 ? 1.0 / (double)nc[b] : 0.0;
     for (int a = 0; a < 3; a++)
-      for (int b = 0; b < 3; b++) Gd[3 * a + b] = (nc[b] > 0) ? Ls[3 * a + b] / (double)nc[b] : 0.0;
+      for (int b = 0; b < 3; b++) Gd[3 * a + b] = Ls[3 * a + b] * inc[b];
     for (int a = 0; a < 3; a++) {
       g->Ginv_scale[a] = (double)nc[a];
       g->w[a] = 0.0;
@@ -298,16 +312,17 @@ __device__ void grid_body(Geo *g, const GridIn &in) {
     maxrows = (2 * kf + 1) * (2 * kf + 1);
     for (int k = 0; k < 9; k++) g->Qf[k] = (k % 4 == 0) ? 1.0f : 0.0f;
   } else {
-    for (int a = 0; a < 3; a++) nc[a] = (int)floor(fac * (double)kf * Rm[4 * a] / rc);
+    for (int a = 0; a < 3; a++) nc[a] = (int)floor(fac * (double)kf * Rm[4 * a] * irc);
     for (int k = 0; k < 9; k++) Gd[k] = 0.0;
     for (int a = 0; a < 3; a++) {
-      double w = (nc[a] > 0) ? Rm[4 * a] / (double)nc[a] : 1.0;
+      const double w = (nc[a] > 0) ? Rm[4 * a] / (double)nc[a] : 1.0;
+      const double iw = 1.0 / w;  // the one reciprocal of the side: binning, windows and reach
       g->w[a] = w;
-      g->Ginv_scale[a] = 1.0 / w;
+      g->Ginv_scale[a] = iw;
       g->wff[a] = to_ff2(w);
-      g->Ginvff[a] = to_ff2(1.0 / w);
+      g->Ginvff[a] = to_ff2(iw);
       Gd[4 * a] = w;
-      reach[a] = (int)ceil(rce / w);
+      reach[a] = (int)ceil(rce * iw);
     }
     maxrows = (2 * reach[2] + 1) * (2 * reach[1] + 2);
     for (int k = 0; k < 9; k++) g->Qf[k] = (float)Ri[k];
@@ -356,7 +371,7 @@ __device__ void grid_body(Geo *g, const GridIn &in) {
   // frame vector between consecutive x-cells: G e_x (dynamic size), (w1, 0, 0) (dynamic offset)
   for (int a = 0; a < 3; a++) {
     double sv = Gd[3 * a];
-    double sq = rint(sv / q) * q;
+    double sq = rint(sv * g->quantum_inv) * q;  // q a power of two: exact
     step[a] = (float)sq;
     g->step_r[a] = (float)(sv - sq);
   }
@@ -383,7 +398,7 @@ __device__ void grid_body(Geo *g, const GridIn &in) {
     if (variant == NEMD_DS) {
       for (int a = 0; a < 3; a++) k3[a] = (double)nc[0] * g->Linv[a];
     } else {
-      k3[0] = nc[0] > 0 ? 1.0 / g->w[0] : 0.0;
+      k3[0] = nc[0] > 0 ? g->Ginv_scale[0] : 0.0;
       k3[1] = k3[2] = 0.0;
     }
     const double kn = sqrt(k3[0] * k3[0] + k3[1] * k3[1] + k3[2] * k3[2]);

@@ -25,13 +25,17 @@ constexpr int DI = kMlpIn, H = kMlpHidden, DO_ = kMlpOut;
 constexpr int OW1 = 0, OB1 = OW1 + H * DI, OW2 = OB1 + H, OB2 = OW2 + H * H, OW3 = OB2 + H, OB3 = OW3 + DO_ * H;
 static_assert(OB3 + DO_ == kMlpParams, "parameter layout");
 
-// Features of the current step, from the device lattice.
+// Features of the current step, from the device lattice, in float32 (inputs
+// of a float32 network; training and inference both come through here).  No
+// float64 division: one costs ~0.3 us of latency on this part, and this runs
+// on one thread at every build.
 __device__ void step_features(const Geo *g, int64_t n, double rc, float *x) {
-  const double s = cbrt(g->V);
-  for (int k = 0; k < 9; k++) x[k] = (float)(g->L[k] / s);
-  x[9] = (float)((double)n / g->V);
+  const float V = (float)g->V;
+  const float is = 1.0f / cbrtf(V);
+  for (int k = 0; k < 9; k++) x[k] = (float)g->L[k] * is;
+  x[9] = (float)n / V;
   x[10] = (float)rc;
-  x[11] = (float)log((double)(n > 0 ? n : 1));
+  x[11] = logf((float)(n > 0 ? n : 1));
 }
 
 // One sample's forward pass in a block of H threads; h1, h2 in shared memory.
