@@ -275,8 +275,15 @@ __global__ void __launch_bounds__(kVlThreads) k_vl_pos(const Geo *__restrict__ g
 // thread per sorted particle, its entries in order; the few candidates within
 // float32 rounding of rc are deferred to the float64 fix-up pass with their
 // canonical image n + m_j - m_i (RECORD: decided here and recorded).
+// Six resident blocks per SM (80 registers): the kernel waits on its gathers,
+// and more warps in flight beat the few spilled registers (measured per step
+// of the N = 2^20 integrator: 1.26 ms at four blocks, 1.12 at six, 1.34 at
+// eight).
+#ifndef NEMD_VL_MINBLOCKS
+#define NEMD_VL_MINBLOCKS 6
+#endif
 template <bool RECORD>
-__global__ void __launch_bounds__(kVlThreads) k_vl_force(
+__global__ void __launch_bounds__(kVlThreads, NEMD_VL_MINBLOCKS) k_vl_force(
     const Geo *__restrict__ g, const VlGeo *__restrict__ vg, const float4 *__restrict__ pos,
     const float4 *__restrict__ res, const int *__restrict__ cnt, const int2 *__restrict__ ent,
     const int4 *__restrict__ idx, int n, const double *__restrict__ q, Pot pp, float *__restrict__ F,
