@@ -273,7 +273,8 @@ struct nemd_ctx {
   int *vl_slot;             // per input particle: its sorted slot at the build
   double *vl_sb;            // per sorted particle: fractional position at the build (3)
   int4 *vl_idx;             // per sorted particle: list cell (x, y, z), brick image (packed) in w
-  float4 *vl_pos, *vl_res;  // per sorted particle, per step: position in its cell, residual
+  float4 *vl_pos, *vl_res;  // per sorted particle, per step: position in its cell and residual
+                            // interleaved in vl_pos (vl_res unused)
   nemd::VlGeo *vl_geo;      // device
   unsigned *vl_disp;        // device: largest displacement (float bits), its maximum entry count
   unsigned *h_vl;           // pinned host copy of vl_disp[0..1]

@@ -39,6 +39,9 @@ namespace nemd {
 namespace {
 
 constexpr int kVlThreads = 128;
+// Per-step position and residual of a particle in one 32-byte record
+// (vl_pos[2k], vl_pos[2k + 1]): a gather of both touches one sector.
+constexpr int kVlRec = 2;
 
 __device__ __forceinline__ int pack3(int x, int y, int z) {
   return (x & 1023) | ((y & 1023) << 10) | ((z & 1023) << 20);
@@ -263,8 +266,8 @@ __global__ void __launch_bounds__(kVlThreads) k_vl_pos(const Geo *__restrict__ g
       X[a] = __fmul_rn(r, qf);
       R[a] = __fadd_rn(__fsub_rn(p.hi, X[a]), p.lo);
     }
-    pos[k] = make_float4(X[0], X[1], X[2], __int_as_float(i));
-    res[k] = make_float4(R[0], R[1], R[2], __int_as_float(pack3(m[0], m[1], m[2])));
+    pos[kVlRec * (size_t)k] = make_float4(X[0], X[1], X[2], __int_as_float(i));
+    res[kVlRec * (size_t)k] = make_float4(R[0], R[1], R[2], __int_as_float(pack3(m[0], m[1], m[2])));
   }
   // largest displacement of the block (positive floats order as their bits)
   for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
@@ -295,7 +298,7 @@ __global__ void __launch_bounds__(kVlThreads, NEMD_VL_MINBLOCKS) k_vl_force(
   int ncand = 0, nre = 0;
   const bool ok = !(g->error & (ERRB_BOX | ERRB_CAPACITY));
   if (ok && k < n) {
-    const float4 pi = pos[k], ri = res[k];
+    const float4 pi = pos[kVlRec * (size_t)k], ri = res[kVlRec * (size_t)k];
     const int oi = __float_as_int(pi.w);
     const float lo = vg->rc2_lo, hi = vg->rc2_hi, lo2 = vg->rc2_lo2, hi2 = vg->rc2_hi2;
     float Gq[9], Gr[9];
@@ -313,7 +316,7 @@ __global__ void __launch_bounds__(kVlThreads, NEMD_VL_MINBLOCKS) k_vl_force(
       for (int h = 0; h < U; h++)
         eu[h] = e0 + h < ne ? __ldcs(&ent[(size_t)(e0 + h) * n + k]) : make_int2(k, 0);
 #pragma unroll
-      for (int h = 0; h < U; h++) pu[h] = pos[eu[h].x];
+      for (int h = 0; h < U; h++) pu[h] = pos[kVlRec * (size_t)eu[h].x];
 #pragma unroll
       for (int h = 0; h < U; h++) {
       if (e0 + h >= ne) break;
@@ -327,7 +330,7 @@ __global__ void __launch_bounds__(kVlThreads, NEMD_VL_MINBLOCKS) k_vl_force(
       const float dz = (pj.z - pi.z) + ((Gq[6] * k0 + Gq[7] * k1) + Gq[8] * k2);
       const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
       if (!(r2 < hi)) continue;
-      const float4 rj = res[j];
+      const float4 rj = res[kVlRec * (size_t)j];
       const float cx = dx + ((rj.x - ri.x) + fmaf(Gr[2], k2, fmaf(Gr[1], k1, Gr[0] * k0)));
       const float cy = dy + ((rj.y - ri.y) + fmaf(Gr[5], k2, fmaf(Gr[4], k1, Gr[3] * k0)));
       const float cz = dz + ((rj.z - ri.z) + fmaf(Gr[8], k2, fmaf(Gr[7], k1, Gr[6] * k0)));
@@ -405,7 +408,7 @@ int vl_reserve(nemd_ctx *c, int64_t n) {
   int r;
   if ((r = vl_grow(c, &c->vl_cnt, n, &cap)) || (r = vl_grow(c, &c->vl_slot, n, &cap)) ||
       (r = vl_grow(c, &c->vl_sb, 3 * n, &cap)) || (r = vl_grow(c, &c->vl_idx, n, &cap)) ||
-      (r = vl_grow(c, &c->vl_pos, n, &cap)) || (r = vl_grow(c, &c->vl_res, n, &cap)))
+      (r = vl_grow(c, &c->vl_pos, kVlRec * n, &cap)))
     return r;
   c->vl_capn = n;
   return NEMD_OK;
@@ -433,7 +436,7 @@ int verlet_forces(nemd_ctx *c, float *F, int variant, double rc, double t) {
     k_vl_geo<<<1, 32, 0, c->stream>>>(c->geo, c->vl_geo, rc);
     if ((r = vl_cuda(c, cudaMemsetAsync(c->vl_disp, 0, sizeof(unsigned), c->stream), "memset"))) return r;
     k_vl_pos<<<nb, kVlThreads, 0, c->stream>>>(c->geo, c->vl_geo, c->q_dev, (int)n, c->vl_slot, c->vl_sb, c->vl_idx,
-                                               c->vl_pos, c->vl_res, c->vl_disp);
+                                               c->vl_pos, c->vl_pos + 1, c->vl_disp);
     if ((r = vl_cuda(c, cudaMemcpyAsync(c->h_vl, c->vl_disp, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream),
                      "copy")))
       return r;
@@ -497,7 +500,7 @@ int verlet_forces(nemd_ctx *c, float *F, int variant, double rc, double t) {
     k_vl_geo<<<1, 32, 0, c->stream>>>(c->geo, c->vl_geo, rc);
     if ((r = vl_cuda(c, cudaMemsetAsync(c->vl_disp, 0, sizeof(unsigned), c->stream), "memset"))) return r;
     k_vl_pos<<<nb, kVlThreads, 0, c->stream>>>(c->geo, c->vl_geo, c->q_dev, (int)n, c->vl_slot, c->vl_sb, c->vl_idx,
-                                               c->vl_pos, c->vl_res, c->vl_disp);
+                                               c->vl_pos, c->vl_pos + 1, c->vl_disp);
     c->launches += 2;
     c->vl_n = n;
     c->vl_tb = t;
@@ -513,7 +516,7 @@ int verlet_forces(nemd_ctx *c, float *F, int variant, double rc, double t) {
   const Pot pp = make_pot(c);
   if (nb + kFixupBlocks > c->cap_partials) return NEMD_ERR_CAPACITY;
 #define NEMD_VL_ARGS                                                                                         \
-  c->geo, c->vl_geo, c->vl_pos, c->vl_res, c->vl_cnt, c->vl_ent, c->vl_idx, (int)n, c->q_dev, pp, F, c->partials, \
+  c->geo, c->vl_geo, c->vl_pos, c->vl_pos + 1, c->vl_cnt, c->vl_ent, c->vl_idx, (int)n, c->q_dev, pp, F, c->partials, \
       c->pair_buf, c->pair_count, (long long)c->record_cap, c->recheck, c->nrecheck, &c->geo->error
   if (c->record_cap > 0)
     k_vl_force<true><<<nb, kVlThreads, 0, c->stream>>>(NEMD_VL_ARGS);
