@@ -237,7 +237,8 @@ int nemd_destroy(nemd_ctx *c) {
                   c->chunk_cnt, c->chunk_off, c->int_state, c->int_part, c->f_int};
   for (void *p : ptrs)
     if (p) cudaFree(p);
-  void *vptrs[] = {c->vl_cnt, c->vl_ent, c->vl_slot, c->vl_sb, c->vl_idx, c->vl_pos, c->vl_res, c->vl_geo, c->vl_disp};
+  void *vptrs[] = {c->vl_cnt, c->vl_ent, c->vl_slot, c->vl_sb, c->vl_idx, c->vl_pos, c->vl_res, c->vl_geo, c->vl_disp,
+                   c->fix_f, c->fix_uw};
   for (void *p : vptrs)
     if (p) cudaFree(p);
   if (c->h_vl) cudaFreeHost(c->h_vl);

@@ -197,21 +197,45 @@ __device__ __forceinline__ void publish_uw(Geo *__restrict__ g, const double (&s
   g->sticky |= g->error;
 }
 
+// Fixed-point scales of the fix-up's sums (per unit of eps): every deferred
+// pair lies within float32 rounding of rc, where |u| / eps and |r f| / eps are
+// O(1) for any rc >= 0.3 sigma, far inside 2^23 (energy, virial) and 2^31
+// (force) at these scales; the roundings (2^-41, 2^-33 per pair) are far
+// below float32.  Integer sums do not depend on the order of the additions.
+constexpr double kFixUW = 1099511627776.0;   // 2^40
+constexpr double kFixF = 4294967296.0;       // 2^32
+
+__device__ __forceinline__ unsigned long long to_fix(double x, double scale) {
+  return (unsigned long long)__double2ll_rn(x * scale);
+}
+__device__ __forceinline__ double from_fix(unsigned long long x, double iscale) {
+  return (double)(long long)x * iscale;
+}
+
 // Float64 fix-up of the candidates the force kernels left within float32
 // rounding of rc: the canonical decision (Sec. 2 images, strict r < rc), and for
-// each accepted pair the force on i (added to F, Cartesian), half of u and of
-// r (x) f (the other half comes from the pair's other orientation, which the
-// full neighbourhood also defers), written as one more block of partials per
-// block in the variant's frame.  Runs after the force kernel.
+// each accepted pair the force on i (Cartesian), half of u and of r (x) f (the
+// other half comes from the pair's other orientation, which the full
+// neighbourhood also defers), in the variant's frame.  The force kernels append
+// the candidates in no fixed order, so their sums are formed in 64-bit fixed
+// point (exact, order-free): U, W and the pair count summed over all blocks in
+// fix_uw, forces per particle in fix_f; the last block converts each total
+// once (adding U and W to the force kernel's partials, summed in block order,
+// and each particle's force to F), taking it by an atomic exchange that also
+// returns the scratch to zero.  Runs after the force kernel.
 __global__ void __launch_bounds__(256) k_recheck_fixup(Geo *__restrict__ g, const int4 *__restrict__ list,
                                                        const int *__restrict__ count, const float4 *__restrict__ pos,
                                                        const double *__restrict__ q, Pot pp, float *__restrict__ F,
+                                                       unsigned long long *__restrict__ fix_f,
+                                                       unsigned long long *__restrict__ fix_uw,
                                                        double *__restrict__ partials, int nforce, int half,
                                                        int frame_is_cartesian, double *__restrict__ uw,
                                                        unsigned long long *__restrict__ counters) {
   double *partial_slot = partials + (size_t)nforce * kPartials;
   double v[kPartials];
   for (int k = 0; k < kPartials; k++) v[k] = 0.0;
+  unsigned long long vf[8] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull};  // U, W (6), pairs
+  const double ie = 1.0 / pp.eps4d * 4.0;  // 1 / eps
   const int n = min(*count, kRecheckCap);
   const bool ok = !(g->error & (ERRB_BOX | ERRB_CAPACITY));
   // entries dealt round robin over the blocks, so that their float64 work
@@ -229,25 +253,25 @@ __global__ void __launch_bounds__(256) k_recheck_fixup(Geo *__restrict__ g, cons
     if (!(r2 < g->rc2)) continue;
     const double inv = 1.0 / r2, s2 = pp.sig2d * inv, s6 = s2 * s2 * s2;
     const double fr = pp.eps24d * inv * s6 * (2.0 * s6 - 1.0);
-    if (F)
+    if (F && fix_f)
       for (int a = 0; a < 3; a++) {
-        atomicAdd(&F[3 * (size_t)oi + a], (float)(-fr * d[a]));
+        atomicAdd(&fix_f[3 * (size_t)oi + a], to_fix(-fr * d[a] * ie, kFixF));
         // half neighbourhoods defer only one orientation of the pair
-        if (half) atomicAdd(&F[3 * (size_t)oj + a], (float)(fr * d[a]));
+        if (half) atomicAdd(&fix_f[3 * (size_t)oj + a], to_fix(fr * d[a] * ie, kFixF));
       }
     // frame components: W_frame = Q^T (d d^T) Q fr, d_frame = Q^T d
     double df[3];
     for (int a = 0; a < 3; a++) df[a] = g->Q[a] * d[0] + g->Q[3 + a] * d[1] + g->Q[6 + a] * d[2];
     if (g->variant != NEMD_DO)
       for (int a = 0; a < 3; a++) df[a] = d[a];
-    v[0] += pp.eps4d * s6 * (s6 - 1.0) - pp.ushiftd;
-    v[1] += fr * df[0] * df[0];
-    v[2] += fr * df[1] * df[1];
-    v[3] += fr * df[2] * df[2];
-    v[4] += fr * df[0] * df[1];
-    v[5] += fr * df[0] * df[2];
-    v[6] += fr * df[1] * df[2];
-    v[7] += 1.0;
+    vf[0] += to_fix((pp.eps4d * s6 * (s6 - 1.0) - pp.ushiftd) * ie, kFixUW);
+    vf[1] += to_fix(fr * df[0] * df[0] * ie, kFixUW);
+    vf[2] += to_fix(fr * df[1] * df[1] * ie, kFixUW);
+    vf[3] += to_fix(fr * df[2] * df[2] * ie, kFixUW);
+    vf[4] += to_fix(fr * df[0] * df[1] * ie, kFixUW);
+    vf[5] += to_fix(fr * df[0] * df[2] * ie, kFixUW);
+    vf[6] += to_fix(fr * df[1] * df[2] * ie, kFixUW);
+    vf[7] += 1ull;
   }
   // Block sum, in a fixed order: the warps' entry sums, then this block's slice
   // of the force kernel's partials (rows b, b + G, b + 2G, ..., G = gridDim.x;
@@ -255,16 +279,21 @@ __global__ void __launch_bounds__(256) k_recheck_fixup(Geo *__restrict__ g, cons
   constexpr int P = 24;
   __shared__ double shw[256 / 32][kPartials];
   __shared__ double shp[P][kPartials];
+  __shared__ unsigned long long shf[256 / 32][8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool any = __any_sync(0xffffffffu, has);
 #pragma unroll
   for (int k = 0; k < kPartials; k++) {
-    double x = v[k];
+    if (lane == 0) shw[warp][k] = 0.0;
+  }
+#pragma unroll
+  for (int k = 0; k < 8; k++) {
+    unsigned long long x = vf[k];
     if (any) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
     }
-    if (lane == 0) shw[warp][k] = any ? x : 0.0;
+    if (lane == 0) shf[warp][k] = any ? x : 0ull;
   }
   if (threadIdx.x < P * kPartials) {
     const int k = threadIdx.x % kPartials, pp0 = threadIdx.x / kPartials;
@@ -274,7 +303,14 @@ __global__ void __launch_bounds__(256) k_recheck_fixup(Geo *__restrict__ g, cons
     shp[pp0][k] = x;
   }
   __syncthreads();
+  if (threadIdx.x < 8) {
+    // the deferred pairs' fixed-point sums, added exactly to the totals of all blocks
+    unsigned long long f = 0ull;
+    for (int w = 0; w < 256 / 32; w++) f += shf[w][threadIdx.x];
+    if (f) atomicAdd(&fix_uw[threadIdx.x], f);
+  }
   if (threadIdx.x < kPartials) {
+    // this block's slice of the force partials in a fixed order
     double x = 0.0;
     for (int w = 0; w < 256 / 32; w++) x += shw[w][threadIdx.x];
     for (int p = 0; p < P; p++) x += shp[p][threadIdx.x];
@@ -290,9 +326,27 @@ __global__ void __launch_bounds__(256) k_recheck_fixup(Geo *__restrict__ g, cons
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // each deferred particle's fixed-point force total, taken once and added to F
+  if (F && fix_f && ok) {
+    const double eps = pp.eps4d * 0.25;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const int4 it = list[e];
+      const int ps[2] = {__float_as_int(pos[it.x].w), __float_as_int(pos[it.y].w)};
+      for (int h = 0; h < (half ? 2 : 1); h++)
+        for (int a = 0; a < 3; a++) {
+          const unsigned long long x = atomicExch(&fix_f[3 * (size_t)ps[h] + a], 0ull);
+          if (x) F[3 * (size_t)ps[h] + a] += (float)(from_fix(x, 1.0 / kFixF) * eps);
+        }
+    }
+  }
   if (threadIdx.x < kPartials) {
     double x = 0.0;
     for (int b = 0; b < (int)gridDim.x; b++) x += __ldcg(&partial_slot[(size_t)b * kPartials + threadIdx.x]);
+    // then the deferred pairs' exact totals, each converted once
+    if (threadIdx.x < 8) {
+      const unsigned long long f = atomicExch(&fix_uw[threadIdx.x], 0ull);
+      x += threadIdx.x < 7 ? from_fix(f, 1.0 / kFixUW) * (pp.eps4d * 0.25) : (double)(long long)f;
+    }
     tot[threadIdx.x] = x;
   }
   __syncthreads();
@@ -401,8 +455,26 @@ cudaError_t launch_recheck_fixup(nemd_ctx *c, float *F_dev, double *UW_dev, int 
                                  bool frame_is_cartesian) {
   int nfix = kFixupBlocks;
   if (nblocks + nfix > c->cap_partials) nfix = (int)(c->cap_partials - nblocks);
+  if (!c->fix_uw) {
+    cudaError_t e = cudaMalloc((void **)&c->fix_uw, 8 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->fix_uw, 0, 8 * sizeof(unsigned long long), c->stream);
+    if (e != cudaSuccess) return e;
+  }
+  if (F_dev && c->fix_cap < c->n) {
+    // the fixed-point force scratch, zero from the start (the fix-up returns
+    // every slot it touches to zero)
+    if (c->fix_f) cudaFree(c->fix_f);
+    c->fix_f = nullptr;
+    c->fix_cap = 0;
+    const size_t bytes = sizeof(unsigned long long) * 3 * (size_t)std::max<int64_t>(c->n, 1);
+    cudaError_t e = cudaMalloc((void **)&c->fix_f, bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->fix_f, 0, bytes, c->stream);
+    if (e != cudaSuccess) return e;
+    c->fix_cap = c->n;
+  }
   k_recheck_fixup<<<nfix, 256, 0, c->stream>>>(c->geo, c->recheck, c->nrecheck, c->pos4, c->q_dev, make_pot(c),
-                                               F_dev, c->partials, nblocks, half ? 1 : 0,
+                                               F_dev, F_dev ? c->fix_f : nullptr, c->fix_uw, c->partials, nblocks,
+                                               half ? 1 : 0,
                                                frame_is_cartesian ? 1 : 0, UW_dev, c->counters);
   c->launches += 1;
   return cudaGetLastError();

@@ -209,6 +209,9 @@ struct nemd_ctx {
   double *partials;
   int64_t cap_partials;
   double *uw_out;        // device U (1) + W (9)
+  unsigned long long *fix_f;  // 3 per particle: the fix-up's forces in 64-bit fixed point (kept zero between uses)
+  unsigned long long *fix_uw; // 8: the fix-up's U, W and pair count in fixed point (kept zero between uses)
+  int64_t fix_cap;            // particles fix_f holds
   float *f_dev;          // internal F buffer (host outputs)
   int32_t *pair_buf;
   unsigned long long *pair_count;
