@@ -211,9 +211,11 @@ int nemd_integrate(nemd_ctx *ctx, double *q, double *p, int64_t n, double t0, do
  * and the library's list kernel), evaluates only those at the following steps
  * (same pair decision, forces, energy and virial as the cell-list path), and
  * rebuilds the list when a pair outside it could have come within rc:
- *     exp(-|A|_F (t - t_b)) (rc + skin) - 2 delta < rc,
- * t_b the time of the build and delta the largest peculiar displacement
- * |L(t) u_i| since it (measured in the deformed frame), and at every remap.
+ *     exp(mu (t - t_b)) (rc + skin) - 2 delta < rc,
+ * t_b the time of the build, mu <= 0 the smallest eigenvalue of (A + A^T)/2
+ * (the flow shrinks no distance faster than exp(mu t)) and delta the largest
+ * peculiar displacement |L(t) u_i| since the build (measured in the deformed
+ * frame), and at every remap.
  * Positions are wrapped at every step; the images of the listed pairs follow
  * the wraps.  The rebuild decision is taken on the host (one synchronisation
  * per step), so these steps are launched rather than replayed as a graph.

@@ -15,12 +15,15 @@ equilibrium list does not:
   (the fractional coordinates of a particle change only by its peculiar
   displacement, so m_i is the integer nearest to s_i(build) - s_i(t));
 * deformation: between remaps L(t) = exp(A (t - t_b)) L(t_b), which stretches
-  or compresses every displacement d_b of the build to F d_b, |F d_b| >=
-  exp(-|A|_F (t - t_b)) |d_b|.  A pair not in the list had |d_b| >= rc + skin,
-  so at time t it is at least exp(-|A|_F (t - t_b)) (rc + skin) - 2 delta away,
-  delta the largest peculiar displacement |L(t) u_i| since the build.  The list
-  is rebuilt when that bound falls below rc, and at every remap (L jumps to
-  L M^-1, and the images of the list no longer mean the same lattice vectors).
+  or compresses every displacement d_b of the build to F d_b with
+  d|F d_b|^2/dt = 2 (F d_b)^T A (F d_b) >= 2 mu |F d_b|^2, mu the smallest
+  eigenvalue of the symmetric part (A + A^T)/2, so |F d_b| >=
+  exp(mu (t - t_b)) |d_b| (mu <= 0 for an incompressible flow).  A pair not in
+  the list had |d_b| >= rc + skin, so at time t it is at least
+  exp(mu (t - t_b)) (rc + skin) - 2 delta away, delta the largest peculiar
+  displacement |L(t) u_i| since the build.  The list is rebuilt when that
+  bound falls below rc, and at every remap (L jumps to L M^-1, and the images
+  of the list no longer mean the same lattice vectors).
 
 Pairs are decided by the canonical expression of the force oracle (Sec. 2:
 d = (q'_j - q'_i) + L n with q' = L frac(L^-1 q), r^2 < rc^2), evaluated in
@@ -51,7 +54,9 @@ class SkinList:
     def __init__(self, rc, skin, A):
         self.rc = float(rc)
         self.skin = float(skin)
-        self.anorm = float(np.linalg.norm(np.asarray(A, dtype=np.float64)))   # Frobenius
+        A = np.asarray(A, dtype=np.float64)
+        # slowest contraction rate of the flow: the smallest eigenvalue of (A + A^T)/2
+        self.mu = min(float(np.linalg.eigvalsh(0.5 * (A + A.T)).min()), 0.0)
         self.pairs = None
         self.builds = 0
 
@@ -77,7 +82,7 @@ class SkinList:
     def must_rebuild(self, L, Linv, q, t, remapped):
         if self.pairs is None or remapped:
             return True
-        sigma = math.exp(-self.anorm * (float(t) - self.tb))
+        sigma = math.exp(self.mu * (float(t) - self.tb))
         return sigma * (self.rc + self.skin) - 2.0 * self.displacement(L, Linv, q) < self.rc * (1.0 + 1e-12)
 
     def pairs_at(self, L, Linv, q):

@@ -10,11 +10,12 @@
 //   displacement, so the lattice vector m_i the wrap has moved particle i by
 //   since the build is the integer nearest to s_i(build) - s_i(t), and a
 //   listed pair (i, j, n) is the pair (i, j, n + m_j - m_i) at time t;
-// * deformation: until the next remap L(t) = exp(A (t - t_b)) L(t_b), so a
-//   pair at distance |d_b| >= rl at the build is at least
-//   exp(-|A|_F (t - t_b)) rl - 2 delta away at t, delta the largest peculiar
-//   displacement |L(t) u_i|.  The host rebuilds when that falls below rc, and
-//   at every remap.
+// * deformation: until the next remap L(t) = exp(A (t - t_b)) L(t_b), and
+//   d|F x|^2/dt = 2 (F x)^T A (F x) >= 2 mu |F x|^2 (F = exp(A (t - t_b)), mu
+//   the smallest eigenvalue of the symmetric part of A), so a pair at
+//   distance |d_b| >= rl at the build is at least exp(mu (t - t_b)) rl - 2 delta
+//   away at t, delta the largest peculiar displacement |L(t) u_i|.  The host
+//   rebuilds when that falls below rc, and at every remap.
 //
 // Every listed pair carries the integer offset k between the cells of its two
 // particles in a dynamic size grid of the build (cells at least rl wide),
@@ -416,6 +417,36 @@ int vl_reserve(nemd_ctx *c, int64_t n) {
 
 }  // namespace
 
+// Smallest eigenvalue of the symmetric 3x3 matrix (A + A^T)/2 (cyclic Jacobi
+// rotations; float64, host), at most 0: the slowest contraction rate of the flow.
+double flow_contraction_rate(const double *A) {
+  double S[3][3];
+  for (int a = 0; a < 3; a++)
+    for (int b = 0; b < 3; b++) S[a][b] = 0.5 * (A[3 * a + b] + A[3 * b + a]);
+  for (int sweep = 0; sweep < 50; sweep++) {
+    const double off = S[0][1] * S[0][1] + S[0][2] * S[0][2] + S[1][2] * S[1][2];
+    if (off < 1e-30 * (S[0][0] * S[0][0] + S[1][1] * S[1][1] + S[2][2] * S[2][2]) + 1e-300) break;
+    for (int p = 0; p < 2; p++)
+      for (int q = p + 1; q < 3; q++) {
+        if (S[p][q] == 0.0) continue;
+        const double th = 0.5 * (S[q][q] - S[p][p]) / S[p][q];
+        const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < 3; k++) {  // columns p, q
+          const double kp = S[k][p], kq = S[k][q];
+          S[k][p] = c * kp - s * kq;
+          S[k][q] = s * kp + c * kq;
+        }
+        for (int k = 0; k < 3; k++) {  // rows p, q
+          const double pk = S[p][k], qk = S[q][k];
+          S[p][k] = c * pk - s * qk;
+          S[q][k] = s * pk + c * qk;
+        }
+      }
+  }
+  return std::min(std::min(std::min(S[0][0], S[1][1]), S[2][2]), 0.0);
+}
+
 // Forces (into F) of the state the integrator has set (lattice at time t,
 // positions c->q_dev) from the Verlet list, rebuilding it first when needed.
 // Synchronises once per call (the displacement check).
@@ -445,8 +476,8 @@ int verlet_forces(nemd_ctx *c, float *F, int variant, double rc, double t) {
     float delta;
     memcpy(&delta, c->h_vl, sizeof delta);
     c->vl_delta = delta;
-    // a pair outside the list is at least exp(-|A| (t - t_b)) rl - 2 delta away
-    const double sigma = exp(-anorm * (t - c->vl_tb));
+    // a pair outside the list is at least exp(mu (t - t_b)) rl - 2 delta away
+    const double sigma = exp(flow_contraction_rate(c->A) * (t - c->vl_tb));
     rebuild = !(sigma * rl - 2.0 * (double)delta >= rc * (1.0 + 1e-9));
   }
   if (rebuild) {
