@@ -5,6 +5,20 @@
 
 namespace nemd {
 
+// Verlet list packing: a 10-bit signed field per component (brick images) and
+// an 8-bit signed cell offset per component of a list entry.
+__device__ __forceinline__ int vl_pack3(int x, int y, int z) {
+  return (x & 1023) | ((y & 1023) << 10) | ((z & 1023) << 20);
+}
+__device__ __forceinline__ int vl_unpack3(int v, int a) {  // sign-extended 10-bit field a
+  const int f = (v >> (10 * a)) & 1023;
+  return f >= 512 ? f - 1024 : f;
+}
+__device__ __forceinline__ int vl_pack_k(int x, int y, int z) {
+  return (x & 255) | ((y & 255) << 8) | ((z & 255) << 16);
+}
+__device__ __forceinline__ int vl_unpack_k(int v, int a) { return (int)(signed char)((v >> (8 * a)) & 255); }
+
 __device__ __forceinline__ int floordiv_dev(int a, int b) {
   int q = a / b;
   if ((a % b != 0) && ((a < 0) != (b < 0))) q--;

@@ -44,16 +44,7 @@ constexpr int kVlThreads = 128;
 // (vl_pos[2k], vl_pos[2k + 1]): a gather of both touches one sector.
 constexpr int kVlRec = 2;
 
-__device__ __forceinline__ int pack3(int x, int y, int z) {
-  return (x & 1023) | ((y & 1023) << 10) | ((z & 1023) << 20);
-}
-__device__ __forceinline__ int unpack3(int v, int a) {  // sign-extended 10-bit field a
-  const int f = (v >> (10 * a)) & 1023;
-  return f >= 512 ? f - 1024 : f;
-}
-// cell offsets fit 8 bits each
-__device__ __forceinline__ int pack_k(int x, int y, int z) { return (x & 255) | ((y & 255) << 8) | ((z & 255) << 16); }
-__device__ __forceinline__ int unpack_k(int v, int a) { return (int)(signed char)((v >> (8 * a)) & 255); }
+
 
 // The list's grid at the build: c_a = floor(h_a / rl) cells along lattice
 // direction a (at least 1).
@@ -82,7 +73,7 @@ __global__ void k_vl_init(const Geo *__restrict__ g, const double *__restrict__ 
   if (g->variant == NEMD_DO) brick_image(g, q, oi, m);
   for (int a = 0; a < 3; a++) sb[3 * (size_t)k + a] = s[a];
   idx[k] = make_int4(min((int)floor(s[0] * c[0]), c[0] - 1), min((int)floor(s[1] * c[1]), c[1] - 1),
-                     min((int)floor(s[2] * c[2]), c[2] - 1), pack3(m[0], m[1], m[2]));
+                     min((int)floor(s[2] * c[2]), c[2] - 1), vl_pack3(m[0], m[1], m[2]));
   slot[oi] = k;
 }
 
@@ -133,13 +124,13 @@ __global__ void __launch_bounds__(kVlThreads) k_vl_build(
             const int4 jj = idx[j];
             int n1 = kx, n2 = R.ky, n3 = R.kz;
             if (dyn_offset) {  // brick images: n = k + m_i - m_j
-              n1 += unpack3(ii.w, 0) - unpack3(jj.w, 0);
-              n2 += unpack3(ii.w, 1) - unpack3(jj.w, 1);
-              n3 += unpack3(ii.w, 2) - unpack3(jj.w, 2);
+              n1 += vl_unpack3(ii.w, 0) - vl_unpack3(jj.w, 0);
+              n2 += vl_unpack3(ii.w, 1) - vl_unpack3(jj.w, 1);
+              n3 += vl_unpack3(ii.w, 2) - vl_unpack3(jj.w, 2);
             }
             if (e < maxk)
               ent[(size_t)e * n + k] =
-                  make_int2(j, pack_k(jj.x - ii.x + c0 * n1, jj.y - ii.y + c1 * n2, jj.z - ii.z + c2 * n3));
+                  make_int2(j, vl_pack_k(jj.x - ii.x + c0 * n1, jj.y - ii.y + c1 * n2, jj.z - ii.z + c2 * n3));
           }
           e++;
         }
@@ -268,7 +259,7 @@ __global__ void __launch_bounds__(kVlThreads) k_vl_pos(const Geo *__restrict__ g
       R[a] = __fadd_rn(__fsub_rn(p.hi, X[a]), p.lo);
     }
     pos[kVlRec * (size_t)k] = make_float4(X[0], X[1], X[2], __int_as_float(i));
-    res[kVlRec * (size_t)k] = make_float4(R[0], R[1], R[2], __int_as_float(pack3(m[0], m[1], m[2])));
+    res[kVlRec * (size_t)k] = make_float4(R[0], R[1], R[2], __int_as_float(vl_pack3(m[0], m[1], m[2])));
   }
   // largest displacement of the block (positive floats order as their bits)
   for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
@@ -323,7 +314,7 @@ __global__ void __launch_bounds__(kVlThreads, NEMD_VL_MINBLOCKS) k_vl_force(
       if (e0 + h >= ne) break;
       const int2 en = eu[h];
       const int j = en.x;
-      const float k0 = (float)unpack_k(en.y, 0), k1 = (float)unpack_k(en.y, 1), k2 = (float)unpack_k(en.y, 2);
+      const float k0 = (float)vl_unpack_k(en.y, 0), k1 = (float)vl_unpack_k(en.y, 1), k2 = (float)vl_unpack_k(en.y, 2);
       const float4 pj = pu[h];
       // quantised part: exact (every term a multiple of the quantum, bounded)
       const float dx = (pj.x - pi.x) + ((Gq[0] * k0 + Gq[1] * k1) + Gq[2] * k2);
@@ -343,12 +334,12 @@ __global__ void __launch_bounds__(kVlThreads, NEMD_VL_MINBLOCKS) k_vl_force(
       if (band || RECORD) {
         // the pair's canonical image: n = (k - idx_j + idx_i) / c, plus m_j - m_i
         const int4 ii = idx[k], jj = idx[j];
-        nn[0] = (unpack_k(en.y, 0) - jj.x + ii.x) / vg->c[0] + unpack3(__float_as_int(rj.w), 0) -
-                unpack3(__float_as_int(ri.w), 0);
-        nn[1] = (unpack_k(en.y, 1) - jj.y + ii.y) / vg->c[1] + unpack3(__float_as_int(rj.w), 1) -
-                unpack3(__float_as_int(ri.w), 1);
-        nn[2] = (unpack_k(en.y, 2) - jj.z + ii.z) / vg->c[2] + unpack3(__float_as_int(rj.w), 2) -
-                unpack3(__float_as_int(ri.w), 2);
+        nn[0] = (vl_unpack_k(en.y, 0) - jj.x + ii.x) / vg->c[0] + vl_unpack3(__float_as_int(rj.w), 0) -
+                vl_unpack3(__float_as_int(ri.w), 0);
+        nn[1] = (vl_unpack_k(en.y, 1) - jj.y + ii.y) / vg->c[1] + vl_unpack3(__float_as_int(rj.w), 1) -
+                vl_unpack3(__float_as_int(ri.w), 1);
+        nn[2] = (vl_unpack_k(en.y, 2) - jj.z + ii.z) / vg->c[2] + vl_unpack3(__float_as_int(rj.w), 2) -
+                vl_unpack3(__float_as_int(ri.w), 2);
       }
       if (band) {
         if (RECORD)
