@@ -452,7 +452,7 @@ def section_main(args, rank, world, dev, torch, nemd, W):
     choice = tune["choice"] if tune is not None else {"kernel": args.kernel, "group": args.group,
                                                       "cell_factor": args.kfac}
     pipe = []
-    for k in range(K):
+    for _ in range(K):
         st = torch.cuda.Stream(dev)
         c = nemd.Context(dev.index, stream=st.cuda_stream)
         c.set_flow(ser.A, ser.L0, ser.M, ser.period)
@@ -502,9 +502,9 @@ def section_main(args, rank, world, dev, torch, nemd, W):
     clk = clocks.stop()
     launches = sum(c.stats()["launches"] for c, _, _ in pipe) - launches0
     # each context's last strain gave the pairs of the untimed pass
-    for k, (c, _, _) in enumerate(pipe):
+    for kc, (c, _, _) in enumerate(pipe):
         c.sync()
-        last = max(i for i in range(S) if i % K == k) if k < S else None
+        last = max(i for i in range(S) if i % K == kc) if kc < S else None
         if last is not None:
             assert c.stats()["pairs"] == per["tuned"]["pairs"][last], "pipelined pairs differ"
     kernel_name = {0: "k_force_plain", 1: "k_force_chunk", 2: "k_force_warp", 3: "k_force_warp (half)",
