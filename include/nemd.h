@@ -138,7 +138,11 @@ typedef struct nemd_stats {
 
 /* Create a context on CUDA device `device`, issuing all work on `stream`
  * (a cudaStream_t; NULL means the legacy default stream).  *ctx receives the
- * handle.  Returns NEMD_ERR_CUDA if the device cannot be used. */
+ * handle.  Returns NEMD_ERR_CUDA if the device cannot be used.  Contexts are
+ * independent: several contexts on several streams may evaluate independent
+ * states at the same time (one context's setup kernels then run beside
+ * another's force kernel), with results equal bit for bit to evaluating the
+ * states one after another. */
 int nemd_create(nemd_ctx **ctx, int device, void *stream);
 
 /* Release all library-owned memory.  Safe on NULL. */
@@ -176,7 +180,10 @@ int nemd_build_cells(nemd_ctx *ctx, int variant, double rc);
  *   U: 1 float64, sum over unordered pairs of u(r);
  *   W: 9 float64 row-major, sum over unordered pairs of r_ij (x) f_ij with
  *      r_ij = q_i - (q_j + L n) and f_ij the force on i from j.
- * Any of F, U, W may be NULL to skip it. */
+ * Any of F, U, W may be NULL to skip it.  Every sum is formed in a fixed order
+ * (the pairs within float32 rounding of rc, decided in float64, in 64-bit
+ * fixed point), so a state gives the same F, U and W bit for bit from run to
+ * run with the same kernel options (kernel 3 excepted, see NEMD_OPT_KERNEL). */
 int nemd_compute_forces(nemd_ctx *ctx, float *F, double *U, double *W);
 
 /* Time integration under the flow (Sec. 2.1: a particle (q, p) has images
@@ -440,7 +447,11 @@ int nemd_batch_set_state(nemd_batch *b, const double *q, const double *t);
  * order), UW -- nsys x 10 float64 (U, then W row-major); each host or device
  * pointer, or NULL to skip.  Asynchronous for device outputs; with a host
  * output it synchronises before it returns.  A system whose step failed (see
- * nemd_batch_sync) gets U = W = 0 and unspecified forces. */
+ * nemd_batch_sync) gets U = W = 0 and unspecified forces.  Sums are formed in
+ * a fixed order except for the pairs within float32 rounding of rc (decided in
+ * float64 and added with float atomics): a particle with two or more of those
+ * in one step can make its system's F, U, W differ in the last bit between
+ * runs. */
 int nemd_batch_compute(nemd_batch *b, float *F, double *UW);
 
 /* Wait for the stream; return the first failing system's status (0 = all
