@@ -138,9 +138,9 @@ cudaError_t enqueue_step(nemd_batch *b, cudaStream_t st) {
   return nemd::launch_batch_finish(st, v);
 }
 
-// lattice, grid, stencil, bin (wrap, 3 scan, scatter, sort, pack), chunks
+// lattice, grid, stencil, bin (wrap, 3 scan, scatter, rank-and-pack), chunks
 // (count, 3 scan, write), force, fix-up, reduce
-constexpr int64_t kStepLaunches = 3 + 7 + 5 + 1 + 2;
+constexpr int64_t kStepLaunches = 3 + 6 + 5 + 1 + 2;
 
 }  // namespace
 
@@ -615,7 +615,7 @@ int nemd_batch_autotune(nemd_batch *b, int reps, nemd_tune_entry *times, int cap
     cudaEventElapsedTime(&ms, e0, e1);
     const double mean = (double)ms / reps;
     if (times && nt < cap) {
-      times[nt].cfg.kernel = 2;
+      times[nt].cfg.kernel = b->force_kernel;
       times[nt].cfg.group = cand[k][1];
       times[nt].cfg.cell_factor = cand[k][0];
       times[nt].cfg.pad = 0;

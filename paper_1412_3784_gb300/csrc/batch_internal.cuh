@@ -71,7 +71,7 @@ cudaError_t launch_batch_lattice(cudaStream_t st, Geo *geo, const LatIn *lat, co
 cudaError_t launch_batch_grid(cudaStream_t st, Geo *geo, const GridIn *grid, const SysInfo *sys, int count);
 // lattice.cu: rows of every class of every system
 cudaError_t launch_batch_stencil(cudaStream_t st, const BatchView &v, int max_clcap);
-// bin.cu: wrap, scan, scatter, per-cell sort, pack
+// bin.cu: wrap, scan, scatter, rank within the cell and pack
 cudaError_t launch_batch_bin(cudaStream_t st, const BatchView &v, int sms);
 // bin.cu: exclusive scan of in[0..len) into out[0..len], out[len] = total
 cudaError_t launch_fixed_scan(cudaStream_t st, const int *in, int *out, int *tiles, int len);

@@ -9,12 +9,14 @@
 //               cell centre in the variant's frame as a float32 multiple of the
 //               step's quantum plus a float32 residual, rank = atomicAdd(count[cell])
 //   k_scan_*    exclusive scan of the per-cell counts -> start[]
-//   k_scatter   perm[start[cell] + rank] = i, and its kappa in the same slot of cell_sorted
-//   k_cellsort  per cell, particles in increasing kappa (the coordinate along
-//               the x-row of cells), ties by input index: the order depends
-//               only on the positions, so sums are reproducible from run to
-//               run, and every x-row of cells is one kappa-sorted run
-//   k_pack      sorted float4 {rel position, input index}, {residual, kappa}, cell ids
+//   k_scatter   perm[start[cell] + rank] = i (cells contiguous, arrival order within)
+//   k_rankpack  per slot, the particle's place in its cell in increasing kappa
+//               (the coordinate along the x-row of cells), ties by input index
+//               -- its rank among the cell's particles -- and the sorted
+//               float4 {rel position, input index}, {residual, kappa} and cell
+//               id written there: the order depends only on the positions, so
+//               sums are reproducible from run to run, and every x-row of
+//               cells is one kappa-sorted run
 #include <math.h>
 
 #include "batch_internal.cuh"
@@ -213,150 +215,71 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_add(const Geo *g, int *__
   if (blockIdx.x == 0 && threadIdx.x == 0) start[ncells] = n;
 }
 
-// perm[start[cell] + rank] = i, and the particle's sort key kappa in the same
-// slot of cell_sorted (overwritten with the cell ids by the sort-and-pack).
-__device__ __forceinline__ void scatter_body(const float4 *__restrict__ relc, const float4 *__restrict__ relr,
-                                             const int *__restrict__ rank, const int *__restrict__ start,
-                                             int *__restrict__ perm, int *__restrict__ key_slot, int i) {
+// perm[start[cell] + rank] = i.
+__device__ __forceinline__ void scatter_body(const float4 *__restrict__ relc, const int *__restrict__ rank,
+                                             const int *__restrict__ start, int *__restrict__ perm, int i) {
   const int cell = __float_as_int(relc[i].w);
-  const int slot = start[cell] + rank[i];
-  perm[slot] = i;
-  key_slot[slot] = __float_as_int(relr[i].w);
+  perm[start[cell] + rank[i]] = i;
 }
 
-__global__ void k_scatter(const Geo *g, const float4 *__restrict__ relc, const float4 *__restrict__ relr,
-                          const int *__restrict__ rank, const int *__restrict__ start, int *__restrict__ perm,
-                          int *__restrict__ key_slot, int n) {
+__global__ void k_scatter(const Geo *g, const float4 *__restrict__ relc, const int *__restrict__ rank,
+                          const int *__restrict__ start, int *__restrict__ perm, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
-  scatter_body(relc, relr, rank, start, perm, key_slot, i);
+  scatter_body(relc, rank, start, perm, i);
 }
 
-// (kappa, input index) of particle i: the within-cell order.
+// (kappa, input index) of particle i: the within-cell order, a strict total
+// order (input indices are distinct).
 __device__ __forceinline__ bool sort_before(float ka, int ia, float kb, int ib) {
   return ka < kb || (ka == kb && ia < ib);
 }
 
-// One thread per cell: the cell's slots sorted by (kappa, input index) --
-// keys in the slots of cell_sorted, indices in perm, both contiguous per cell.
-// A cell of up to 32 particles is sorted in registers by a bitonic network of
-// the smallest power-of-two width that holds it (padded with keys that sort
-// last); a longer one in place by insertion.
-constexpr int kNet = 32;
-
-template <int K>
-__device__ __forceinline__ void cellsort_net(int *__restrict__ perm, int *__restrict__ key_slot, int b, int n) {
-  float key[K];
-  int idx[K];
+// Scattered slot u (cells contiguous, arrival order within a cell): particle
+// i = perm[u] goes to slot start[c] + (number of the cell's particles that sort
+// before it), which over the cell is a permutation of its slots -- the order
+// of a sort of the cell by (kappa, input index).  There it is packed: float4
+// {rel position, input index}, {residual, kappa} and its cell id.  Every
+// thread of a cell reads the cell's keys (kappa of particle perm[v] is
+// relr[perm[v]].w): a few dozen reads at most, shared through L1.
+__device__ __forceinline__ void rankpack_body(const float4 *__restrict__ relc, const float4 *__restrict__ relr,
+                                              const int *__restrict__ perm, const int *__restrict__ start,
+                                              float4 *__restrict__ pos4, float4 *__restrict__ posr,
+                                              int *__restrict__ cell_sorted, int u) {
+  const int i = perm[u];
+  const float4 r = relc[i], rr = relr[i];
+  const int c = __float_as_int(r.w);
+  const int b = start[c], e = start[c + 1];
+  const float *kap = reinterpret_cast<const float *>(relr) + 3;  // kappa of particle j: kap[4 j]
+  int k = b;
+  int v = b;
+  for (; v + 4 <= e; v += 4) {
+    int iv[4];
+    float kv[4];
 #pragma unroll
-  for (int t = 0; t < K; t++) {
-    key[t] = t < n ? __int_as_float(key_slot[b + t]) : INFINITY;
-    idx[t] = t < n ? perm[b + t] : 0x7fffffff;
-  }
+    for (int h = 0; h < 4; h++) iv[h] = perm[v + h];
 #pragma unroll
-  for (int k = 2; k <= K; k <<= 1) {
+    for (int h = 0; h < 4; h++) kv[h] = __ldg(kap + 4 * (size_t)iv[h]);
 #pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-#pragma unroll
-      for (int i = 0; i < K; i++) {
-        const int l = i ^ j;
-        if (l > i) {
-          const bool up = (i & k) == 0;
-          const bool swap = up ? sort_before(key[l], idx[l], key[i], idx[i]) : sort_before(key[i], idx[i], key[l], idx[l]);
-          const float ka = key[i], kb = key[l];
-          const int ia = idx[i], ib = idx[l];
-          key[i] = swap ? kb : ka;
-          key[l] = swap ? ka : kb;
-          idx[i] = swap ? ib : ia;
-          idx[l] = swap ? ia : ib;
-        }
-      }
-    }
+    for (int h = 0; h < 4; h++) k += sort_before(kv[h], iv[h], rr.w, i);
   }
-#pragma unroll
-  for (int t = 0; t < K; t++)
-    if (t < n) {
-      key_slot[b + t] = __float_as_int(key[t]);
-      perm[b + t] = idx[t];
-    }
-}
-
-// wn: the largest cell of the calling warp (one network width per warp: no
-// divergence between widths).
-__device__ __forceinline__ void cellsort_body(const int *__restrict__ start, int *__restrict__ perm,
-                                              int *__restrict__ key_slot, int c, int wn) {
-  const int b = start[c], e = start[c + 1], n = e - b;
-  if (n <= 1) return;
-  if (wn <= 2) {
-    const int k0 = key_slot[b], k1 = key_slot[b + 1], i0 = perm[b], i1 = perm[b + 1];
-    if (sort_before(__int_as_float(k1), i1, __int_as_float(k0), i0)) {
-      key_slot[b] = k1;
-      key_slot[b + 1] = k0;
-      perm[b] = i1;
-      perm[b + 1] = i0;
-    }
-    return;
+  for (; v < e; v++) {
+    const int iv = perm[v];
+    k += sort_before(__ldg(kap + 4 * (size_t)iv), iv, rr.w, i);
   }
-  if (wn <= 4) return cellsort_net<4>(perm, key_slot, b, n);
-  if (wn <= 8) return cellsort_net<8>(perm, key_slot, b, n);
-  if (wn <= 16) return cellsort_net<16>(perm, key_slot, b, n);
-  if (n <= kNet) return cellsort_net<kNet>(perm, key_slot, b, n);
-  for (int k = b + 1; k < e; k++) {
-    const int kbits = key_slot[k];
-    const float kv = __int_as_float(kbits);
-    const int iv = perm[k];
-    int u = k - 1;
-    while (u >= b) {
-      const int ubits = key_slot[u];
-      const int iu = perm[u];
-      if (!sort_before(kv, iv, __int_as_float(ubits), iu)) break;
-      key_slot[u + 1] = ubits;
-      perm[u + 1] = iu;
-      u--;
-    }
-    key_slot[u + 1] = kbits;
-    perm[u + 1] = iv;
-  }
-}
-
-// Cells [0, ncells) a thread each, in warp-aligned strides (each warp's
-// network width from its largest cell).
-__device__ __forceinline__ void cellsort_cells(const int *__restrict__ start, int *__restrict__ perm,
-                                               int *__restrict__ key_slot, int ncells) {
-  const int lane = threadIdx.x & 31;
-  for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < ncells; base += gridDim.x * blockDim.x) {
-    const int c = base + lane;
-    const int n = c < ncells ? start[c + 1] - start[c] : 0;
-    const int wn = __reduce_max_sync(0xffffffffu, n);
-    if (c < ncells) cellsort_body(start, perm, key_slot, c, wn);
-  }
-}
-
-__global__ void k_cellsort(const Geo *g, const int *__restrict__ start, int *__restrict__ perm,
-                           int *__restrict__ key_slot) {
-  if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
-  cellsort_cells(start, perm, key_slot, g->ncells);
-}
-
-// Sorted slot k: float4 {rel position, input index}, {residual, kappa}, cell id.
-__device__ __forceinline__ void pack_body(const float4 *__restrict__ relc, const float4 *__restrict__ relr,
-                                          const int *__restrict__ perm, float4 *__restrict__ pos4,
-                                          float4 *__restrict__ posr, int *__restrict__ cell_sorted, int k) {
-  const int i = perm[k];
-  const float4 r = relc[i];
   pos4[k] = make_float4(r.x, r.y, r.z, __int_as_float(i));
-  posr[k] = relr[i];
-  cell_sorted[k] = __float_as_int(r.w);
+  posr[k] = rr;
+  cell_sorted[k] = c;
 }
 
-__global__ void k_pack(const Geo *g, const float4 *__restrict__ relc, const float4 *__restrict__ relr,
-                       const int *__restrict__ perm, float4 *__restrict__ pos4, float4 *__restrict__ posr,
-                       int *__restrict__ cell_sorted, int n) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
+__global__ void k_rankpack(const Geo *g, const float4 *__restrict__ relc, const float4 *__restrict__ relr,
+                           const int *__restrict__ perm, const int *__restrict__ start, float4 *__restrict__ pos4,
+                           float4 *__restrict__ posr, int *__restrict__ cell_sorted, int n) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= n) return;
   if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
-  pack_body(relc, relr, perm, pos4, posr, cell_sorted, k);
+  rankpack_body(relc, relr, perm, start, pos4, posr, cell_sorted, u);
 }
 
 cudaError_t launch_bin(nemd_ctx *c) {
@@ -377,12 +300,9 @@ cudaError_t launch_bin(nemd_ctx *c) {
   if (n > 0) {
     const int tb = 256;
     const int nb = (n + tb - 1) / tb;
-    k_scatter<<<nb, tb, 0, c->stream>>>(c->geo, c->relc, c->relr, c->rank, c->start, c->perm, c->cell_sorted, n);
-    int64_t cb = (c->cap_cells + 255) / 256;
-    if (cb > 8 * (int64_t)c->sms) cb = 8 * (int64_t)c->sms;
-    k_cellsort<<<(int)cb, 256, 0, c->stream>>>(c->geo, c->start, c->perm, c->cell_sorted);
-    k_pack<<<nb, tb, 0, c->stream>>>(c->geo, c->relc, c->relr, c->perm, c->pos4, c->posr, c->cell_sorted, n);
-    c->launches += 1;
+    k_scatter<<<nb, tb, 0, c->stream>>>(c->geo, c->relc, c->rank, c->start, c->perm, n);
+    k_rankpack<<<nb, tb, 0, c->stream>>>(c->geo, c->relc, c->relr, c->perm, c->start, c->pos4, c->posr,
+                                         c->cell_sorted, n);
     c->launches += 2;
   }
   return cudaGetLastError();
@@ -472,19 +392,15 @@ __global__ void k_b_scatter(BatchView v) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= v.ntot) return;
   if (v.geo[v.sys_of[i]].error & (ERRB_BOX | ERRB_CAPACITY)) return;
-  scatter_body(v.relc, v.relr, v.rank, v.start, v.perm, v.cell_sorted, i);
+  scatter_body(v.relc, v.rank, v.start, v.perm, i);
 }
 
-// Every system's cells (the cell slots of all systems are one array).
-__global__ void k_b_cellsort(BatchView v) {
-  cellsort_cells(v.start, v.perm, v.cell_sorted, v.ncells);
-}
-
-// Sorted slots [0, start[ncells]): the particles of every system that binned.
-__global__ void k_b_pack(BatchView v) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= v.start[v.ncells]) return;
-  pack_body(v.relc, v.relr, v.perm, v.pos4, v.posr, v.cell_sorted, k);
+// Scattered slots [0, start[ncells]): the particles of every system that binned
+// (the cell slots of all systems are one array).
+__global__ void k_b_rankpack(BatchView v) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= v.start[v.ncells]) return;
+  rankpack_body(v.relc, v.relr, v.perm, v.start, v.pos4, v.posr, v.cell_sorted, u);
 }
 
 cudaError_t launch_batch_bin(cudaStream_t st, const BatchView &v, int sms) {
@@ -496,11 +412,8 @@ cudaError_t launch_batch_bin(cudaStream_t st, const BatchView &v, int sms) {
   e = launch_fixed_scan(st, v.count, v.start, v.tiles, v.ncells);
   if (e != cudaSuccess) return e;
   k_b_scatter<<<nb, tb, 0, st>>>(v);
-  int cb = (v.ncells + 255) / 256;
-  if (cb > 8 * sms) cb = 8 * sms;
-  if (cb < 1) cb = 1;
-  k_b_cellsort<<<cb, 256, 0, st>>>(v);
-  k_b_pack<<<nb, tb, 0, st>>>(v);
+  k_b_rankpack<<<nb, tb, 0, st>>>(v);
+  (void)sms;
   return cudaGetLastError();
 }
 

@@ -260,6 +260,22 @@ def test_ragged_counts_and_empty_cells(kernel):
         check_against(w, v, ref, kernel=kernel)
 
 
+@pytest.mark.parametrize("kernel", MAIN)
+def test_crowded_cells(kernel):
+    """A strained general-flow system with 200 of its particles packed into a
+    cube of side 3 (local density ~7): cells of 40 to 200 particles, well past
+    the 32 of a warp, beside cells of ordinary occupancy."""
+    w = W.config_general(t=0.3, k=8)
+    rng = np.random.default_rng(41)
+    q = w.q.copy()
+    q[:200] = q[500] + 3.0 * rng.random((200, 3))
+    w = W.Workload(name="crowded", A=w.A, L0=w.L0, M=w.M, T=w.T, t=w.t, q=q, kind=w.kind, rc=w.rc)
+    ref = oracle.evaluate(w, "brute", want_pairs=True)
+    for v in (DS, DO):
+        g = check_against(w, v, ref, kernel=kernel)
+        assert g["stats"]["pairs"] == ref.npairs
+
+
 # ------------------------------------------------------------ properties ----
 
 @pytest.mark.parametrize("kernel", DETERMINISTIC)
