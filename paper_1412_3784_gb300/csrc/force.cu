@@ -543,16 +543,31 @@ __global__ void __launch_bounds__(256) k_b_reduce(BatchView v) {
 #pragma unroll
   for (int k = 0; k < K; k++) a[k] = {0.f, 0.f};
   long long np = 0;
-  for (int k = b + threadIdx.x; k < e; k += blockDim.x) {
-    const float4 p0 = v.ppart[2 * (size_t)k], p1 = v.ppart[2 * (size_t)k + 1];
-    a[0] = ff_add(a[0], ff{p0.x, 0.f});
-    a[1] = ff_add(a[1], ff{p0.y, 0.f});
-    a[2] = ff_add(a[2], ff{p0.z, 0.f});
-    a[3] = ff_add(a[3], ff{p0.w, 0.f});
-    a[4] = ff_add(a[4], ff{p1.x, 0.f});
-    a[5] = ff_add(a[5], ff{p1.y, 0.f});
-    a[6] = ff_add(a[6], ff{p1.z, 0.f});
-    np += __float_as_int(p1.w);
+  // four particles' loads in flight before their sums (the same order of
+  // additions as one particle at a time)
+  constexpr int kAhead = 4;
+  for (int k0 = b + threadIdx.x; k0 < e; k0 += kAhead * blockDim.x) {
+    float4 p0[kAhead], p1[kAhead];
+#pragma unroll
+    for (int h = 0; h < kAhead; h++) {
+      const int k = k0 + h * blockDim.x;
+      if (k < e) {
+        p0[h] = v.ppart[2 * (size_t)k];
+        p1[h] = v.ppart[2 * (size_t)k + 1];
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < kAhead; h++) {
+      if (k0 + h * (int)blockDim.x >= e) break;
+      a[0] = ff_add(a[0], ff{p0[h].x, 0.f});
+      a[1] = ff_add(a[1], ff{p0[h].y, 0.f});
+      a[2] = ff_add(a[2], ff{p0[h].z, 0.f});
+      a[3] = ff_add(a[3], ff{p0[h].w, 0.f});
+      a[4] = ff_add(a[4], ff{p1[h].x, 0.f});
+      a[5] = ff_add(a[5], ff{p1[h].y, 0.f});
+      a[6] = ff_add(a[6], ff{p1[h].z, 0.f});
+      np += __float_as_int(p1[h].w);
+    }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll

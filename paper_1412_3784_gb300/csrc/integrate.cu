@@ -125,18 +125,34 @@ __global__ void __launch_bounds__(kIntThreads) k_int_p2(const double *__restrict
   block_p2(x, part);
 }
 
-// K0 = sum of the partials (block order); no rescale before the first kick
-__global__ void k_int_k0(double *st, const double *part, int nb) {
-  if (threadIdx.x != 0) return;
+// Sum of part[0..m) by all threads of one block in a fixed order: each thread
+// adds the partials b = tid, tid + blockDim, ... in turn, then the shuffle
+// tree of each warp and the warps' sums in warp order (a tree of depth
+// ~log2(m) instead of m dependent float64 adds).  The result is in thread 0.
+__device__ __forceinline__ double block_sum_fixed(const double *part, int m) {
+  __shared__ double sh[kIntThreads / 32];
   double y = 0.0;
-  for (int b = 0; b < nb; b++) y += part[b];
+  for (int b = threadIdx.x; b < m; b += blockDim.x) y += __ldcg(part + b);
+  for (int o = 16; o > 0; o >>= 1) y += __shfl_down_sync(0xffffffffu, y, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = y;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += sh[w];
+  return s;
+}
+
+// K0 = sum of the partials; no rescale before the first kick
+__global__ void __launch_bounds__(kIntThreads) k_int_k0(double *st, const double *part, int nb) {
+  const double y = block_sum_fixed(part, nb);
+  if (threadIdx.x != 0) return;
   st[kK0] = y;
   st[kScale] = 1.0;
 }
 
 // After every block has written its partial of sum |p|^2: the last block to
 // arrive (ticket in st, returned to zero) sets the rescale factor from the
-// partials in block order and, with tick, advances the clock one step,
+// partials (block_sum_fixed) and, with tick, advances the clock one step,
 // t = t0 + k dt (each operation rounded once).
 template <bool TICK>
 __device__ __forceinline__ void last_block_scale(double *st, const double *part) {
@@ -146,10 +162,10 @@ __device__ __forceinline__ void last_block_scale(double *st, const double *part)
   if (threadIdx.x == 0)
     last = atomicAdd(reinterpret_cast<unsigned long long *>(st + kTicket), 1ull) == (unsigned long long)(gridDim.x - 1);
   __syncthreads();
-  if (!last || threadIdx.x != 0) return;
+  if (!last) return;
   __threadfence();
-  double y = 0.0;
-  for (int b = 0; b < (int)gridDim.x; b++) y += __ldcg(part + b);
+  const double y = block_sum_fixed(part, (int)gridDim.x);
+  if (threadIdx.x != 0) return;
   st[kScale] = (st[kThermo] != 0.0 && y > 0.0) ? sqrt(st[kK0] / y) : 1.0;
   if (TICK) {
     const double k = st[kStep] + 1.0;
@@ -354,7 +370,7 @@ int nemd_integrate(nemd_ctx *c, double *q, double *p, int64_t n, double t0, doub
   do {
     if ((r = nemd_set_state(c, q, n, t0))) break;
     k_int_p2<<<nb, kIntThreads, 0, c->stream>>>(p, (int)n, c->int_part);
-    k_int_k0<<<1, 32, 0, c->stream>>>(c->int_state, c->int_part, nb);
+    k_int_k0<<<1, kIntThreads, 0, c->stream>>>(c->int_state, c->int_part, nb);
     c->launches += 2;
     if ((r = int_forces(c, variant, rc, t0))) break;
     int64_t k = 0;
