@@ -102,6 +102,9 @@ def parse():
                         "'kernel' alone: one strain's forces evaluated three times back to back "
                         "(the force kernel of the default options, for a counter capture)")
     p.add_argument("--batch-steps", type=int, default=10)
+    p.add_argument("--batch-streams", type=int, default=2,
+                   help="batches of the same systems (each on its own CUDA stream) that take the batched "
+                        "section's steps in turn")
     p.add_argument("--learned-strains", type=int, default=64,
                    help="strains of the N = 2^21 system in the learned section (256 = one per period step)")
     return p.parse_args()
@@ -605,16 +608,17 @@ def section_main(args, rank, world, dev, torch, nemd, W):
     # freshly pinned pages are measurably slower than later ones
     for _ in range(2):
         e2e_pass(True)
-    # three timed passes over the Se strains; the median pass is reported
+    # five timed passes over the Se strains; the median pass is reported (the
+    # host's copy rate varies from pass to pass on a shared machine)
     e2e_reps = []
-    for _ in range(3):
+    for _ in range(5):
         barrier(world)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         e2e_pass(True)
         torch.cuda.synchronize(dev)
         e2e_reps.append(max_over_ranks(time.perf_counter() - t0, world, dev))
-    e2e_s = sorted(e2e_reps)[1]
+    e2e_s = sorted(e2e_reps)[len(e2e_reps) // 2]
     for c, _, _ in pipe:
         c.set_option(nemd.NEMD_OPT_ASYNC_HOST, 0)
     e2e_pairs = sum_over_ranks(float(sum(per["tuned"]["pairs"][i] for i in e2e_idx)), world, dev)
@@ -648,7 +652,7 @@ def section_main(args, rank, world, dev, torch, nemd, W):
            "mode": f"host positions in and host F, U, W out every strain through the C ABI with "
                    f"NEMD_OPT_ASYNC_HOST (copies on a second stream of each context overlap the evaluations), "
                    f"the {K} contexts of the tuned step taking the strains in turn, one sync per context at the "
-                   f"end; median of three passes"}
+                   f"end; median of five passes"}
     ctx.close()
     del q_all
 
@@ -711,11 +715,51 @@ def section_batched(args, world, dev, torch, nemd, W):
     b.sync()
     st, launches = b.stats()
     pairs = sum(x["pairs"] for x in st)
-    ms = timed_loop(torch, dev, world, lambda: b.compute(F, UW), args.batch_steps, 3,
-                    nvtx="timed_batched") / args.batch_steps
+    ms_one = timed_loop(torch, dev, world, lambda: b.compute(F, UW), args.batch_steps, 3) / args.batch_steps
     b.sync()
     best = min(times, key=lambda x: x[1] if x[1] == x[1] else 0.0)[0]
     b.close()
+    # the steps taken in turn by batch_streams batches of the same systems, each
+    # on its own CUDA stream with its own outputs (one step's setup kernels run
+    # beside another step's force kernel); every step evaluates all systems
+    KB = max(1, args.batch_streams)
+    bstreams = [torch.cuda.Stream(dev) for _ in range(KB)]
+    pipe = []
+    for st in bstreams:
+        bk = nemd.Batch(specs, device=dev.index, stream=st.cuda_stream)
+        bk.set_option(nemd.NEMD_BATCH_OPT_CELL_FACTOR, best["cell_factor"])
+        bk.set_option(nemd.NEMD_BATCH_OPT_TILE, best["tile"])
+        bk.set_state(q, ts)
+        pipe.append((bk, st, torch.zeros((b.ntot, 3), dtype=torch.float32, device=dev),
+                     torch.zeros((b.nsys, 10), dtype=torch.float64, device=dev)))
+    home = torch.cuda.current_stream(dev)
+
+    def pipe_steps(m):
+        for i in range(m):
+            bk, _, Fk, UWk = pipe[i % KB]
+            bk.compute(Fk, UWk)
+
+    pipe_steps(3 * KB)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed_batched")   # marks the timed region for profilers
+    e0.record(home)
+    for _, st, _, _ in pipe:
+        st.wait_event(e0)
+    pipe_steps(args.batch_steps)
+    for _, st, _, _ in pipe:
+        home.wait_stream(st)
+    e1.record(home)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    ms = e0.elapsed_time(e1) / args.batch_steps
+    for bk, _, _, _ in pipe:
+        bk.sync()
+        assert sum(x["pairs"] for x in bk.stats()[0]) == pairs, "pipelined batch pairs differ"
+        bk.close()
     # the same systems through per-system contexts with the same force kernel
     # (row kernel, cell list per system by neighbourhood volume), one after another
     ctxs = []
@@ -741,6 +785,8 @@ def section_batched(args, world, dev, torch, nemd, W):
     return {"workload": f"{len(ws)} systems, N ~ U[1000, 20000] (total {b.ntot}), density ~ U(0.8, 0.9), "
                         "planar or general flow at rate ~ U(0.5, 2) and random phase, WCA or LJ rc 2.5",
             "pairs_per_step": pairs, "ms_per_step": ms, "pairs_per_s": pairs / ms * 1e3,
+            "streams": KB,
+            "single_stream": {"ms_per_step": ms_one, "pairs_per_s": pairs / ms_one * 1e3},
             "kernel_launches_per_step": launches,
             "autotuned": {"cell_factor": best["cell_factor"], "tile": best["tile"],
                           "candidates_ms": [[c["cell_factor"], c["tile"], round(t, 4)] for c, t in times

@@ -371,10 +371,11 @@ int nemd_measure_peaks(int device, double *out);
  * systems, the force kernel being a single persistent launch over the chunks
  * of every system.  The step is captured once into a CUDA graph and replayed
  * (NEMD_BATCH_OPT_GRAPH).  Per system the results are those of a context with
- * the same flow, potential, variant and cell factor running the warp kernel
- * (nemd_compute_forces with NEMD_OPT_KERNEL = 2): same pair set, same forces
- * per particle; U and W are float64 sums of the same pair terms in another
- * order.
+ * the same flow, potential, variant and cell factor running the same force
+ * kernel (NEMD_BATCH_OPT_KERNEL, as NEMD_OPT_KERNEL): same pair set, forces
+ * per particle equal up to rounding; U and W are float64 sums of the same
+ * pair terms in another order.  Several batches, each on its own stream, run
+ * independently (a caller may keep two steps in flight on two streams).
  *
  * Call order: nemd_batch_create, nemd_batch_add (once per system, in order),
  * nemd_batch_finalize, then per step nemd_batch_set_state and
@@ -468,7 +469,8 @@ int nemd_batch_get_stats(nemd_batch *b, nemd_batch_stats *out, int64_t *launches
 /* Autotuner of a batch: times `reps` steps (after one untimed step) of every
  * candidate -- cell factor 1, 2 x particles per chunk 16, 32 -- on the current
  * state and keeps the fastest.  times (optional, cap entries) receives each
- * candidate as {kernel = 2, group = tile, cell_factor, ms}.  Synchronises. */
+ * candidate as {kernel = the batch's force kernel, group = tile, cell_factor,
+ * ms}.  Synchronises. */
 int nemd_batch_autotune(nemd_batch *b, int reps, nemd_tune_entry *times, int cap, int *ntimes);
 
 /* ---- Force evaluation without any memory allocation --------------------

@@ -1,7 +1,7 @@
 """Batches of independent systems (nemd_batch_*): every system's results equal
-those of a context running the same system alone with the warp kernel, and the
-FP64 oracle's; graph replay, eager launches, options, host pointers and
-per-system errors."""
+those of a context running the same system alone with the same force kernel,
+and the FP64 oracle's; graph replay, eager launches, options, host pointers,
+per-system errors and two batches in flight on two streams."""
 import numpy as np
 import pytest
 
@@ -46,11 +46,11 @@ def test_batch_equals_single_contexts_and_oracle():
     b = nemd.Batch([spec(w, v) for w, v in zip(ws, vs)])
     F, UW = evaluate(b, ws)
     st, launches = b.stats()
-    assert launches == 18
+    assert launches == 17
     for s, (w, v) in enumerate(zip(ws, vs)):
         lo, hi = b.offsets[s], b.offsets[s + 1]
-        one = run(w, v, kernel=(2, 32))
-        # same chunks and per-particle summation order as the warp kernel alone
+        one = run(w, v, kernel=(4, 32))
+        # the batch's default force kernel (the row kernel) on the system alone
         assert st[s]["pairs"] == one["stats"]["pairs"], s
         assert st[s]["variant"] == one["stats"]["variant"]
         assert force_err(F[lo:hi], one["F"]) <= 1e-6, s
@@ -95,6 +95,52 @@ def test_strains_advance_each_system():
             assert force_err(F[lo:hi], ref.F) <= 1e-5
             assert rel(UW[s, 0], ref.U) <= 3e-6
     b.close()
+
+
+def test_two_batches_in_flight_on_two_streams():
+    """Two batches of the same systems, each on its own CUDA stream, take the
+    steps (new strains every step) in turn with no synchronisation between
+    them (the form the bench times): every step's F and U, W equal those of
+    one batch running the steps one after another."""
+    ws, vs = systems(nsys=7, seed=27)
+    specs = [spec(w, v) for w, v in zip(ws, vs)]
+    q = torch.from_numpy(np.concatenate([w.q for w in ws])).cuda()
+    rng = np.random.default_rng(1)
+    steps = [[float(rng.uniform(0, w.T)) for w in ws] for _ in range(6)]
+
+    one = nemd.Batch(specs)
+    ref = []
+    for ts in steps:
+        F = torch.zeros((one.ntot, 3), dtype=torch.float32, device="cuda")
+        UW = torch.zeros((one.nsys, 10), dtype=torch.float64, device="cuda")
+        one.set_state(q, ts)
+        one.compute(F, UW)
+        one.sync()
+        ref.append((F.cpu().numpy(), UW.cpu().numpy(), [x["pairs"] for x in one.stats()[0]]))
+    one.close()
+
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    bs = [nemd.Batch(specs, stream=st.cuda_stream) for st in streams]
+    outs = [(torch.zeros((bs[0].ntot, 3), dtype=torch.float32, device="cuda"),
+             torch.zeros((bs[0].nsys, 10), dtype=torch.float64, device="cuda")) for _ in steps]
+    for i, ts in enumerate(steps):
+        bs[i % 2].set_state(q, ts)
+        bs[i % 2].compute(*outs[i])
+    for b in bs:
+        b.sync()
+    torch.cuda.synchronize()
+    for i, (F, UW) in enumerate(outs):
+        assert np.array_equal(F.cpu().numpy(), ref[i][0]), i
+        assert np.array_equal(UW.cpu().numpy(), ref[i][1]), i
+    for k, b in enumerate(bs):
+        assert [x["pairs"] for x in b.stats()[0]] == ref[len(steps) - 2 + k][2]
+        b.close()
+    # one system of the last step against the oracle
+    moved = W.Workload(name=ws[0].name, A=ws[0].A, L0=ws[0].L0, M=ws[0].M, T=ws[0].T, t=steps[-1][0],
+                       q=ws[0].q, kind=ws[0].kind, rc=ws[0].rc)
+    o = oracle.evaluate(moved, "ds")
+    assert ref[-1][2][0] == o.npairs
+    assert force_err(ref[-1][0][:ws[0].n].astype(np.float64), o.F) <= 1e-5
 
 
 @pytest.mark.parametrize("kfac,tile", [(2, 32), (1, 16), (2, 16)])
