@@ -45,18 +45,6 @@ __device__ __forceinline__ void mm3(const double *a, const double *b, double *c,
   __syncwarp();
 }
 
-// Row shift split into an exact multiple of the quantum q (a power of two, so
-// scaling by 1/q is exact) and a float32 residual.
-__device__ __forceinline__ void set_shift(Row &r, double ox, double oy, double oz, double q, double qi) {
-  double qx = rint(ox * qi) * q, qy = rint(oy * qi) * q, qz = rint(oz * qi) * q;
-  r.shx = (float)qx;
-  r.shy = (float)qy;
-  r.shz = (float)qz;
-  r.srx = (float)(ox - qx);
-  r.sry = (float)(oy - qy);
-  r.srz = (float)(oz - qz);
-}
-
 }  // namespace
 
 // Shared scratch of one warp's lattice.
@@ -314,6 +302,10 @@ __device__ void grid_body(Geo *g, const GridIn &in) {
   } else {
     for (int a = 0; a < 3; a++) nc[a] = (int)floor(fac * (double)kf * Rm[4 * a] * irc);
     for (int k = 0; k < 9; k++) Gd[k] = 0.0;
+    // the stencil forms its window bounds in float-float (error below 2^-40
+    // lsum, a sixteenth of wrap_tol) from this reach, one wrap_tol longer
+    const double rcs = rce + wtol;
+    g->rceff = to_ff2(rcs);
     for (int a = 0; a < 3; a++) {
       const double w = (nc[a] > 0) ? Rm[4 * a] / (double)nc[a] : 1.0;
       const double iw = 1.0 / w;  // the one reciprocal of the side: binning, windows and reach
@@ -322,7 +314,7 @@ __device__ void grid_body(Geo *g, const GridIn &in) {
       g->wff[a] = to_ff2(w);
       g->Ginvff[a] = to_ff2(iw);
       Gd[4 * a] = w;
-      reach[a] = (int)ceil(rce * iw);
+      reach[a] = (int)ceil(rcs * iw);
     }
     maxrows = (2 * reach[2] + 1) * (2 * reach[1] + 2);
     for (int k = 0; k < 9; k++) g->Qf[k] = (float)Ri[k];
@@ -418,6 +410,30 @@ __global__ void k_grid(Geo *g, GridIn in) {
   if (threadIdx.x == 0) grid_body(g, in);
 }
 
+// ---- the stencil in float-float: a class's window bounds and row shifts take
+// a few dozen operations, and float64 runs at a small fraction of the float32
+// rate here ----
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+__device__ __forceinline__ int ff_floor_int(ff x) { return (int)ff_floor(x); }
+__device__ __forceinline__ int ff_ceil_int(ff x) { return -(int)ff_floor(ff_neg(x)); }
+
+// Nearest integer to hi + lo (|hi| < 2^22; halves as round-half-even on hi).
+__device__ __forceinline__ float ff_rint(ff x) {
+  const float r = rintf(x.hi);
+  const float d = __fadd_rn(__fsub_rn(x.hi, r), x.lo);  // x.hi - r is exact
+  return d > 0.5f ? __fadd_rn(r, 1.f) : (d < -0.5f ? __fsub_rn(r, 1.f) : r);
+}
+
+// One component o of a row shift split as the rows store it: the nearest
+// multiple sh of the quantum q (a power of two; qi = 1 / q) and the rest
+// o - sh rounded once to float32 (o.hi - sh is exact: both lie within a factor
+// two of each other, or sh = 0).
+__device__ __forceinline__ void split_shift_ff(ff o, float q, float qi, float &sh, float &sr) {
+  const ff t = {__fmul_rn(o.hi, qi), __fmul_rn(o.lo, qi)};  // exact scaling
+  sh = __fmul_rn(ff_rint(t), q);
+  sr = __fadd_rn(__fsub_rn(o.hi, sh), o.lo);
+}
+
 // The neighbour rows of one home (iy, iz) class, written to out[0..maxrows) by
 // the lanes of one warp (one row per lane); returns their number on every
 // lane.  Row order: dz (jz) outer, dy (jy) inner.  cell_base is added to every
@@ -426,8 +442,7 @@ __device__ int stencil_class_warp(Geo *g, int cls, int cell_base, Row *out, int 
   constexpr int kMaxZ = 2 * kMaxFactor + 4;  // bound on the z-rows of a dynamic offset class
   const int l1 = g->nc[0], l2 = g->nc[1], l3 = g->nc[2];
   const int maxrows = g->maxrows;
-  const double rce = g->rc * (1.0 + kMargin) + (g->variant == NEMD_DS ? 0.0 : 2.0 * g->wrap_tol);
-  const double q = g->quantum;
+  const float qf = g->quantum_f, qif = g->quantum_inv_f;
   const int iy = cls % l2, iz = cls / l2;
   int nr;
   if (g->variant == NEMD_DS) {
@@ -438,9 +453,15 @@ __device__ int stencil_class_warp(Geo *g, int cls, int cell_base, Row *out, int 
       const int jyu = iy + dy, jzu = iz + dz;
       const int ky = floordiv_i(jyu, l2), kz = floordiv_i(jzu, l3);
       const int jy = jyu - ky * l2, jz = jzu - kz * l3;
-      const double c1 = dy, c2 = dz;
+      const float c1 = (float)dy, c2 = (float)dz;
       Row r;
-      set_shift(r, g->G[1] * c1 + g->G[2] * c2, g->G[4] * c1 + g->G[5] * c2, g->G[7] * c1 + g->G[8] * c2, q, g->quantum_inv);
+      ff o[3];
+#pragma unroll
+      for (int a = 0; a < 3; a++)
+        o[a] = ff_add(ff_mul_f(ff_of(g->Gff[3 * a + 1]), c1), ff_mul_f(ff_of(g->Gff[3 * a + 2]), c2));
+      split_shift_ff(o[0], qf, qif, r.shx, r.srx);
+      split_shift_ff(o[1], qf, qif, r.shy, r.sry);
+      split_shift_ff(o[2], qf, qif, r.shz, r.srz);
       r.cbase = cell_base + l1 * (jy + l2 * jz);
       r.sxi = 0;
       r.dxlo = -K;
@@ -451,15 +472,16 @@ __device__ int stencil_class_warp(Geo *g, int cls, int cell_base, Row *out, int 
       out[e] = r;
     }
   } else {
-    // window bounds by reciprocals of the cell sides (those of the grid, the
-    // same rounded quotients): a bound that moves by a rounding only adds or
-    // drops a cell lying at distance rc (1 + 1e-12) or more, which holds no
-    // partner
-    const double w1 = g->w[0], w2 = g->w[1], w3 = g->w[2];
-    const double iw1 = g->Ginv_scale[0], iw2 = g->Ginv_scale[1], iw3 = g->Ginv_scale[2];
-    const double r12 = g->R[1], r13 = g->R[2], r23 = g->R[5];
-    const int zlo = (int)floor(((double)iz * w3 - rce) * iw3);
-    int zhi = (int)ceil(((double)(iz + 1) * w3 + rce) * iw3) - 1;
+    // window bounds in units of the cell sides (the grid's reciprocals): the
+    // reach rce includes rc (1 + 1e-12), the wrap's tolerance on both sides and
+    // one more wrap_tol for the float-float roundings here, so a bound that
+    // moves by a rounding only adds or drops a cell lying farther than rc
+    const ff rce = ff_of(g->rceff);
+    const ff w1 = ff_of(g->wff[0]), w2 = ff_of(g->wff[1]), w3 = ff_of(g->wff[2]);
+    const ff iw1 = ff_of(g->Ginvff[0]), iw2 = ff_of(g->Ginvff[1]), iw3 = ff_of(g->Ginvff[2]);
+    const ff r12 = ff_of(g->Rff[1]), r13 = ff_of(g->Rff[2]), r23 = ff_of(g->Rff[5]);
+    const int zlo = ff_floor_int(ff_mul(ff_sub(ff_mul_f(w3, (float)iz), rce), iw3));
+    int zhi = ff_ceil_int(ff_mul(ff_add(ff_mul_f(w3, (float)(iz + 1)), rce), iw3)) - 1;
     if (zhi - zlo + 1 > kMaxZ) {
       if (lane == 0) atomicOr(&g->error, ERRB_CAPACITY);
       zhi = zlo + kMaxZ - 1;
@@ -470,9 +492,9 @@ __device__ int stencil_class_warp(Geo *g, int cls, int cell_base, Row *out, int 
     if (lane < nz) {
       const int jzu = zlo + lane;
       const int kz = floordiv_i(jzu, l3);
-      const double yshift = (double)kz * r23;
-      ylo_l = (int)floor(((double)iy * w2 - rce - yshift) * iw2);
-      const int hi = (int)ceil(((double)(iy + 1) * w2 + rce - yshift) * iw2) - 1;
+      const ff yshift = ff_mul_f(r23, (float)kz);
+      ylo_l = ff_floor_int(ff_mul(ff_sub(ff_sub(ff_mul_f(w2, (float)iy), rce), yshift), iw2));
+      const int hi = ff_ceil_int(ff_mul(ff_sub(ff_add(ff_mul_f(w2, (float)(iy + 1)), rce), yshift), iw2)) - 1;
       ycnt_l = hi - ylo_l + 1;
     }
     int ylo[kMaxZ], ycnt[kMaxZ];
@@ -489,13 +511,14 @@ __device__ int stencil_class_warp(Geo *g, int cls, int cell_base, Row *out, int 
       const int jzu = zlo + z, jyu = ylo[z] + (e - base);
       const int kz = floordiv_i(jzu, l3), jz = jzu - kz * l3;
       const int ky = floordiv_i(jyu, l2), jy = jyu - ky * l2;
-      const double yshift = (double)kz * r23;
-      const double sx = (double)ky * r12 + (double)kz * r13;
-      const int xlo = (int)floor((-rce - sx) * iw1);
-      const int xhi = (int)ceil((w1 + rce - sx) * iw1) - 1;
+      const ff sx = ff_add(ff_mul_f(r12, (float)ky), ff_mul_f(r13, (float)kz));
+      const int xlo = ff_floor_int(ff_mul(ff_sub(ff_neg(rce), sx), iw1));
+      const int xhi = ff_ceil_int(ff_mul(ff_sub(ff_add(w1, rce), sx), iw1)) - 1;
+      const float sxi = ff_rint(ff_mul(sx, iw1));
       Row r;
-      const double sxi = rint(sx * iw1);
-      set_shift(r, sx - sxi * w1, (double)(jyu - iy) * w2 + yshift, (double)(jzu - iz) * w3, q, g->quantum_inv);
+      split_shift_ff(ff_sub(sx, ff_mul_f(w1, sxi)), qf, qif, r.shx, r.srx);
+      split_shift_ff(ff_add(ff_mul_f(w2, (float)(jyu - iy)), ff_mul_f(r23, (float)kz)), qf, qif, r.shy, r.sry);
+      split_shift_ff(ff_mul_f(w3, (float)(jzu - iz)), qf, qif, r.shz, r.srz);
       r.cbase = cell_base + l1 * (jy + l2 * jz);
       r.sxi = (int)sxi;
       r.dxlo = xlo;

@@ -70,7 +70,8 @@ struct Geo {
   // float-float (hi, lo) copies of the wrap's frame data: R, 1 / r_ii, G, the
   // dynamic offset 1 / w_i and w_i.  The wrap works in float-float after the
   // float64 fractional coordinates; wrap_tol bounds its position error.
-  float2 Rff[9], rinvff[3], Gff[9], Ginvff[3], wff[3], Linvff[9];
+  // rceff: the dynamic offset stencil's reach rc (1 + 1e-12) + 3 wrap_tol.
+  float2 Rff[9], rinvff[3], Gff[9], Ginvff[3], wff[3], Linvff[9], rceff;
   double wrap_tol;
   float quantum_f, quantum_inv_f;  // the quantum and its inverse (powers of two) as float
   double quantum;     // float32 coordinates and offsets are multiples of this power of 2
