@@ -13,6 +13,15 @@
 // a fixed order by the last block of each kick, so a run repeats bit for bit.
 // The paper gives no integrator: this is the reading stated with
 // nemd_integrate in include/nemd.h.
+//
+// Arithmetic: the per-particle kernels (the kicks and the drift) read q and p
+// as float64, work in float-float (pairs of float32 from error-free
+// transformations, about 2^-47 relative per operation) and write float64, the
+// propagators applied as x + (M - I) x so that the large part of x passes
+// through exactly; one rounded float64 addition per stored component is their
+// only float64 arithmetic (float64 runs at a small fraction of the float32
+// rate here).  A value outside [2^-100, 2^100) in magnitude, or not finite,
+// sends its particle through the same step in float64.
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -26,14 +35,76 @@ namespace nemd {
 namespace {
 
 constexpr int kIntThreads = 256;
-// int_state layout (doubles)
+// int_state layout (doubles); from kDff on, float-float copies (two floats in
+// each double slot) of exp(A dt) - I, exp(-A dt/2) - I, Phi(dt), the rescale
+// factor and h
 constexpr int kE = 0, kEh = 9, kPhi = 18, kK0 = 27, kScale = 28, kH = 29, kThermo = 30, kT0 = 31, kDt = 32,
-              kStep = 33, kTnow = 34, kTicket = 35, kIntState = 36;
+              kStep = 33, kTnow = 34, kTicket = 35, kDff = 36, kDhff = 45, kPhiff = 54, kScaleff = 63,
+              kHff = 64, kIntState = 65;
 
 // The flow matrix by value.
 struct Mat9 {
   double a[9];
 };
+
+// float-float copy of a float64 value (one thread, set-up only)
+__device__ __forceinline__ float2 int_ff2(double x) {
+  const float hi = __double2float_rn(x);
+  return make_float2(hi, __double2float_rn(x - (double)hi));
+}
+
+__device__ __forceinline__ ff st_ff(const double *st, int k) {
+  const float2 v = reinterpret_cast<const float2 *>(st)[k];
+  return {v.x, v.y};
+}
+
+__device__ __forceinline__ void st_set_ff(double *st, int k, double x) {
+  reinterpret_cast<float2 *>(st)[k] = int_ff2(x);
+}
+
+// float32 to float64 from the bits (exact; zero and subnormal floats give 0,
+// an error below 2^-126)
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xffu;
+  if (e == 0u) return 0.0;
+  const unsigned long long ex = e == 0xffu ? 0x7ffull : (unsigned long long)(e + 896u);
+  return __longlong_as_double((long long)(((unsigned long long)(b & 0x80000000u) << 32) | (ex << 52) |
+                                          ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
+
+// the float64 nearest to hi + lo: both exactly in float64, one rounded addition
+__device__ __forceinline__ double ff_to_double(ff x) { return __dadd_rn(f2d_bits(x.hi), f2d_bits(x.lo)); }
+
+// x + D x for a 3x3 float-float matrix D (row-major, in st from slot k) and
+// float-float x: the products and their sums in float-float, x added last
+__device__ __forceinline__ void ff_apply(const double *st, int k, const ff x[3], ff out[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    const ff d = ff_add(ff_add(ff_mul(st_ff(st, k + 3 * a), x[0]), ff_mul(st_ff(st, k + 3 * a + 1), x[1])),
+                        ff_mul(st_ff(st, k + 3 * a + 2), x[2]));
+    out[a] = ff_add(x[a], d);
+  }
+}
+
+// Phi x (float-float)
+__device__ __forceinline__ void ff_matvec(const double *st, int k, const ff x[3], ff out[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+    out[a] = ff_add(ff_add(ff_mul(st_ff(st, k + 3 * a), x[0]), ff_mul(st_ff(st, k + 3 * a + 1), x[1])),
+                    ff_mul(st_ff(st, k + 3 * a + 2), x[2]));
+}
+
+__device__ __forceinline__ ff ff_norm2(const ff x[3]) {
+  return ff_add(ff_add(ff_mul(x[0], x[0]), ff_mul(x[1], x[1])), ff_mul(x[2], x[2]));
+}
+
+// the three components of row i of a float64 N x 3 array in float-float; ok
+// is cleared when one is out of the split's range
+__device__ __forceinline__ void load_ff3(const double *v, size_t i, ff x[3], bool &ok) {
+#pragma unroll
+  for (int a = 0; a < 3; a++) x[a] = split_double(v[3 * i + a], ok);
+}
 
 __device__ __forceinline__ void mat3(const double *a, const double *b, double *c) {
   double t[9];
@@ -94,6 +165,14 @@ __global__ void k_int_setup(double *st, Mat9 A, double t0, double dt, int thermo
   expm_phi(B, st + kE, P);
   for (int k = 0; k < 9; k++) st[kPhi + k] = dt * P[k];
   expm_phi(Bh, st + kEh, Ph);
+  for (int k = 0; k < 9; k++) {
+    const double id = (k % 4 == 0) ? 1.0 : 0.0;
+    st_set_ff(st, kDff + k, st[kE + k] - id);
+    st_set_ff(st, kDhff + k, st[kEh + k] - id);
+    st_set_ff(st, kPhiff + k, st[kPhi + k]);
+  }
+  st_set_ff(st, kScaleff, 1.0);
+  st_set_ff(st, kHff, 0.5 * dt);
   st[kScale] = 1.0;
   st[kH] = 0.5 * dt;
   st[kThermo] = thermostat;
@@ -148,6 +227,7 @@ __global__ void __launch_bounds__(kIntThreads) k_int_k0(double *st, const double
   if (threadIdx.x != 0) return;
   st[kK0] = y;
   st[kScale] = 1.0;
+  st_set_ff(st, kScaleff, 1.0);
 }
 
 // After every block has written its partial of sum |p|^2: the last block to
@@ -167,6 +247,7 @@ __device__ __forceinline__ void last_block_scale(double *st, const double *part)
   const double y = block_sum_fixed(part, (int)gridDim.x);
   if (threadIdx.x != 0) return;
   st[kScale] = (st[kThermo] != 0.0 && y > 0.0) ? sqrt(st[kK0] / y) : 1.0;
+  st_set_ff(st, kScaleff, st[kScale]);
   if (TICK) {
     const double k = st[kStep] + 1.0;
     st[kStep] = k;
@@ -186,20 +267,34 @@ __device__ __forceinline__ void mv3(const double *M, double x, double y, double 
 // clock advanced to the step's end time
 __global__ void __launch_bounds__(kIntThreads) k_int_kick1(double *__restrict__ p, const float *__restrict__ F,
                                                            int n, double *st, double *part) {
-  const double h = st[kH], sc = st[kScale];
-  double x2 = 0.0;
+  const ff h = st_ff(st, kHff), sc = st_ff(st, kScaleff);
+  ff x2 = {0.f, 0.f};
+  double x2d = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const double a = sc * p[3 * (size_t)i] + h * (double)F[3 * (size_t)i];
-    const double b = sc * p[3 * (size_t)i + 1] + h * (double)F[3 * (size_t)i + 1];
-    const double c = sc * p[3 * (size_t)i + 2] + h * (double)F[3 * (size_t)i + 2];
-    double ox, oy, oz;
-    mv3(st + kEh, a, b, c, ox, oy, oz);
-    p[3 * (size_t)i] = ox;
-    p[3 * (size_t)i + 1] = oy;
-    p[3 * (size_t)i + 2] = oz;
-    x2 += (ox * ox + oy * oy) + oz * oz;
+    bool ok = true;
+    ff v[3], o[3];
+    load_ff3(p, (size_t)i, v, ok);
+    if (ok) {
+#pragma unroll
+      for (int a = 0; a < 3; a++) v[a] = ff_add(ff_mul(sc, v[a]), ff_mul_f(h, F[3 * (size_t)i + a]));
+      ff_apply(st, kDhff, v, o);
+#pragma unroll
+      for (int a = 0; a < 3; a++) p[3 * (size_t)i + a] = ff_to_double(o[a]);
+      x2 = ff_add(x2, ff_norm2(o));
+    } else {
+      const double hd = st[kH], sd = st[kScale];
+      const double a0 = sd * p[3 * (size_t)i] + hd * (double)F[3 * (size_t)i];
+      const double a1 = sd * p[3 * (size_t)i + 1] + hd * (double)F[3 * (size_t)i + 1];
+      const double a2 = sd * p[3 * (size_t)i + 2] + hd * (double)F[3 * (size_t)i + 2];
+      double ox, oy, oz;
+      mv3(st + kEh, a0, a1, a2, ox, oy, oz);
+      p[3 * (size_t)i] = ox;
+      p[3 * (size_t)i + 1] = oy;
+      p[3 * (size_t)i + 2] = oz;
+      x2d += (ox * ox + oy * oy) + oz * oz;
+    }
   }
-  block_p2(x2, part);
+  block_p2(ff_to_double(x2) + x2d, part);
   last_block_scale<true>(st, part);
 }
 
@@ -208,36 +303,63 @@ __global__ void __launch_bounds__(kIntThreads) k_int_kick1(double *__restrict__ 
 // fractional coordinates (estimated in float32, error ~1e-6) lie within
 // [1e-3, 1 - 1e-3] is inside the cell already and keeps its drifted q; the
 // others take the float64 wrap q = L frac(L^-1 q)
+// (xf, yf, zf: the new position within a float32 ulp, for the inside test)
+__device__ __forceinline__ void drift_store(double *__restrict__ q, size_t i, double xx, double yy, double zz,
+                                            float xf, float yf, float zf, const Geo *g) {
+  bool inside = true;
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    const float sa = fmaf(g->Linvff[3 * a + 2].x, zf, fmaf(g->Linvff[3 * a + 1].x, yf, g->Linvff[3 * a].x * xf));
+    inside = inside && sa > 1e-3f && sa < 0.999f;
+  }
+  if (inside) {
+    q[3 * i] = xx;
+    q[3 * i + 1] = yy;
+    q[3 * i + 2] = zz;
+  } else {
+    double s[3], qp[3];
+    frac_wrap(g->Linv, xx, yy, zz, s);
+    frac_to_cart(g->L, s, qp);
+    q[3 * i] = qp[0];
+    q[3 * i + 1] = qp[1];
+    q[3 * i + 2] = qp[2];
+  }
+}
+
 __global__ void __launch_bounds__(kIntThreads) k_int_drift(double *__restrict__ q, double *__restrict__ p, int n,
                                                            const double *__restrict__ st, const Geo *g) {
-  const double sc = st[kScale];
+  const ff sc = st_ff(st, kScaleff);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const double px = sc * p[3 * (size_t)i], py = sc * p[3 * (size_t)i + 1], pz = sc * p[3 * (size_t)i + 2];
-    p[3 * (size_t)i] = px;
-    p[3 * (size_t)i + 1] = py;
-    p[3 * (size_t)i + 2] = pz;
-    double ex, ey, ez, fx, fy, fz;
-    mv3(st + kE, q[3 * (size_t)i], q[3 * (size_t)i + 1], q[3 * (size_t)i + 2], ex, ey, ez);
-    mv3(st + kPhi, px, py, pz, fx, fy, fz);
-    const double xx = ex + fx, yy = ey + fy, zz = ez + fz;
-    const float xf = __double2float_rn(xx), yf = __double2float_rn(yy), zf = __double2float_rn(zz);
-    bool inside = true;
+    bool ok = true;
+    ff pv[3], qv[3];
+    load_ff3(p, (size_t)i, pv, ok);
+    load_ff3(q, (size_t)i, qv, ok);
+    if (ok) {
+      ff e[3], f[3];
 #pragma unroll
-    for (int a = 0; a < 3; a++) {
-      const float sa = fmaf(g->Linvff[3 * a + 2].x, zf, fmaf(g->Linvff[3 * a + 1].x, yf, g->Linvff[3 * a].x * xf));
-      inside = inside && sa > 1e-3f && sa < 0.999f;
-    }
-    if (inside) {
-      q[3 * (size_t)i] = xx;
-      q[3 * (size_t)i + 1] = yy;
-      q[3 * (size_t)i + 2] = zz;
+      for (int a = 0; a < 3; a++) {
+        pv[a] = ff_mul(sc, pv[a]);
+        p[3 * (size_t)i + a] = ff_to_double(pv[a]);
+      }
+      // q + (exp(A dt) - I) q + Phi p: the increments first, q added last
+      ff_matvec(st, kDff, qv, e);
+      ff_matvec(st, kPhiff, pv, f);
+      ff x[3];
+#pragma unroll
+      for (int a = 0; a < 3; a++) x[a] = ff_add(qv[a], ff_add(e[a], f[a]));
+      drift_store(q, (size_t)i, ff_to_double(x[0]), ff_to_double(x[1]), ff_to_double(x[2]), x[0].hi, x[1].hi,
+                  x[2].hi, g);
     } else {
-      double s[3], qp[3];
-      frac_wrap(g->Linv, xx, yy, zz, s);
-      frac_to_cart(g->L, s, qp);
-      q[3 * (size_t)i] = qp[0];
-      q[3 * (size_t)i + 1] = qp[1];
-      q[3 * (size_t)i + 2] = qp[2];
+      const double sd = st[kScale];
+      const double px = sd * p[3 * (size_t)i], py = sd * p[3 * (size_t)i + 1], pz = sd * p[3 * (size_t)i + 2];
+      p[3 * (size_t)i] = px;
+      p[3 * (size_t)i + 1] = py;
+      p[3 * (size_t)i + 2] = pz;
+      double ex, ey, ez, fx, fy, fz;
+      mv3(st + kE, q[3 * (size_t)i], q[3 * (size_t)i + 1], q[3 * (size_t)i + 2], ex, ey, ez);
+      mv3(st + kPhi, px, py, pz, fx, fy, fz);
+      const double xx = ex + fx, yy = ey + fy, zz = ez + fz;
+      drift_store(q, (size_t)i, xx, yy, zz, __double2float_rn(xx), __double2float_rn(yy), __double2float_rn(zz), g);
     }
   }
 }
@@ -245,20 +367,39 @@ __global__ void __launch_bounds__(kIntThreads) k_int_drift(double *__restrict__ 
 // second half: p <- h F + exp(-A h) p; the new rescale factor
 __global__ void __launch_bounds__(kIntThreads) k_int_kick2(double *__restrict__ p, const float *__restrict__ F,
                                                            int n, double *st, double *part) {
-  const double h = st[kH];
-  double x2 = 0.0;
+  const ff h = st_ff(st, kHff);
+  ff x2 = {0.f, 0.f};
+  double x2d = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    double ox, oy, oz;
-    mv3(st + kEh, p[3 * (size_t)i], p[3 * (size_t)i + 1], p[3 * (size_t)i + 2], ox, oy, oz);
-    ox += h * (double)F[3 * (size_t)i];
-    oy += h * (double)F[3 * (size_t)i + 1];
-    oz += h * (double)F[3 * (size_t)i + 2];
-    p[3 * (size_t)i] = ox;
-    p[3 * (size_t)i + 1] = oy;
-    p[3 * (size_t)i + 2] = oz;
-    x2 += (ox * ox + oy * oy) + oz * oz;
+    bool ok = true;
+    ff v[3], o[3];
+    load_ff3(p, (size_t)i, v, ok);
+    if (ok) {
+      // p + (exp(-A h) - I) p + h F: the increments first, p added last
+#pragma unroll
+      for (int a = 0; a < 3; a++) {
+        const ff d = ff_add(ff_add(ff_add(ff_mul(st_ff(st, kDhff + 3 * a), v[0]),
+                                          ff_mul(st_ff(st, kDhff + 3 * a + 1), v[1])),
+                                   ff_mul(st_ff(st, kDhff + 3 * a + 2), v[2])),
+                            ff_mul_f(h, F[3 * (size_t)i + a]));
+        o[a] = ff_add(v[a], d);
+        p[3 * (size_t)i + a] = ff_to_double(o[a]);
+      }
+      x2 = ff_add(x2, ff_norm2(o));
+    } else {
+      const double hd = st[kH];
+      double ox, oy, oz;
+      mv3(st + kEh, p[3 * (size_t)i], p[3 * (size_t)i + 1], p[3 * (size_t)i + 2], ox, oy, oz);
+      ox += hd * (double)F[3 * (size_t)i];
+      oy += hd * (double)F[3 * (size_t)i + 1];
+      oz += hd * (double)F[3 * (size_t)i + 2];
+      p[3 * (size_t)i] = ox;
+      p[3 * (size_t)i + 1] = oy;
+      p[3 * (size_t)i + 2] = oz;
+      x2d += (ox * ox + oy * oy) + oz * oz;
+    }
   }
-  block_p2(x2, part);
+  block_p2(ff_to_double(x2) + x2d, part);
   last_block_scale<false>(st, part);
 }
 
