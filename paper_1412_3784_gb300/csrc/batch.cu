@@ -138,9 +138,9 @@ cudaError_t enqueue_step(nemd_batch *b, cudaStream_t st) {
   return nemd::launch_batch_finish(st, v);
 }
 
-// lattice, grid, stencil, bin (wrap, 3 scan, scatter, rank-and-pack), chunks
-// (count, 3 scan, write), force, fix-up, reduce
-constexpr int64_t kStepLaunches = 3 + 6 + 5 + 1 + 2;
+// lattice, grid, stencil, bin (wrap, 3 scan, scatter, rank-and-pack), chunk
+// list, force, fix-up, reduce
+constexpr int64_t kStepLaunches = 3 + 6 + 1 + 1 + 2;
 
 }  // namespace
 
@@ -179,8 +179,8 @@ int nemd_batch_destroy(nemd_batch *b) {
   drop_graph(b);
   BatchView &v = b->v;
   void *ptrs[] = {v.geo,      (void *)v.sys_of,  (void *)v.class_sys, v.relc,       v.relr,      v.rank,   v.count,     v.start,
-                  v.tiles,    v.perm,    v.pos4,      v.posr,       v.cell_sorted, v.rows, v.rowcnt,    v.chunk_cnt,
-                  v.chunk_off, v.chunk_tiles, v.chunks, v.work,     v.ppart,     v.recheck, v.nrecheck, v.sys_counters,
+                  v.tiles,    v.perm,    v.pos4,      v.posr,       v.cell_sorted, v.rows, v.rowcnt,
+                  v.chunk_off, v.chunks, v.work,     v.ppart,     v.recheck, v.nrecheck, v.sys_counters,
                   v.sys_pairs, b->sys_dev, b->lat_dev, b->grid_dev, b->pot_dev,  b->t_dev, b->q_copy,   b->f_int,
                   b->uw_int,  b->err_dev};
   for (void *p : ptrs)
@@ -358,7 +358,7 @@ int nemd_batch_finalize(nemd_batch *b) {
   v.gs = b->gs;
   v.wide = b->force_kernel == 4;
   const int64_t np = ntot > 0 ? ntot : 1;
-  const int64_t cell_tiles = ncells / nemd::kFixedScanTile + 2, cls_tiles = nclasses / nemd::kFixedScanTile + 2;
+  const int64_t cell_tiles = ncells / nemd::kFixedScanTile + 2;
   // clang-format off
   if ((r = alloc(b, &v.geo, S, "geo")) || (r = alloc(b, &b->sys_dev, S, "systems")) ||
       (r = alloc(b, &b->lat_dev, S, "lattice inputs")) || (r = alloc(b, &b->grid_dev, S, "grid inputs")) ||
@@ -372,9 +372,9 @@ int nemd_batch_finalize(nemd_batch *b) {
       (r = alloc(b, &v.count, ncells + 1, "count")) || (r = alloc(b, &v.start, ncells + 1, "start")) ||
       (r = alloc(b, &v.tiles, cell_tiles, "scan tiles")) ||
       (r = alloc(b, &v.rows, nclasses * nemd::kBatchRowStride, "rows")) ||
-      (r = alloc(b, &v.rowcnt, nclasses, "rowcnt")) || (r = alloc(b, &v.chunk_cnt, nclasses + 1, "chunk counts")) ||
+      (r = alloc(b, &v.rowcnt, nclasses, "rowcnt")) ||
       (r = alloc(b, &v.chunk_off, nclasses + 1, "chunk offsets")) ||
-      (r = alloc(b, &v.chunk_tiles, cls_tiles, "chunk scan tiles")) || (r = alloc(b, &v.work, 1, "work")) ||
+      (r = alloc(b, &v.work, 1, "work")) ||
       (r = alloc(b, &v.recheck, nemd::kRecheckCap, "recheck")) || (r = alloc(b, &v.nrecheck, 1, "nrecheck")) ||
       (r = alloc(b, &v.sys_counters, 2 * S, "counters")) || (r = alloc(b, &v.sys_pairs, S, "pairs")) ||
       (r = alloc(b, &b->uw_int, 10 * S, "UW")) || (r = alloc(b, &b->err_dev, S, "errors")))

@@ -50,7 +50,7 @@ struct BatchView {
   int *cell_sorted;
   Row *rows;
   int *rowcnt;
-  int *chunk_cnt, *chunk_off, *chunk_tiles;
+  int *chunk_off;  // [nclasses]: the length of the chunk list
   int4 *chunks;
   int *work;     // dynamic chunk counter of the force kernel
   float4 *ppart;  // per sorted particle: {u, wxx, wyy, wzz}, {wxy, wxz, wyz, pairs (int bits)}

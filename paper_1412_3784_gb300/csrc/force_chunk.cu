@@ -362,28 +362,40 @@ __device__ __forceinline__ bool batch_class(const BatchView &v, int slot, const 
 
 // One thread per class slot: the rows of batched systems are short (a few
 // dozen cells) and there are many of them, so each thread walks its own row
-// in global memory.
+// in global memory.  The batched force kernels take chunks from a shared
+// counter and write every particle's sums to its own slot, so no result
+// depends on where a chunk sits in the list: one kernel builds it, each warp
+// counting its rows' chunks, claiming a contiguous range of the list with one
+// atomic addition and walking its rows again to write them (the second walk
+// reads what the first brought into L1).  The list's length ends at
+// chunk_off[nclasses], which the force kernels read.
 constexpr int kBatchWalkThreads = 128;
 
-__global__ void __launch_bounds__(kBatchWalkThreads) k_b_chunk_count(BatchView v) {
-  for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < v.nclasses; slot += gridDim.x * blockDim.x) {
-    const Geo *g;
-    int c0, l1, n = 0;
-    if (batch_class(v, slot, g, c0, l1))
-      chunk_walk(v.start, c0, l1, v.gs, v.wide ? g->span : kMaxSpan, [&](int, int, int, int) { n++; });
-    v.chunk_cnt[slot] = n;
-  }
-}
-
-__global__ void __launch_bounds__(kBatchWalkThreads) k_b_chunk_write(BatchView v) {
-  for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < v.nclasses; slot += gridDim.x * blockDim.x) {
-    const Geo *g;
-    int c0, l1;
-    if (!batch_class(v, slot, g, c0, l1)) continue;
-    int k = v.chunk_off[slot];
-    chunk_walk(v.start, c0, l1, v.gs, v.wide ? g->span : kMaxSpan, [&](int first, int count, int ixlo, int ixhi) {
-      v.chunks[k++] = make_int4(first, count, slot, ixlo | (ixhi << 16));
-    });
+__global__ void __launch_bounds__(kBatchWalkThreads) k_b_chunk_list(BatchView v) {
+  const int lane = threadIdx.x & 31;
+  int *total = v.chunk_off + v.nclasses;
+  for (int b0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); b0 < v.nclasses; b0 += gridDim.x * blockDim.x) {
+    const int slot = b0 + lane;
+    const Geo *g = nullptr;
+    int c0 = 0, l1 = 0, n = 0;
+    const bool has = slot < v.nclasses && batch_class(v, slot, g, c0, l1);
+    const int span = has ? (v.wide ? g->span : kMaxSpan) : 0;
+    if (has) chunk_walk(v.start, c0, l1, v.gs, span, [&](int, int, int, int) { n++; });
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int wsum = __shfl_sync(0xffffffffu, incl, 31);
+    int wbase = 0;
+    if (lane == 0 && wsum > 0) wbase = atomicAdd(total, wsum);
+    wbase = __shfl_sync(0xffffffffu, wbase, 0);
+    int k = wbase + incl - n;
+    if (n > 0)
+      chunk_walk(v.start, c0, l1, v.gs, span, [&](int first, int count, int ixlo, int ixhi) {
+        v.chunks[k++] = make_int4(first, count, slot, ixlo | (ixhi << 16));
+      });
   }
 }
 
@@ -391,10 +403,9 @@ cudaError_t launch_batch_chunks(cudaStream_t st, const BatchView &v, int sms) {
   int blocks = (v.nclasses + kBatchWalkThreads - 1) / kBatchWalkThreads;
   if (blocks > 16 * sms) blocks = 16 * sms;
   if (blocks < 1) blocks = 1;
-  k_b_chunk_count<<<blocks, kBatchWalkThreads, 0, st>>>(v);
-  cudaError_t e = launch_fixed_scan(st, v.chunk_cnt, v.chunk_off, v.chunk_tiles, v.nclasses);
+  cudaError_t e = cudaMemsetAsync(v.chunk_off + v.nclasses, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  k_b_chunk_write<<<blocks, kBatchWalkThreads, 0, st>>>(v);
+  k_b_chunk_list<<<blocks, kBatchWalkThreads, 0, st>>>(v);
   return cudaGetLastError();
 }
 
