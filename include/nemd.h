@@ -206,6 +206,12 @@ int nemd_compute_forces(nemd_ctx *ctx, float *F, double *U, double *W);
  *         they must stay valid until nemd_sync returns.
  *   dt > 0 finite; nsteps >= 0.  Asynchronous (enqueues every step); the
  *   context's time afterwards is t0 + nsteps dt.
+ * Arithmetic: q and p are stored in float64; the kicks and the drift compute
+ * in float-float (about 2^-47 relative per operation, the propagators applied
+ * as x + (M - I) x) and round each stored component once, so a step adds an
+ * error of a few 2^-47 |q| and |p|; components below 2^-100 in magnitude
+ * count as 0 there (an error under 2^-100), and a particle with a component
+ * of 2^100 or more, or not finite, is stepped in float64.
  * Errors: NEMD_ERR_ARG (host arrays, n < 0, bad dt or nsteps), NEMD_ERR_ORDER
  * (no flow), and the errors of the force evaluation. */
 int nemd_integrate(nemd_ctx *ctx, double *q, double *p, int64_t n, double t0, double dt, int64_t nsteps,

@@ -181,15 +181,22 @@ __device__ __forceinline__ void brick_wrap_ff(const Geo *g, const ff s[3], ff b[
   ff x = ff_add(ff_add(ff_mul(r11, s[0]), ff_mul(r12, s[1])), ff_mul(r13, s[2]));
   ff y = ff_add(ff_mul(r22, s[1]), ff_mul(r23, s[2]));
   ff z = ff_mul(r33, s[2]);
+  // a shift by 0 lattice vectors leaves a float-float value bit for bit (its
+  // hi is already the rounding of hi + lo), so it is skipped: z (s3 in [0, 1))
+  // almost never moves
   const float m3 = ff_floor(ff_mul(z, ff_of(g->rinvff[2])));
-  z = ff_add(z, ff_neg(ff_mul_f(r33, m3)));
-  y = ff_add(y, ff_neg(ff_mul_f(r23, m3)));
-  x = ff_add(x, ff_neg(ff_mul_f(r13, m3)));
+  if (m3 != 0.f) {
+    z = ff_add(z, ff_neg(ff_mul_f(r33, m3)));
+    y = ff_add(y, ff_neg(ff_mul_f(r23, m3)));
+    x = ff_add(x, ff_neg(ff_mul_f(r13, m3)));
+  }
   const float m2 = ff_floor(ff_mul(y, ff_of(g->rinvff[1])));
-  y = ff_add(y, ff_neg(ff_mul_f(r22, m2)));
-  x = ff_add(x, ff_neg(ff_mul_f(r12, m2)));
+  if (m2 != 0.f) {
+    y = ff_add(y, ff_neg(ff_mul_f(r22, m2)));
+    x = ff_add(x, ff_neg(ff_mul_f(r12, m2)));
+  }
   const float m1 = ff_floor(ff_mul(x, ff_of(g->rinvff[0])));
-  x = ff_add(x, ff_neg(ff_mul_f(r11, m1)));
+  if (m1 != 0.f) x = ff_add(x, ff_neg(ff_mul_f(r11, m1)));
   b[0] = x;
   b[1] = y;
   b[2] = z;
