@@ -240,31 +240,47 @@ __device__ __forceinline__ bool sort_before(float ka, int ia, float kb, int ib) 
 // i = perm[u] goes to slot start[c] + (number of the cell's particles that sort
 // before it), which over the cell is a permutation of its slots -- the order
 // of a sort of the cell by (kappa, input index).  There it is packed: float4
-// {rel position, input index}, {residual, kappa} and its cell id.  Every
-// thread of a cell reads the cell's keys (kappa of particle perm[v] is
-// relr[perm[v]].w): a few dozen reads at most, shared through L1.
-__device__ __forceinline__ void rankpack_body(const float4 *__restrict__ relc, const float4 *__restrict__ relr,
-                                              const int *__restrict__ perm, const int *__restrict__ start,
-                                              float4 *__restrict__ pos4, float4 *__restrict__ posr,
-                                              int *__restrict__ cell_sorted, int u) {
-  const int i = perm[u];
-  const float4 r = relc[i], rr = relr[i];
+// {rel position, input index}, {residual, kappa} and its cell id.  A block of
+// kRankThreads threads takes kRankThreads consecutive slots and first puts its
+// slots' keys (input index and kappa, the latter relr[perm[v]].w) in shared
+// memory: each thread then reads the keys of its cell's slots there, and only
+// a cell that crosses the block's range reads the rest of its keys from
+// global memory.
+constexpr int kRankThreads = 256;
+
+__device__ __forceinline__ void rankpack_block(const float4 *__restrict__ relc, const float4 *__restrict__ relr,
+                                               const int *__restrict__ perm, const int *__restrict__ start,
+                                               float4 *__restrict__ pos4, float4 *__restrict__ posr,
+                                               int *__restrict__ cell_sorted, int nslots) {
+  __shared__ int sidx[kRankThreads];
+  __shared__ float skap[kRankThreads];
+  const int u0 = blockIdx.x * kRankThreads;
+  const int u = u0 + threadIdx.x;
+  const bool valid = u < nslots;
+  const int i = valid ? perm[u] : 0;
+  const float4 rr = valid ? relr[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  sidx[threadIdx.x] = i;
+  skap[threadIdx.x] = rr.w;
+  __syncthreads();
+  if (!valid) return;
+  const float4 r = relc[i];
   const int c = __float_as_int(r.w);
   const int b = start[c], e = start[c + 1];
   const float *kap = reinterpret_cast<const float *>(relr) + 3;  // kappa of particle j: kap[4 j]
+  // the cell's slots in this block: [lo, hi), which holds slot u
+  const int lo = max(b, u0), hi = min(e, u0 + kRankThreads);
   int k = b;
-  int v = b;
-  for (; v + 4 <= e; v += 4) {
-    int iv[4];
-    float kv[4];
-#pragma unroll
-    for (int h = 0; h < 4; h++) iv[h] = perm[v + h];
-#pragma unroll
-    for (int h = 0; h < 4; h++) kv[h] = __ldg(kap + 4 * (size_t)iv[h]);
-#pragma unroll
-    for (int h = 0; h < 4; h++) k += sort_before(kv[h], iv[h], rr.w, i);
+  for (int v = b; v < lo; v++) {
+    const int iv = perm[v];
+    k += sort_before(__ldg(kap + 4 * (size_t)iv), iv, rr.w, i);
   }
-  for (; v < e; v++) {
+  int v = lo;
+  for (; v + 4 <= hi; v += 4) {
+#pragma unroll
+    for (int h = 0; h < 4; h++) k += sort_before(skap[v + h - u0], sidx[v + h - u0], rr.w, i);
+  }
+  for (; v < hi; v++) k += sort_before(skap[v - u0], sidx[v - u0], rr.w, i);
+  for (v = hi; v < e; v++) {
     const int iv = perm[v];
     k += sort_before(__ldg(kap + 4 * (size_t)iv), iv, rr.w, i);
   }
@@ -273,13 +289,13 @@ __device__ __forceinline__ void rankpack_body(const float4 *__restrict__ relc, c
   cell_sorted[k] = c;
 }
 
-__global__ void k_rankpack(const Geo *g, const float4 *__restrict__ relc, const float4 *__restrict__ relr,
-                           const int *__restrict__ perm, const int *__restrict__ start, float4 *__restrict__ pos4,
-                           float4 *__restrict__ posr, int *__restrict__ cell_sorted, int n) {
-  const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= n) return;
+__global__ void __launch_bounds__(kRankThreads) k_rankpack(const Geo *g, const float4 *__restrict__ relc,
+                                                           const float4 *__restrict__ relr,
+                                                           const int *__restrict__ perm, const int *__restrict__ start,
+                                                           float4 *__restrict__ pos4, float4 *__restrict__ posr,
+                                                           int *__restrict__ cell_sorted, int n) {
   if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
-  rankpack_body(relc, relr, perm, start, pos4, posr, cell_sorted, u);
+  rankpack_block(relc, relr, perm, start, pos4, posr, cell_sorted, n);
 }
 
 cudaError_t launch_bin(nemd_ctx *c) {
@@ -301,8 +317,8 @@ cudaError_t launch_bin(nemd_ctx *c) {
     const int tb = 256;
     const int nb = (n + tb - 1) / tb;
     k_scatter<<<nb, tb, 0, c->stream>>>(c->geo, c->relc, c->rank, c->start, c->perm, n);
-    k_rankpack<<<nb, tb, 0, c->stream>>>(c->geo, c->relc, c->relr, c->perm, c->start, c->pos4, c->posr,
-                                         c->cell_sorted, n);
+    k_rankpack<<<(n + kRankThreads - 1) / kRankThreads, kRankThreads, 0, c->stream>>>(
+        c->geo, c->relc, c->relr, c->perm, c->start, c->pos4, c->posr, c->cell_sorted, n);
     c->launches += 2;
   }
   return cudaGetLastError();
@@ -397,10 +413,10 @@ __global__ void k_b_scatter(BatchView v) {
 
 // Scattered slots [0, start[ncells]): the particles of every system that binned
 // (the cell slots of all systems are one array).
-__global__ void k_b_rankpack(BatchView v) {
-  const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= v.start[v.ncells]) return;
-  rankpack_body(v.relc, v.relr, v.perm, v.start, v.pos4, v.posr, v.cell_sorted, u);
+__global__ void __launch_bounds__(kRankThreads) k_b_rankpack(BatchView v) {
+  const int nslots = v.start[v.ncells];
+  if ((int)(blockIdx.x * kRankThreads) >= nslots) return;  // whole block
+  rankpack_block(v.relc, v.relr, v.perm, v.start, v.pos4, v.posr, v.cell_sorted, nslots);
 }
 
 cudaError_t launch_batch_bin(cudaStream_t st, const BatchView &v, int sms) {
@@ -412,7 +428,7 @@ cudaError_t launch_batch_bin(cudaStream_t st, const BatchView &v, int sms) {
   e = launch_fixed_scan(st, v.count, v.start, v.tiles, v.ncells);
   if (e != cudaSuccess) return e;
   k_b_scatter<<<nb, tb, 0, st>>>(v);
-  k_b_rankpack<<<nb, tb, 0, st>>>(v);
+  k_b_rankpack<<<v.ntot > 0 ? (v.ntot + kRankThreads - 1) / kRankThreads : 1, kRankThreads, 0, st>>>(v);
   (void)sms;
   return cudaGetLastError();
 }
