@@ -138,9 +138,9 @@ cudaError_t enqueue_step(nemd_batch *b, cudaStream_t st) {
   return nemd::launch_batch_finish(st, v);
 }
 
-// lattice, grid, stencil, bin (wrap, 3 scan, scatter, rank-and-pack), chunk
+// lattice, grid, stencil, bin (wrap, scan, scatter, rank-and-pack), chunk
 // list, force, fix-up, reduce
-constexpr int64_t kStepLaunches = 3 + 6 + 1 + 1 + 2;
+constexpr int64_t kStepLaunches = 3 + 4 + 1 + 1 + 2;
 
 }  // namespace
 
@@ -179,7 +179,7 @@ int nemd_batch_destroy(nemd_batch *b) {
   drop_graph(b);
   BatchView &v = b->v;
   void *ptrs[] = {v.geo,      (void *)v.sys_of,  (void *)v.class_sys, v.relc,       v.relr,      v.rank,   v.count,     v.start,
-                  v.tiles,    v.perm,    v.pos4,      v.posr,       v.cell_sorted, v.rows, v.rowcnt,
+                  v.perm,    v.pos4,      v.posr,       v.cell_sorted, v.rows, v.rowcnt,
                   v.chunk_off, v.chunks, v.work,     v.ppart,     v.recheck, v.nrecheck, v.sys_counters,
                   v.sys_pairs, b->sys_dev, b->lat_dev, b->grid_dev, b->pot_dev,  b->t_dev, b->q_copy,   b->f_int,
                   b->uw_int,  b->err_dev};
@@ -358,7 +358,6 @@ int nemd_batch_finalize(nemd_batch *b) {
   v.gs = b->gs;
   v.wide = b->force_kernel == 4;
   const int64_t np = ntot > 0 ? ntot : 1;
-  const int64_t cell_tiles = ncells / nemd::kFixedScanTile + 2;
   // clang-format off
   if ((r = alloc(b, &v.geo, S, "geo")) || (r = alloc(b, &b->sys_dev, S, "systems")) ||
       (r = alloc(b, &b->lat_dev, S, "lattice inputs")) || (r = alloc(b, &b->grid_dev, S, "grid inputs")) ||
@@ -370,7 +369,6 @@ int nemd_batch_finalize(nemd_batch *b) {
       (r = alloc(b, &v.cell_sorted, np, "cell_sorted")) || (r = alloc(b, &v.ppart, 2 * np, "pair sums")) ||
       (r = alloc(b, &v.chunks, np, "chunks")) ||
       (r = alloc(b, &v.count, ncells + 1, "count")) || (r = alloc(b, &v.start, ncells + 1, "start")) ||
-      (r = alloc(b, &v.tiles, cell_tiles, "scan tiles")) ||
       (r = alloc(b, &v.rows, nclasses * nemd::kBatchRowStride, "rows")) ||
       (r = alloc(b, &v.rowcnt, nclasses, "rowcnt")) ||
       (r = alloc(b, &v.chunk_off, nclasses + 1, "chunk offsets")) ||

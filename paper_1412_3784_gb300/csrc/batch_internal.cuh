@@ -45,7 +45,7 @@ struct BatchView {
   const int *class_sys;  // per class slot
   const double *q;
   float4 *relc, *relr;
-  int *rank, *count, *start, *tiles, *perm;
+  int *rank, *count, *start, *perm;
   float4 *pos4, *posr;
   int *cell_sorted;
   Row *rows;
@@ -62,8 +62,6 @@ struct BatchView {
   double *UW;  // per system: U, W[9]
 };
 
-// Scan tile size of the fixed-length scans (bin.cu).
-constexpr int kFixedScanTile = 4096;
 
 // lattice.cu: one warp per entry; t (may be null) overrides lat[e].t
 cudaError_t launch_batch_lattice(cudaStream_t st, Geo *geo, const LatIn *lat, const double *t, int count);
@@ -73,8 +71,6 @@ cudaError_t launch_batch_grid(cudaStream_t st, Geo *geo, const GridIn *grid, con
 cudaError_t launch_batch_stencil(cudaStream_t st, const BatchView &v, int max_clcap);
 // bin.cu: wrap, scan, scatter, rank within the cell and pack
 cudaError_t launch_batch_bin(cudaStream_t st, const BatchView &v, int sms);
-// bin.cu: exclusive scan of in[0..len) into out[0..len], out[len] = total
-cudaError_t launch_fixed_scan(cudaStream_t st, const int *in, int *out, int *tiles, int len);
 // One block: exclusive scan of the per-class chunk counts (c2 c3 classes from
 // the grid), total at out[cap].
 cudaError_t launch_class_scan(nemd_ctx *c, const int *in, int *out, int cap);

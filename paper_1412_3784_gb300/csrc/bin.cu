@@ -248,15 +248,16 @@ __device__ __forceinline__ bool sort_before(float ka, int ia, float kb, int ib) 
 // global memory.
 constexpr int kRankThreads = 256;
 
+// valid: the block's slot u = blockIdx.x * kRankThreads + threadIdx.x holds a
+// binned particle.
 __device__ __forceinline__ void rankpack_block(const float4 *__restrict__ relc, const float4 *__restrict__ relr,
                                                const int *__restrict__ perm, const int *__restrict__ start,
                                                float4 *__restrict__ pos4, float4 *__restrict__ posr,
-                                               int *__restrict__ cell_sorted, int nslots) {
+                                               int *__restrict__ cell_sorted, bool valid) {
   __shared__ int sidx[kRankThreads];
   __shared__ float skap[kRankThreads];
   const int u0 = blockIdx.x * kRankThreads;
   const int u = u0 + threadIdx.x;
-  const bool valid = u < nslots;
   const int i = valid ? perm[u] : 0;
   const float4 rr = valid ? relr[i] : make_float4(0.f, 0.f, 0.f, 0.f);
   sidx[threadIdx.x] = i;
@@ -295,7 +296,7 @@ __global__ void __launch_bounds__(kRankThreads) k_rankpack(const Geo *g, const f
                                                            float4 *__restrict__ pos4, float4 *__restrict__ posr,
                                                            int *__restrict__ cell_sorted, int n) {
   if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
-  rankpack_block(relc, relr, perm, start, pos4, posr, cell_sorted, n);
+  rankpack_block(relc, relr, perm, start, pos4, posr, cell_sorted, blockIdx.x * kRankThreads + threadIdx.x < n);
 }
 
 cudaError_t launch_bin(nemd_ctx *c) {
@@ -361,38 +362,6 @@ cudaError_t launch_class_scan(nemd_ctx *c, const int *in, int *out, int cap) {
   return cudaGetLastError();
 }
 
-// ---- fixed-length scan: out[0..len) exclusive, out[len] = total ----
-static_assert(kFixedScanTile == kScanTile, "scan tile");
-
-__global__ void __launch_bounds__(kScanThreads) k_fscan_tiles(const int *__restrict__ in, int *__restrict__ out,
-                                                              int *__restrict__ tiles, int len) {
-  scan_tiles_body(in, out, tiles, len);
-}
-
-__global__ void __launch_bounds__(kScanThreads) k_fscan_top(int *__restrict__ tiles, int ntiles) {
-  const int total = scan_top_body(tiles, ntiles);
-  if (threadIdx.x == 0) tiles[ntiles] = total;
-}
-
-__global__ void __launch_bounds__(kScanThreads) k_fscan_add(int *__restrict__ out, const int *__restrict__ tiles,
-                                                            int len, int ntiles) {
-  const int base = blockIdx.x * kScanTile;
-  const int add = tiles[blockIdx.x];
-  for (int k = 0; k < kScanItems; k++) {
-    int idx = base + threadIdx.x * kScanItems + k;
-    if (idx < len) out[idx] += add;
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) out[len] = tiles[ntiles];
-}
-
-cudaError_t launch_fixed_scan(cudaStream_t st, const int *in, int *out, int *tiles, int len) {
-  const int ntiles = len > 0 ? (len + kScanTile - 1) / kScanTile : 1;
-  k_fscan_tiles<<<ntiles, kScanThreads, 0, st>>>(in, out, tiles, len);
-  k_fscan_top<<<1, kScanThreads, 0, st>>>(tiles, ntiles);
-  k_fscan_add<<<ntiles, kScanThreads, 0, st>>>(out, tiles, len, ntiles);
-  return cudaGetLastError();
-}
-
 // ---- batches: every system's particles in one launch per stage ----
 
 __global__ void k_b_wrap(BatchView v) {
@@ -411,12 +380,47 @@ __global__ void k_b_scatter(BatchView v) {
   scatter_body(v.relc, v.rank, v.start, v.perm, i);
 }
 
-// Scattered slots [0, start[ncells]): the particles of every system that binned
-// (the cell slots of all systems are one array).
+// One block per system: the exclusive scan of the counts of its cells
+// j < ncells into start[coff + j], from the base poff (system s's particles
+// take the sorted slots [poff, poff + n), as in the input), and
+// start[coff + ncells] = poff + n.  Only the cells of the step's grid are read
+// (a system's cell slots are sized for the largest cell factor); a system that
+// failed this step binned nothing, and no kernel reads its cells.
+__global__ void __launch_bounds__(kScanThreads) k_b_scan_cells(BatchView v) {
+  __shared__ int sh[32];
+  const Geo *g = v.geo + blockIdx.x;
+  if (g->error & (ERRB_BOX | ERRB_CAPACITY)) return;
+  const SysInfo si = v.sys[blockIdx.x];
+  const int len = g->ncells;
+  const int *in = v.count + si.coff;
+  int *out = v.start + si.coff;
+  int carry = si.poff;
+  for (int base = 0; base < len; base += kScanTile) {
+    int c[kScanItems];
+    int sum = 0;
+    for (int k = 0; k < kScanItems; k++) {
+      const int idx = base + threadIdx.x * kScanItems + k;
+      c[k] = (idx < len) ? in[idx] : 0;
+      sum += c[k];
+    }
+    int total;
+    int ex = block_exclusive_scan(sum, sh, total) + carry;
+    for (int k = 0; k < kScanItems; k++) {
+      const int idx = base + threadIdx.x * kScanItems + k;
+      if (idx < len) out[idx] = ex;
+      ex += c[k];
+    }
+    carry += total;
+  }
+  if (threadIdx.x == 0) out[len] = carry;
+}
+
+// Sorted slots of every system that binned (the slots of a system that failed
+// this step hold nothing).
 __global__ void __launch_bounds__(kRankThreads) k_b_rankpack(BatchView v) {
-  const int nslots = v.start[v.ncells];
-  if ((int)(blockIdx.x * kRankThreads) >= nslots) return;  // whole block
-  rankpack_block(v.relc, v.relr, v.perm, v.start, v.pos4, v.posr, v.cell_sorted, nslots);
+  const int u = blockIdx.x * kRankThreads + threadIdx.x;
+  const bool valid = u < v.ntot && !(v.geo[v.sys_of[u]].error & (ERRB_BOX | ERRB_CAPACITY));
+  rankpack_block(v.relc, v.relr, v.perm, v.start, v.pos4, v.posr, v.cell_sorted, valid);
 }
 
 cudaError_t launch_batch_bin(cudaStream_t st, const BatchView &v, int sms) {
@@ -425,8 +429,7 @@ cudaError_t launch_batch_bin(cudaStream_t st, const BatchView &v, int sms) {
   const int tb = 256;
   const int nb = v.ntot > 0 ? (v.ntot + tb - 1) / tb : 1;
   k_b_wrap<<<nb, tb, 0, st>>>(v);
-  e = launch_fixed_scan(st, v.count, v.start, v.tiles, v.ncells);
-  if (e != cudaSuccess) return e;
+  k_b_scan_cells<<<v.nsys > 0 ? v.nsys : 1, kScanThreads, 0, st>>>(v);
   k_b_scatter<<<nb, tb, 0, st>>>(v);
   k_b_rankpack<<<v.ntot > 0 ? (v.ntot + kRankThreads - 1) / kRankThreads : 1, kRankThreads, 0, st>>>(v);
   (void)sms;

@@ -46,7 +46,7 @@ def test_batch_equals_single_contexts_and_oracle():
     b = nemd.Batch([spec(w, v) for w, v in zip(ws, vs)])
     F, UW = evaluate(b, ws)
     st, launches = b.stats()
-    assert launches == 13
+    assert launches == 11
     for s, (w, v) in enumerate(zip(ws, vs)):
         lo, hi = b.offsets[s], b.offsets[s + 1]
         one = run(w, v, kernel=(4, 32))
