@@ -636,11 +636,14 @@ __global__ void __launch_bounds__(kRowThreads, kRowMinBlocks) k_b_force_row(Batc
   __shared__ RowStage stage[kWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nch = v.chunk_off[v.nclasses];
+  // lane 0 claims the warp's next chunk while the current one is evaluated, so
+  // the counter's round trip overlaps useful work
+  int nxt = 0;
+  if (lane == 0) nxt = atomicAdd(v.work, 1);
   for (;;) {
-    int ch = 0;
-    if (lane == 0) ch = atomicAdd(v.work, 1);
-    ch = __shfl_sync(FULL, ch, 0);
+    const int ch = __shfl_sync(FULL, nxt, 0);
     if (ch >= nch) break;
+    if (lane == 0) nxt = atomicAdd(v.work, 1);
     const int4 cd = v.chunks[ch];
     const int s = v.class_sys[cd.z];
     Geo *g = v.geo + s;
