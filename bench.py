@@ -65,8 +65,8 @@ C_PAIR = 24    # FP32 instructions per interacting pair (force, energy, virial, 
 # dram__bytes_write.sum; bench.py --sections kernel, third of three back-to-back
 # launches, so that no earlier kernel's output is written back during it); valid
 # only while the kernel's sources are the ones captured (sha1 prefixes).
-ROW_TRAFFIC = {"bytes": 40.330496e6 + 1.498624e6,
-               "sha1": {"paper_1412_3784_gb300/csrc/force_row.cu": "7c7d642f7bf0",
+ROW_TRAFFIC = {"bytes": 40.376832e6 + 1.360128e6,
+               "sha1": {"paper_1412_3784_gb300/csrc/force_row.cu": "de5d4de416f6",
                         "paper_1412_3784_gb300/csrc/force_common.cuh": "7add2c4a0360"}}
 
 
