@@ -95,14 +95,14 @@ def parse():
                    help="force kernel without autotuning (0 plain, 1 grouped, 2 warp, 3 warp half, 4 row)")
     p.add_argument("--group", type=int, default=16, help="lanes per group of the grouped kernel")
     p.add_argument("--kfac", type=int, default=1, help="cell-size factor without autotuning")
-    p.add_argument("--streams", type=int, default=4,
+    p.add_argument("--streams", type=int, default=5,
                    help="contexts (each on its own CUDA stream) that take the strains of the tuned step in turn")
     p.add_argument("--sections", default="main,batched,learned,shear,equilibrium,integrate",
                    help="comma list of main, batched, learned, shear, equilibrium, integrate; or "
                         "'kernel' alone: one strain's forces evaluated three times back to back "
                         "(the force kernel of the default options, for a counter capture)")
     p.add_argument("--batch-steps", type=int, default=10)
-    p.add_argument("--batch-streams", type=int, default=3,
+    p.add_argument("--batch-streams", type=int, default=4,
                    help="batches of the same systems (each on its own CUDA stream) that take the batched "
                         "section's steps in turn")
     p.add_argument("--learned-strains", type=int, default=64,
