@@ -181,7 +181,7 @@ int nemd_batch_destroy(nemd_batch *b) {
   void *ptrs[] = {v.geo,      (void *)v.sys_of,  (void *)v.class_sys, v.relc,       v.relr,      v.rank,   v.count,     v.start,
                   v.perm,    v.pos4,      v.posr,       v.cell_sorted, v.rows, v.rowcnt,
                   v.chunk_off, v.chunks, v.work,     v.ppart,     v.recheck, v.nrecheck, v.sys_counters,
-                  v.sys_pairs, b->sys_dev, b->lat_dev, b->grid_dev, b->pot_dev,  b->t_dev, b->q_copy,   b->f_int,
+                  v.sys_pairs, v.red_part, v.red_ticket, b->sys_dev, b->lat_dev, b->grid_dev, b->pot_dev,  b->t_dev, b->q_copy,   b->f_int,
                   b->uw_int,  b->err_dev};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -375,6 +375,7 @@ int nemd_batch_finalize(nemd_batch *b) {
       (r = alloc(b, &v.work, 1, "work")) ||
       (r = alloc(b, &v.recheck, nemd::kRecheckCap, "recheck")) || (r = alloc(b, &v.nrecheck, 1, "nrecheck")) ||
       (r = alloc(b, &v.sys_counters, 2 * S, "counters")) || (r = alloc(b, &v.sys_pairs, S, "pairs")) ||
+      (r = alloc(b, &v.red_part, (int64_t)nemd::kReduceSums * nemd::kReduceSplit * S, "reduction partials")) || (r = alloc(b, &v.red_ticket, S, "tickets")) ||
       (r = alloc(b, &b->uw_int, 10 * S, "UW")) || (r = alloc(b, &b->err_dev, S, "errors")))
     return r;
   // clang-format on
@@ -389,6 +390,7 @@ int nemd_batch_finalize(nemd_batch *b) {
   v.t = b->t_dev;
   CKB(cudaMemsetAsync(v.geo, 0, sizeof(Geo) * S, b->stream));
   CKB(cudaMemsetAsync(v.sys_pairs, 0, sizeof(unsigned long long) * S, b->stream));
+  CKB(cudaMemsetAsync(v.red_ticket, 0, sizeof(unsigned) * S, b->stream));
   CKB(cudaMemsetAsync(v.sys_counters, 0, 2 * sizeof(unsigned long long) * S, b->stream));
   CKB(cudaMemcpyAsync(b->sys_dev, si.data(), sizeof(SysInfo) * S, cudaMemcpyHostToDevice, b->stream));
   CKB(cudaMemcpyAsync(b->lat_dev, lat.data(), sizeof(LatIn) * S, cudaMemcpyHostToDevice, b->stream));

@@ -30,6 +30,11 @@ struct SysInfo {
   int pad[2];
 };
 
+// Blocks per system of the batch's final reduction, and the sums each writes
+// (U, six virial components, pairs).
+constexpr int kReduceSplit = 4;
+constexpr int kReduceSums = 8;
+
 // Pointers and totals one batched step uses (passed by value to the kernels).
 struct BatchView {
   int nsys, ntot, ncells, nclasses;  // systems; totals of particles, cell and class slots
@@ -58,6 +63,8 @@ struct BatchView {
   int *nrecheck;
   unsigned long long *sys_counters;  // per system: candidates, band candidates
   unsigned long long *sys_pairs;     // per system: interacting pairs
+  double *red_part;      // per system and reduction block: its kReduceSums sums
+  unsigned *red_ticket;  // per system: reduction blocks finished (0 between steps)
   float *F;
   double *UW;  // per system: U, W[9]
 };

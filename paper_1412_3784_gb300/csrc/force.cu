@@ -519,9 +519,13 @@ __global__ void k_b_fixup(BatchView v) {
   }
 }
 
-// One block per system: float64 sums of its particles' pair sums in sorted
-// order (fixed), halved for the full neighbourhoods, the virial rotated back to
-// Cartesian for the dynamic offset frame (W = Q W_R Q^T).
+// kReduceSplit blocks per system: block r sums the r-th contiguous quarter of
+// the system's sorted particles' pair sums; the last of them to finish (a
+// ticket per system, returned to zero) adds the blocks' sums in block order,
+// halves them for the full neighbourhoods, rotates the virial back to
+// Cartesian for the dynamic offset frame (W = Q W_R Q^T) and publishes.  The
+// order of every addition is fixed.
+
 __global__ void __launch_bounds__(256) k_b_reduce(BatchView v) {
   // float32 pair sums accumulated in float-float (the float64 pipe runs at
   // 1/64 of the float32 rate here), pair counts in 64-bit integers; a fixed
@@ -530,14 +534,17 @@ __global__ void __launch_bounds__(256) k_b_reduce(BatchView v) {
   constexpr int kW = 256 / 32;
   __shared__ float shh[kW][K], shl[kW][K];
   __shared__ long long shn[kW];
-  const int s = blockIdx.x;
+  __shared__ bool last;
+  const int s = blockIdx.x / kReduceSplit, r = blockIdx.x % kReduceSplit;
   Geo *g = v.geo + s;
   const bool ok = !(g->error & (ERRB_BOX | ERRB_CAPACITY));
   int b = 0, e = 0;
   if (ok) {
     const int coff = v.sys[s].coff;
-    b = v.start[coff];
-    e = v.start[coff + g->ncells];
+    const int b0 = v.start[coff], e0 = v.start[coff + g->ncells];
+    const long long len = e0 - b0;
+    b = b0 + (int)(len * r / kReduceSplit);
+    e = b0 + (int)(len * (r + 1) / kReduceSplit);
   }
   ff a[K];
 #pragma unroll
@@ -586,18 +593,35 @@ __global__ void __launch_bounds__(256) k_b_reduce(BatchView v) {
     shn[warp] = np;
   }
   __syncthreads();
-  double sh0[K + 1];
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < K; k++) {
-      double x = 0.0;
-      for (int w = 0; w < kW; w++) x += (double)shh[w][k] + (double)shl[w][k];
-      sh0[k] = x;
-    }
+  // this block's sums in float64 (thread k: value k, warps in order)
+  static_assert(K + 1 == kReduceSums, "reduction sums");
+  double *mine = v.red_part + (size_t)blockIdx.x * kReduceSums;
+  if (threadIdx.x < K) {
+    double x = 0.0;
+    for (int w = 0; w < kW; w++) x += (double)shh[w][threadIdx.x] + (double)shl[w][threadIdx.x];
+    mine[threadIdx.x] = x;
+  } else if (threadIdx.x == K) {
     long long n2 = 0;
     for (int w = 0; w < kW; w++) n2 += shn[w];
-    sh0[K] = (double)n2;
+    mine[K] = (double)n2;
   }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0)
+    last = atomicAdd(&v.red_ticket[s], 1u) == (unsigned)(kReduceSplit - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  __shared__ double sh0[K + 1];
+  if (threadIdx.x <= K) {
+    const double *part = v.red_part + (size_t)s * kReduceSplit * kReduceSums;
+    double x = 0.0;
+    for (int q = 0; q < kReduceSplit; q++) x += __ldcg(part + q * kReduceSums + threadIdx.x);
+    sh0[threadIdx.x] = x;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
+    v.red_ticket[s] = 0u;
     double Wr[9];
     Wr[0] = 0.5 * sh0[1];
     Wr[4] = 0.5 * sh0[2];
@@ -628,7 +652,7 @@ __global__ void __launch_bounds__(256) k_b_reduce(BatchView v) {
 
 cudaError_t launch_batch_finish(cudaStream_t st, const BatchView &v) {
   k_b_fixup<<<4, 256, 0, st>>>(v);
-  k_b_reduce<<<v.nsys, 256, 0, st>>>(v);
+  k_b_reduce<<<v.nsys * kReduceSplit, 256, 0, st>>>(v);
   return cudaGetLastError();
 }
 

@@ -364,14 +364,17 @@ __device__ __forceinline__ bool batch_class(const BatchView &v, int slot, const 
 // dozen cells) and there are many of them, so each thread walks its own row
 // in global memory.  The batched force kernels take chunks from a shared
 // counter and write every particle's sums to its own slot, so no result
-// depends on where a chunk sits in the list: one kernel builds it, each warp
-// counting its rows' chunks, claiming a contiguous range of the list with one
-// atomic addition and walking its rows again to write them (the second walk
-// reads what the first brought into L1).  The list's length ends at
+// depends on where a chunk sits in the list: one kernel builds it, each thread
+// walking its row once and keeping the first kChunkBuf chunks in shared
+// memory, each warp claiming a contiguous range of the list for its rows'
+// chunks with one atomic addition, then writing them (a row with more chunks
+// is walked again for the rest).  The list's length ends at
 // chunk_off[nclasses], which the force kernels read.
 constexpr int kBatchWalkThreads = 128;
+constexpr int kChunkBuf = 8;
 
 __global__ void __launch_bounds__(kBatchWalkThreads) k_b_chunk_list(BatchView v) {
+  __shared__ int4 cbuf[kChunkBuf][kBatchWalkThreads];
   const int lane = threadIdx.x & 31;
   int *total = v.chunk_off + v.nclasses;
   for (int b0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); b0 < v.nclasses; b0 += gridDim.x * blockDim.x) {
@@ -380,7 +383,11 @@ __global__ void __launch_bounds__(kBatchWalkThreads) k_b_chunk_list(BatchView v)
     int c0 = 0, l1 = 0, n = 0;
     const bool has = slot < v.nclasses && batch_class(v, slot, g, c0, l1);
     const int span = has ? (v.wide ? g->span : kMaxSpan) : 0;
-    if (has) chunk_walk(v.start, c0, l1, v.gs, span, [&](int, int, int, int) { n++; });
+    if (has)
+      chunk_walk(v.start, c0, l1, v.gs, span, [&](int first, int count, int ixlo, int ixhi) {
+        if (n < kChunkBuf) cbuf[n][threadIdx.x] = make_int4(first, count, slot, ixlo | (ixhi << 16));
+        n++;
+      });
     int incl = n;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -391,11 +398,15 @@ __global__ void __launch_bounds__(kBatchWalkThreads) k_b_chunk_list(BatchView v)
     int wbase = 0;
     if (lane == 0 && wsum > 0) wbase = atomicAdd(total, wsum);
     wbase = __shfl_sync(0xffffffffu, wbase, 0);
-    int k = wbase + incl - n;
-    if (n > 0)
+    const int k = wbase + incl - n;
+    for (int j = 0; j < min(n, kChunkBuf); j++) v.chunks[k + j] = cbuf[j][threadIdx.x];
+    if (n > kChunkBuf) {
+      int j = 0;
       chunk_walk(v.start, c0, l1, v.gs, span, [&](int first, int count, int ixlo, int ixhi) {
-        v.chunks[k++] = make_int4(first, count, slot, ixlo | (ixhi << 16));
+        if (j >= kChunkBuf) v.chunks[k + j] = make_int4(first, count, slot, ixlo | (ixhi << 16));
+        j++;
       });
+    }
   }
 }
 

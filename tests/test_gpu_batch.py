@@ -143,6 +143,37 @@ def test_two_batches_in_flight_on_two_streams():
     assert force_err(ref[-1][0][:ws[0].n].astype(np.float64), o.F) <= 1e-5
 
 
+def test_warp_kernel_option_agrees_with_row_kernel():
+    """NEMD_BATCH_OPT_KERNEL = 2 (the warp kernel over the same chunk list)
+    against the default row kernel: the same pairs per system, forces, U and W
+    within float32 rounding of each other, and both against the oracle; the
+    option changes the captured step (graph re-captured) and back."""
+    ws, vs = systems(nsys=8, seed=28)
+    b = nemd.Batch([spec(w, v) for w, v in zip(ws, vs)])
+    F4, U4 = evaluate(b, ws)
+    st4, l4 = b.stats()
+    b.set_option(nemd.NEMD_BATCH_OPT_KERNEL, 2)
+    F2, U2 = evaluate(b, ws)
+    st2, l2 = b.stats()
+    b.set_option(nemd.NEMD_BATCH_OPT_KERNEL, 4)
+    F4b, U4b = evaluate(b, ws)
+    assert l4 == l2 == 11
+    assert np.array_equal(F4, F4b) and np.array_equal(U4, U4b)
+    for s, w in enumerate(ws):
+        lo, hi = b.offsets[s], b.offsets[s + 1]
+        ref = oracle.evaluate(w, "ds")
+        assert st4[s]["pairs"] == st2[s]["pairs"] == ref.npairs, s
+        # each within its own bar of the oracle (row 1e-6, warp 3e-6)
+        assert force_err(F4[lo:hi], F2[lo:hi]) <= 3e-6, s
+        assert rel(U4[s, 0], U2[s, 0]) <= 4e-6
+        assert mat_rel(U4[s, 1:].reshape(3, 3), U2[s, 1:].reshape(3, 3)) <= 4e-6
+        assert force_err(F2[lo:hi], ref.F) <= 1e-5, s
+        assert rel(U2[s, 0], ref.U) <= 3e-6
+    with pytest.raises(nemd.NemdError):
+        b.set_option(nemd.NEMD_BATCH_OPT_KERNEL, 3)
+    b.close()
+
+
 @pytest.mark.parametrize("kfac,tile", [(2, 32), (1, 16), (2, 16)])
 def test_cell_factor_and_tile_keep_results(kfac, tile):
     ws, vs = systems(nsys=6, seed=24)
